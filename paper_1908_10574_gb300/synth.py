@@ -1,0 +1,240 @@
+"""Seeded synthetic protein inputs shared by the CUDA path, the oracle and the tests.
+
+This module holds inputs only: the 20-letter alphabet, the BLOSUM62 substitution matrix
+(Henikoff & Henikoff 1992, as the paper's related-work section names it) and a background
+residue distribution, plus generators for proteome-shaped sequence sets.  It performs none of
+the method's arithmetic (no alignment, no clustering), so both the CUDA path and the CPU oracle
+may import it without sharing any computation.
+
+Workload recipes (the paper's OMA / QfO datasets are not available; these stand in for them):
+
+* families: a random root is drawn from the background distribution; each member is derived
+  from the root independently with a per-residue 30 % substitution (to a different residue,
+  drawn from the background) and a per-position 5 % single-residue indel (insertion or
+  deletion, 50/50).  This mimics homologous proteins (Sec. 4 of the paper).
+* lengths: uniform 50-300 for the small case; lognormal (median 350, sigma 0.6, clipped to
+  30-5000) for the proteome-shaped cases.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+#: residue letters in the order used for residue codes 0..19 (NCBI matrix order)
+ALPHABET = "ARNDCQEGHILKMFPSTWYV"
+
+#: BLOSUM62, rows/columns in ALPHABET order (published NCBI table, integer half-bit units)
+BLOSUM62 = np.array([
+    # A   R   N   D   C   Q   E   G   H   I   L   K   M   F   P   S   T   W   Y   V
+    [ 4, -1, -2, -2,  0, -1, -1,  0, -2, -1, -1, -1, -1, -2, -1,  1,  0, -3, -2,  0],  # A
+    [-1,  5,  0, -2, -3,  1,  0, -2,  0, -3, -2,  2, -1, -3, -2, -1, -1, -3, -2, -3],  # R
+    [-2,  0,  6,  1, -3,  0,  0,  0,  1, -3, -3,  0, -2, -3, -2,  1,  0, -4, -2, -3],  # N
+    [-2, -2,  1,  6, -3,  0,  2, -1, -1, -3, -4, -1, -3, -3, -1,  0, -1, -4, -3, -3],  # D
+    [ 0, -3, -3, -3,  9, -3, -4, -3, -3, -1, -1, -3, -1, -2, -3, -1, -1, -2, -2, -1],  # C
+    [-1,  1,  0,  0, -3,  5,  2, -2,  0, -3, -2,  1,  0, -3, -1,  0, -1, -2, -1, -2],  # Q
+    [-1,  0,  0,  2, -4,  2,  5, -2,  0, -3, -3,  1, -2, -3, -1,  0, -1, -3, -2, -2],  # E
+    [ 0, -2,  0, -1, -3, -2, -2,  6, -2, -4, -4, -2, -3, -3, -2,  0, -2, -2, -3, -3],  # G
+    [-2,  0,  1, -1, -3,  0,  0, -2,  8, -3, -3, -1, -2, -1, -2, -1, -2, -2,  2, -3],  # H
+    [-1, -3, -3, -3, -1, -3, -3, -4, -3,  4,  2, -3,  1,  0, -3, -2, -1, -3, -1,  3],  # I
+    [-1, -2, -3, -4, -1, -2, -3, -4, -3,  2,  4, -2,  2,  0, -3, -2, -1, -2, -1,  1],  # L
+    [-1,  2,  0, -1, -3,  1,  1, -2, -1, -3, -2,  5, -1, -3, -1,  0, -1, -3, -2, -2],  # K
+    [-1, -1, -2, -3, -1,  0, -2, -3, -2,  1,  2, -1,  5,  0, -2, -1, -1, -1, -1,  1],  # M
+    [-2, -3, -3, -3, -2, -3, -3, -3, -1,  0,  0, -3,  0,  6, -4, -2, -2,  1,  3, -1],  # F
+    [-1, -2, -2, -1, -3, -1, -1, -2, -2, -3, -3, -1, -2, -4,  7, -1, -1, -4, -3, -2],  # P
+    [ 1, -1,  1,  0, -1,  0,  0,  0, -1, -2, -2,  0, -1, -2, -1,  4,  1, -3, -2, -2],  # S
+    [ 0, -1,  0, -1, -1, -1, -1, -2, -2, -1, -1, -1, -1, -2, -1,  1,  5, -2, -2,  0],  # T
+    [-3, -3, -4, -4, -2, -2, -3, -2, -2, -3, -2, -3, -1,  1, -4, -3, -2, 11,  2, -3],  # W
+    [-2, -2, -2, -3, -2, -1, -2, -3,  2, -1, -1, -2, -1,  3, -3, -2, -2,  2,  7, -1],  # Y
+    [ 0, -3, -3, -3, -1, -2, -2, -3, -3,  3,  1, -2,  1, -1, -2, -2,  0, -3, -1,  4],  # V
+], dtype=np.int8)
+
+#: Background amino-acid frequencies (Robinson & Robinson 1991), ALPHABET order, normalised.
+_BG_RAW = np.array([0.07805, 0.05129, 0.04487, 0.05364, 0.01925, 0.04264, 0.06295, 0.07377,
+                    0.02199, 0.05142, 0.09019, 0.05744, 0.02243, 0.03856, 0.05203, 0.07120,
+                    0.05841, 0.01330, 0.03216, 0.06441])
+BACKGROUND = _BG_RAW / _BG_RAW.sum()
+
+#: default affine gap penalties (gap of k residues costs GAP_OPEN + (k-1)*GAP_EXTEND)
+GAP_OPEN = 11
+GAP_EXTEND = 1
+
+SEED = 1908
+
+_CODE = np.full(256, 255, dtype=np.uint8)
+for _i, _c in enumerate(ALPHABET):
+    _CODE[ord(_c)] = _i
+    _CODE[ord(_c.lower())] = _i
+
+
+def encode(s: str) -> np.ndarray:
+    """Map an amino-acid string to residue codes 0..19 (raises on any other letter)."""
+    a = _CODE[np.frombuffer(s.encode("ascii"), dtype=np.uint8)]
+    if (a == 255).any():
+        raise ValueError("non-amino-acid letter in %r" % s[:40])
+    return a
+
+
+def decode(codes) -> str:
+    return "".join(ALPHABET[int(c)] for c in codes)
+
+
+class SeqSet:
+    """Sequences as one concatenated uint8 code array plus int64 offsets (n+1)."""
+
+    def __init__(self, seqs, offsets, family=None):
+        self.seqs = np.ascontiguousarray(seqs, dtype=np.uint8)
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.family = None if family is None else np.asarray(family, dtype=np.int32)
+
+    @classmethod
+    def from_list(cls, arrays, family=None):
+        lens = np.array([len(a) for a in arrays], dtype=np.int64)
+        off = np.zeros(len(arrays) + 1, dtype=np.int64)
+        np.cumsum(lens, out=off[1:])
+        cat = np.concatenate([np.asarray(a, dtype=np.uint8) for a in arrays]) if arrays else \
+            np.zeros(0, dtype=np.uint8)
+        return cls(cat, off, family)
+
+    def __len__(self):
+        return len(self.offsets) - 1
+
+    @property
+    def lengths(self):
+        return np.diff(self.offsets)
+
+    def __getitem__(self, i):
+        return self.seqs[self.offsets[i]:self.offsets[i + 1]]
+
+    def subset(self, ids):
+        ids = np.asarray(ids)
+        return SeqSet.from_list([self[int(i)] for i in ids],
+                                None if self.family is None else self.family[ids])
+
+
+def _rng(stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED, stream])))
+
+
+def random_seq(rng, n):
+    return rng.choice(20, size=n, p=BACKGROUND).astype(np.uint8)
+
+
+def mutate(rng, root, sub_rate=0.30, indel_rate=0.05):
+    """Member derived from root: per-residue substitution to a different residue, then
+    per-position single-residue indels (insertion or deletion with equal probability)."""
+    out = []
+    for r in root:
+        if rng.random() < indel_rate:
+            if rng.random() < 0.5:          # deletion of this position
+                continue
+            out.append(int(random_seq(rng, 1)[0]))   # insertion before this position
+        if rng.random() < sub_rate:
+            p = BACKGROUND.copy()
+            p[r] = 0.0
+            p /= p.sum()
+            out.append(int(rng.choice(20, p=p)))
+        else:
+            out.append(int(r))
+    if not out:
+        out.append(int(root[0]))
+    return np.array(out, dtype=np.uint8)
+
+
+def _mutate_fast(rng, root, sub_rate=0.30, indel_rate=0.05):
+    """Vectorised form of `mutate` with the same model (used for the large sets)."""
+    n = len(root)
+    ev = rng.random(n) < indel_rate
+    ins = rng.random(n) < 0.5
+    sub = rng.random(n) < sub_rate
+    base = root.copy()
+    if sub.any():
+        # different residue: draw from background conditioned on != original
+        cand = random_seq(rng, int(sub.sum()) * 2 + 8)
+        k = 0
+        idx = np.nonzero(sub)[0]
+        for pos in idx:
+            while cand[k] == base[pos]:
+                k += 1
+                if k >= len(cand):
+                    cand = random_seq(rng, len(idx) * 2 + 8)
+                    k = 0
+            base[pos] = cand[k]
+            k += 1
+    keep = ~(ev & ~ins)
+    insert_here = ev & ins
+    parts = []
+    ins_res = random_seq(rng, int(insert_here.sum()) + 1)
+    j = 0
+    out = np.empty(n + int(insert_here.sum()), dtype=np.uint8)
+    o = 0
+    for pos in range(n):
+        if insert_here[pos]:
+            out[o] = ins_res[j]; j += 1; o += 1
+        if keep[pos]:
+            out[o] = base[pos]; o += 1
+    out = out[:o]
+    if o == 0:
+        out = root[:1].copy()
+    del parts
+    return out
+
+
+def lognormal_lengths(rng, n, median=350.0, sigma=0.6, lo=30, hi=5000):
+    return np.clip(np.round(rng.lognormal(np.log(median), sigma, size=n)), lo, hi).astype(np.int64)
+
+
+def families(n_families, members, root_lengths, stream, singletons=0, singleton_lengths=None,
+             fast=True):
+    """Planted families plus optional unrelated singletons, shuffled with a seeded permutation."""
+    rng = _rng(stream)
+    seqs, fam = [], []
+    mut = _mutate_fast if fast else mutate
+    for f in range(n_families):
+        root = random_seq(rng, int(root_lengths[f]))
+        for _ in range(members):
+            seqs.append(mut(rng, root))
+            fam.append(f)
+    for s in range(singletons):
+        seqs.append(random_seq(rng, int(singleton_lengths[s])))
+        fam.append(n_families + s)
+    perm = rng.permutation(len(seqs))
+    return SeqSet.from_list([seqs[i] for i in perm], np.array(fam, dtype=np.int32)[perm])
+
+
+def small_families(stream=1):
+    """200 proteins: 20 families of 10, root length uniform 50-300 (the small all-pairs case)."""
+    rng = _rng(100 + stream)
+    return families(20, 10, rng.integers(50, 301, size=20), stream)
+
+
+def proteome(n_seqs=20000, family_size=10, singleton_frac=0.0, stream=2):
+    """Proteome-shaped set: lognormal lengths (median 350, sigma 0.6, clip 30-5000),
+    planted families of `family_size`, plus a fraction of unrelated singletons."""
+    rng = _rng(200 + stream)
+    n_single = int(round(n_seqs * singleton_frac))
+    n_fam = (n_seqs - n_single) // family_size
+    return families(n_fam, family_size, lognormal_lengths(rng, n_fam), stream,
+                    singletons=n_single, singleton_lengths=lognormal_lengths(rng, n_single))
+
+
+def tandem_repeat(rng, length, motif_len=40, sub_rate=0.05):
+    """Long self-similar sequence: copies of one random motif, each copy with 5 % substitutions."""
+    motif = random_seq(rng, motif_len)
+    reps = []
+    while sum(len(r) for r in reps) < length:
+        c = motif.copy()
+        m = rng.random(motif_len) < sub_rate
+        c[m] = random_seq(rng, int(m.sum()))
+        reps.append(c)
+    return np.concatenate(reps)[:length]
+
+
+def random_pairs(n_seqs, n_pairs, stream=3):
+    rng = _rng(300 + stream)
+    a = rng.integers(0, n_seqs, size=n_pairs)
+    b = rng.integers(0, n_seqs, size=n_pairs)
+    return np.stack([a, b], axis=1).astype(np.int32)
+
+
+def random_codes(n, stream=4, alphabet=20):
+    rng = _rng(400 + stream)
+    return rng.integers(0, alphabet, size=n).astype(np.uint8)
