@@ -1,0 +1,135 @@
+/*
+ * cm.h -- C ABI of the GB300 batched Smith-Waterman / ClusterMerge library (libcm.so).
+ *
+ * What is computed (Byma et al., "Parallel and Scalable Precise Clustering for Homologous
+ * Protein Discovery", PPoPP'20):
+ *   - the similarity f of two proteins is their Smith-Waterman local-alignment score under a
+ *     substitution matrix with gaps (Sec. 4); this library uses the affine (Gotoh) gap model,
+ *     a gap of k residues costing gap_open + (k-1)*gap_extend (CM_GAP_BLAST: open + k*extend);
+ *   - a pair (i, j) is significant when f(i, j) > T (Sec. 3);
+ *   - ClusterMerge builds a precise clustering by bottom-up cluster-set merges (Algorithm 1
+ *     Merge, Algorithm 2 BottomUpMerge) with the protein transitivity test of Sec. 4 (score >
+ *     mT and fewer than mU uncovered residues), then aligns all pairs inside each final
+ *     cluster (Sec. 6.1).
+ *
+ * Conventions for every entry point
+ *   - Return value: CM_OK (0) or a negative CM_ERR_* code; cm_last_error() describes the last
+ *     error on that context.  On error no output array has been written.
+ *   - Sequences: `seqs` is one concatenated array of residue codes 0..19 in the order
+ *     ARNDCQEGHILKMFPSTWYV (or ASCII letters with CM_ASCII); sequence i is
+ *     seqs[offsets[i] .. offsets[i+1]), offsets has n_seqs+1 non-decreasing int64 entries
+ *     starting at 0.  Sequences may be empty (their scores are 0).
+ *   - Matrix: 400 int8 entries, row-major, matrix[x*20 + y] = score of residue x of the
+ *     pair's FIRST sequence against residue y of its SECOND sequence.  Entries must lie in
+ *     [-1000, 1000]; it need not be symmetric.
+ *   - Gaps: 1 <= first-gap cost (gap_open, or gap_open+gap_extend with CM_GAP_BLAST) <= 1000,
+ *     0 <= gap_extend <= first-gap cost.
+ *   - Pointers: host memory by default; with CM_DEVICE_PTRS every array argument is device
+ *     memory on the context's device and all work is ordered on the context's stream
+ *     (cm_set_stream); the call still returns after the results are written.
+ *   - Ownership: the caller owns every input and output array; the library never keeps a
+ *     pointer to them after returning.  cm_result objects are owned by the library and freed
+ *     with cm_result_free().
+ *   - Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef CM_H
+#define CM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CM_OK              0
+#define CM_ERR_ARG        -1   /* invalid argument (null pointer, bad size, bad offsets) */
+#define CM_ERR_RESIDUE    -2   /* residue code >= 20, or non-amino-acid letter with CM_ASCII */
+#define CM_ERR_OOM        -3   /* device or host allocation failed */
+#define CM_ERR_CUDA       -4   /* a CUDA call failed; message in cm_last_error() */
+#define CM_ERR_TIMEOUT    -5   /* a bounded device wait gave up (work queue never filled) */
+#define CM_ERR_CAPACITY   -6   /* output capacity too small; *n_found holds the needed size */
+#define CM_ERR_INTERNAL   -7   /* a kernel's own bounds check fired (a library bug) */
+
+/* ---- flags ---- */
+#define CM_DEVICE_PTRS    0x1u  /* all array arguments are device pointers */
+#define CM_ASCII          0x2u  /* seqs holds ASCII letters (upper or lower case) */
+#define CM_GAP_BLAST      0x4u  /* gap of k residues costs open + k*extend */
+#define CM_FORCE_INT32    0x8u  /* score every pair on the int32 path (no int16x2 first pass) */
+
+typedef struct cm_ctx cm_ctx;
+
+/* Create a context on CUDA device `device`: a stream, device scratch grown on demand, and
+ * the scheduler's tuning state.  *out is set to NULL on failure. */
+int cm_create(cm_ctx **out, int device);
+
+/* Release the context and every device buffer it owns.  NULL is ignored. */
+void cm_destroy(cm_ctx *ctx);
+
+/* Message of the last error on this context ("" if none).  Valid until the next call on it. */
+const char *cm_last_error(const cm_ctx *ctx);
+
+/* Order all further device work of this context on `cuda_stream` (a cudaStream_t on the
+ * context's device; NULL selects the context's own stream). */
+int cm_set_stream(cm_ctx *ctx, void *cuda_stream);
+
+/* Scheduler tuning of the int16x2 kernel: warps per CTA (4, 8 or 16) and target rows per
+ * warp stream (256 .. 65536).  0 keeps the current value.  The autotuner sets these. */
+int cm_set_tuning(cm_ctx *ctx, int32_t warps_per_cta, int32_t rows_per_warp);
+
+/* Counters of the work done since cm_create or the last cm_reset_stats. */
+typedef struct {
+    int64_t pairs;              /* pairs scored */
+    int64_t cells;              /* sum of len(a)*len(b) over the pairs scored */
+    int64_t cells_padded;       /* cells actually computed by the int16x2 kernel (padding incl.) */
+    int64_t saturated;          /* pairs rerun on the int32 path after int16 saturation */
+    int64_t launches;           /* kernel launches */
+    int64_t sw16_launches;      /* launches of the int16x2 Smith-Waterman kernel */
+    double  sw16_ms;            /* device time of those launches (CUDA events on the stream) */
+    double  total_ms;           /* device time of whole calls (CUDA events on the stream) */
+} cm_stats;
+int cm_get_stats(const cm_ctx *ctx, cm_stats *out);
+int cm_reset_stats(cm_ctx *ctx);
+
+/* sw_score_batch -- similarity f (Sec. 4) of every pair in a list.
+ *   pairs:      2*n_pairs int32 sequence indices; pair k is (pairs[2k], pairs[2k+1]) and is
+ *               scored with the matrix indexed [first][second].
+ *   scores_out: n_pairs int32, the Smith-Waterman (Gotoh) local-alignment score of each pair,
+ *               exact (int16x2 pass; pairs that could overflow int16 are rerun in int32).
+ * Pairs sharing their first sequence are scored together against that sequence's query
+ * profile, so listing the sequence with many partners first is fastest. */
+int sw_score_batch(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                   const int32_t *pairs, int64_t n_pairs, const int8_t *matrix,
+                   int32_t gap_open, int32_t gap_extend, int32_t *scores_out, uint32_t flags);
+
+/* sw_cells_batch -- score plus the cells of one optimal local alignment per pair, the
+ * quantity the protein transitivity test needs (Sec. 4: residues uA, uD left uncovered).
+ *   cells_out: 5*n_pairs int32: score, i_start, i_end, j_start, j_end (1-based, inclusive,
+ *              i over the first sequence).  The end cell is the first cell in row-major order
+ *              (i, then j) whose score equals the optimum; the start is the first row-major
+ *              cell of the same recurrence run on the reversed prefixes a[i_end..1],
+ *              b[j_end..1] (the optimal alignment ending there that spans the fewest residues
+ *              of a, then of b).  All four cells are 0 when the score is 0. */
+int sw_cells_batch(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                   const int32_t *pairs, int64_t n_pairs, const int8_t *matrix,
+                   int32_t gap_open, int32_t gap_extend, int32_t *cells_out, uint32_t flags);
+
+/* sw_allpairs -- the all-against-all comparison (Sec. 1, Sec. 6.1): every pair i < j of the
+ * set is aligned and the significant pairs f(i, j) > T (Sec. 3) are returned.
+ *   part, n_parts: the triangle of pairs is split into n_parts parts of about equal cell
+ *               count (pairs grouped by the longer sequence); this call scores part `part`
+ *               (0 <= part < n_parts).  The union over all parts is the full result.
+ *   pairs_out:  2*capacity int32 (i, j) with i < j;  scores_out: capacity int32.
+ *   n_found:    number of significant pairs of this part (host pointer, always host).
+ * If *n_found > capacity nothing is written and CM_ERR_CAPACITY is returned.  Output order
+ * is deterministic: by (longer sequence, shorter sequence) in length order (ties by index). */
+int sw_allpairs(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                const int8_t *matrix, int32_t gap_open, int32_t gap_extend, int32_t T,
+                int64_t part, int64_t n_parts, int32_t *pairs_out, int32_t *scores_out,
+                int64_t capacity, int64_t *n_found, uint32_t flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CM_H */

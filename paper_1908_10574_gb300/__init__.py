@@ -1,0 +1,201 @@
+"""GB300-native batched Smith-Waterman scoring and ClusterMerge precise clustering.
+
+Thin Python binding of libcm.so (see include/cm.h).  Host inputs are numpy arrays; device
+inputs are torch CUDA tensors (then every array must be on the GPU and the current torch
+stream is used).  Names follow the C ABI: sw_score_batch, sw_cells_batch, sw_allpairs.
+
+The library is loaded on first use; importing the package does not need a GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as _L
+from ._lib import CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS  # noqa: F401
+
+__all__ = ["Context", "sw_score_batch", "sw_cells_batch", "sw_allpairs", "CMError",
+           "default_context"]
+
+
+def _is_torch_cuda(x):
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch_cuda(x):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+class Context:
+    """Owns a cm_ctx (stream, device scratch, tuning) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        L = _L.lib()
+        h = ctypes.c_void_p()
+        code = L.cm_create(ctypes.byref(h), int(device))
+        if code != 0:
+            raise CMError(code, "cm_create failed (no usable CUDA device %d?)" % device)
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _L.lib().cm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- plumbing -------------------------------------------------------------------------
+    def _prep(self, arrays):
+        dev = [_is_torch_cuda(a) for a in arrays if a is not None]
+        if any(dev) and not all(dev):
+            raise ValueError("mix of host and device arrays: pass all numpy or all CUDA tensors")
+        if dev and dev[0]:
+            import torch
+            _L.check(self._h, _L.lib().cm_set_stream(
+                self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+            return CM_DEVICE_PTRS
+        _L.check(self._h, _L.lib().cm_set_stream(self._h, None))
+        return 0
+
+    @staticmethod
+    def _host(x, dtype, shape=None):
+        x = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+        if shape is not None:
+            x = x.reshape(shape)
+        return x
+
+    def _inputs(self, seqs, offsets, matrix, pairs=None):
+        if _is_torch_cuda(seqs):
+            import torch
+            for t, dt in ((seqs, torch.uint8), (offsets, torch.int64), (matrix, torch.int8)):
+                if t.dtype != dt or not t.is_contiguous():
+                    raise TypeError("device inputs must be contiguous %s" % dt)
+            if pairs is not None and (pairs.dtype != torch.int32 or not pairs.is_contiguous()):
+                raise TypeError("device pairs must be contiguous int32")
+            return seqs, offsets, matrix, pairs
+        seqs = self._host(seqs, np.uint8)
+        offsets = self._host(offsets, np.int64)
+        matrix = self._host(matrix, np.int8, (400,))
+        if pairs is not None:
+            pairs = self._host(pairs, np.int32, (-1, 2))
+        return seqs, offsets, matrix, pairs
+
+    def stats(self):
+        s = _L.cm_stats()
+        _L.check(self._h, _L.lib().cm_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def reset_stats(self):
+        _L.check(self._h, _L.lib().cm_reset_stats(self._h))
+
+    def set_tuning(self, warps_per_cta=0, rows_per_warp=0):
+        _L.check(self._h, _L.lib().cm_set_tuning(self._h, int(warps_per_cta), int(rows_per_warp)))
+
+    # ---- entry points ---------------------------------------------------------------------
+    def sw_score_batch(self, seqs, offsets, pairs, matrix, gap_open, gap_extend, flags=0,
+                       out=None):
+        seqs, offsets, matrix, pairs = self._inputs(seqs, offsets, matrix, pairs)
+        flags |= self._prep([seqs, offsets, matrix, pairs])
+        n = int(offsets.shape[0]) - 1
+        npairs = int(pairs.shape[0])
+        if out is None:
+            if flags & CM_DEVICE_PTRS:
+                import torch
+                out = torch.empty(npairs, dtype=torch.int32, device=seqs.device)
+            else:
+                out = np.empty(npairs, dtype=np.int32)
+        _L.check(self._h, _L.lib().sw_score_batch(self._h, _ptr(seqs), _ptr(offsets), n,
+                                                  _ptr(pairs), npairs, _ptr(matrix),
+                                                  int(gap_open), int(gap_extend), _ptr(out),
+                                                  flags))
+        return out
+
+    def sw_cells_batch(self, seqs, offsets, pairs, matrix, gap_open, gap_extend, flags=0,
+                       out=None):
+        seqs, offsets, matrix, pairs = self._inputs(seqs, offsets, matrix, pairs)
+        flags |= self._prep([seqs, offsets, matrix, pairs])
+        n = int(offsets.shape[0]) - 1
+        npairs = int(pairs.shape[0])
+        if out is None:
+            if flags & CM_DEVICE_PTRS:
+                import torch
+                out = torch.empty((npairs, 5), dtype=torch.int32, device=seqs.device)
+            else:
+                out = np.empty((npairs, 5), dtype=np.int32)
+        _L.check(self._h, _L.lib().sw_cells_batch(self._h, _ptr(seqs), _ptr(offsets), n,
+                                                  _ptr(pairs), npairs, _ptr(matrix),
+                                                  int(gap_open), int(gap_extend), _ptr(out),
+                                                  flags))
+        return out
+
+    def sw_allpairs(self, seqs, offsets, matrix, gap_open, gap_extend, T, part=0, n_parts=1,
+                    flags=0, capacity=None, pairs_out=None, scores_out=None):
+        """Significant pairs (i < j, f > T) of one part of the all-against-all triangle.
+        Returns (pairs (k, 2) int32, scores (k,) int32)."""
+        seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
+        flags |= self._prep([seqs, offsets, matrix])
+        n = int(offsets.shape[0]) - 1
+        found = ctypes.c_int64(0)
+        dev = bool(flags & CM_DEVICE_PTRS)
+        if capacity is None:
+            capacity = pairs_out.shape[0] if pairs_out is not None else 1 << 16
+        for _attempt in range(2):
+            if pairs_out is None or pairs_out.shape[0] < capacity:
+                if dev:
+                    import torch
+                    pairs_out = torch.empty((capacity, 2), dtype=torch.int32, device=seqs.device)
+                    scores_out = torch.empty(capacity, dtype=torch.int32, device=seqs.device)
+                else:
+                    pairs_out = np.empty((capacity, 2), dtype=np.int32)
+                    scores_out = np.empty(capacity, dtype=np.int32)
+            code = _L.lib().sw_allpairs(self._h, _ptr(seqs), _ptr(offsets), n, _ptr(matrix),
+                                        int(gap_open), int(gap_extend), int(T), int(part),
+                                        int(n_parts), _ptr(pairs_out), _ptr(scores_out),
+                                        int(capacity), ctypes.byref(found), flags)
+            if code == _L.CM_ERR_CAPACITY:
+                capacity = int(found.value)
+                pairs_out = scores_out = None
+                continue
+            _L.check(self._h, code)
+            k = int(found.value)
+            return pairs_out[:k], scores_out[:k]
+        raise CMError(_L.CM_ERR_CAPACITY, "capacity retry failed")
+
+
+_default = {}
+
+
+def default_context(device: int = 0) -> Context:
+    if device not in _default:
+        _default[device] = Context(device)
+    return _default[device]
+
+
+def sw_score_batch(seqs, offsets, pairs, matrix, gap_open, gap_extend, flags=0, out=None):
+    return default_context().sw_score_batch(seqs, offsets, pairs, matrix, gap_open, gap_extend,
+                                            flags, out)
+
+
+def sw_cells_batch(seqs, offsets, pairs, matrix, gap_open, gap_extend, flags=0, out=None):
+    return default_context().sw_cells_batch(seqs, offsets, pairs, matrix, gap_open, gap_extend,
+                                            flags, out)
+
+
+def sw_allpairs(seqs, offsets, matrix, gap_open, gap_extend, T, part=0, n_parts=1, flags=0,
+                capacity=None):
+    return default_context().sw_allpairs(seqs, offsets, matrix, gap_open, gap_extend, T, part,
+                                         n_parts, flags, capacity)

@@ -1,0 +1,71 @@
+"""ctypes binding of libcm.so (include/cm.h).  Argument marshalling only: every step of the
+path runs in the library's CUDA kernels.  There is no CPU fallback; if the library is missing
+or no GPU is present, calls raise."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcm.so")
+
+CM_OK = 0
+CM_ERR_CAPACITY = -6
+CM_DEVICE_PTRS = 0x1
+CM_ASCII = 0x2
+CM_GAP_BLAST = 0x4
+CM_FORCE_INT32 = 0x8
+
+_ERRNAMES = {-1: "CM_ERR_ARG", -2: "CM_ERR_RESIDUE", -3: "CM_ERR_OOM", -4: "CM_ERR_CUDA",
+             -5: "CM_ERR_TIMEOUT", -6: "CM_ERR_CAPACITY", -7: "CM_ERR_INTERNAL"}
+
+
+class CMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "CM_ERR"), code, msg))
+        self.code = code
+
+
+class cm_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("cells", ctypes.c_int64),
+                ("cells_padded", ctypes.c_int64), ("saturated", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("sw16_launches", ctypes.c_int64),
+                ("sw16_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libcm.so is not built; run `python -c \"import __graft_entry__ as g; "
+                           "g.build()\"` (or paper_1908_10574_gb300/build.py) first")
+    L = ctypes.CDLL(LIB_PATH)
+    p, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "cm_create": (ctypes.c_int, [ctypes.POINTER(p), ctypes.c_int]),
+        "cm_destroy": (None, [p]),
+        "cm_last_error": (ctypes.c_char_p, [p]),
+        "cm_set_stream": (ctypes.c_int, [p, p]),
+        "cm_set_tuning": (ctypes.c_int, [p, i32, i32]),
+        "cm_get_stats": (ctypes.c_int, [p, ctypes.POINTER(cm_stats)]),
+        "cm_reset_stats": (ctypes.c_int, [p]),
+        "sw_score_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
+        "sw_cells_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
+        "sw_allpairs": (ctypes.c_int, [p, p, p, i32, p, i32, i32, i32, i64, i64, p, p, i64,
+                                       ctypes.POINTER(i64), u32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(ctx, code):
+    if code != CM_OK:
+        raise CMError(code, lib().cm_last_error(ctx).decode(errors="replace"))

@@ -1,0 +1,722 @@
+// C ABI of libcm: context, input validation, the host planner that turns pair lists into
+// length-binned CTA tasks for the persistent int16x2 kernel, the int32 rerun of saturated
+// pairs, and threshold compaction.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "cm_internal.h"
+
+namespace cm {
+int64_t compact_chunks(int64_t nslots);
+int sw16_ctas_per_sm(int R, int W);
+int sw32_ctas_per_sm();
+}  // namespace cm
+
+using namespace cm;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+enum BufId {
+    B_DB, B_RAW, B_OFF, B_BLOCKS, B_TASKS, B_IDS, B_STREAM, B_SROW, B_OUT, B_OMAP, B_BND,
+    B_FLAGS, B_PREF, B_FIRST, B_PAIRS, B_CELLS, B_SCRATCH, B_CHUNK, B_POUT, B_SOUT, B_MAT,
+    B_COUNT
+};
+
+}  // namespace
+
+struct cm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    cm_stats stats{};
+    int W = 8;
+    int rows_per_warp = 4096;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    DevBuf buf[B_COUNT];
+};
+
+namespace {
+
+int fail(cm_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA,      \
+                        std::string(#call " failed: ") + cudaGetErrorString(e_));           \
+    } while (0)
+
+template <class T>
+int ensure(cm_ctx* c, BufId id, size_t count, T** out)
+{
+    DevBuf& b = c->buf[id];
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (bytes > b.cap) {
+        if (b.p) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(b.p);
+        }
+        const size_t want = std::max(bytes, b.cap + b.cap / 2);
+        b.p = nullptr;
+        b.cap = 0;
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CM_ERR_OOM, "device allocation of " + std::to_string(want) +
+                                           " bytes failed: " + cudaGetErrorString(e));
+        }
+        b.cap = want;
+    }
+    *out = reinterpret_cast<T*>(b.p);
+    return CM_OK;
+}
+
+#define ENSURE(id, n, ptr)                                                                  \
+    do {                                                                                    \
+        int r_ = ensure(c, id, (size_t)(n), &(ptr));                                        \
+        if (r_) return r_;                                                                  \
+    } while (0)
+
+struct Prepared {
+    const uint8_t* db = nullptr;     // device residue codes
+    const int64_t* off = nullptr;    // device offsets
+    std::vector<int64_t> hoff;       // host offsets
+    int16_t mat[400];
+    int32_t g1 = 0, ge = 0;          // first-gap cost, extension cost
+    int32_t beta = 0, sat_thr = 0;
+    bool symmetric = true;
+    int64_t maxlen = 0;
+};
+
+int copy_in(cm_ctx* c, void* dst, const void* src, size_t bytes, bool dev)
+{
+    if (bytes == 0) return CM_OK;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice, c->stream));
+    return CM_OK;
+}
+
+int prepare(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+            const int8_t* matrix, int32_t gap_open, int32_t gap_extend, uint32_t flags,
+            Prepared& P)
+{
+    const bool dev = (flags & CM_DEVICE_PTRS) != 0;
+    if (!c) return CM_ERR_ARG;
+    c->err.clear();
+    if (n_seqs < 0 || !offsets || !matrix) return fail(c, CM_ERR_ARG, "null argument or n_seqs < 0");
+    // gaps
+    const int64_t g1 = (flags & CM_GAP_BLAST) ? (int64_t)gap_open + gap_extend : gap_open;
+    if (g1 < 1 || g1 > 1000 || gap_extend < 0 || gap_extend > g1)
+        return fail(c, CM_ERR_ARG, "gap costs must satisfy 1 <= first-gap cost <= 1000 and "
+                                   "0 <= gap_extend <= first-gap cost");
+    P.g1 = (int32_t)g1;
+    P.ge = gap_extend;
+    // matrix
+    int8_t hm[400];
+    if (dev) CUDA_TRY(cudaMemcpy(hm, matrix, 400, cudaMemcpyDeviceToHost));
+    else std::memcpy(hm, matrix, 400);
+    int mn = 0, mx = 0;
+    for (int i = 0; i < 400; ++i) {
+        P.mat[i] = hm[i];
+        mn = std::min<int>(mn, hm[i]);
+        mx = std::max<int>(mx, hm[i]);
+    }
+    for (int x = 0; x < 20; ++x)
+        for (int y = 0; y < 20; ++y)
+            if (hm[x * 20 + y] != hm[y * 20 + x]) P.symmetric = false;
+    P.beta = std::max<int32_t>(P.g1 + P.ge, -mn) + 1;
+    P.sat_thr = 32767 - std::max(mx, 0);
+    // offsets
+    P.hoff.resize((size_t)n_seqs + 1);
+    if (dev) CUDA_TRY(cudaMemcpy(P.hoff.data(), offsets, sizeof(int64_t) * (n_seqs + 1),
+                                 cudaMemcpyDeviceToHost));
+    else std::memcpy(P.hoff.data(), offsets, sizeof(int64_t) * (n_seqs + 1));
+    if (P.hoff[0] != 0) return fail(c, CM_ERR_ARG, "offsets[0] must be 0");
+    for (int32_t i = 0; i < n_seqs; ++i) {
+        const int64_t L = P.hoff[i + 1] - P.hoff[i];
+        if (L < 0) return fail(c, CM_ERR_ARG, "offsets must be non-decreasing");
+        P.maxlen = std::max(P.maxlen, L);
+    }
+    const int64_t total = P.hoff[n_seqs];
+    if (total > 0 && !seqs) return fail(c, CM_ERR_ARG, "seqs is null");
+    // residues
+    int32_t* flags_d;
+    ENSURE(B_FLAGS, 64, flags_d);
+    CUDA_TRY(cudaMemsetAsync(flags_d, 0, 64 * sizeof(int32_t), c->stream));
+    uint8_t* db;
+    if (flags & CM_ASCII) {
+        ENSURE(B_DB, total, db);
+        const uint8_t* src = seqs;
+        if (!dev) {
+            uint8_t* raw;
+            ENSURE(B_RAW, total, raw);
+            int r = copy_in(c, raw, seqs, total, false);
+            if (r) return r;
+            src = raw;
+        }
+        CUDA_TRY(launch_ascii_to_codes(src, db, total, flags_d, c->stream));
+        P.db = db;
+    } else if (dev) {
+        P.db = seqs;
+        CUDA_TRY(launch_check_codes(seqs, total, flags_d, c->stream));
+    } else {
+        ENSURE(B_DB, total, db);
+        int r = copy_in(c, db, seqs, total, false);
+        if (r) return r;
+        CUDA_TRY(launch_check_codes(db, total, flags_d, c->stream));
+        P.db = db;
+    }
+    if (dev) {
+        P.off = offsets;
+    } else {
+        int64_t* off;
+        ENSURE(B_OFF, n_seqs + 1, off);
+        int r = copy_in(c, off, P.hoff.data(), sizeof(int64_t) * (n_seqs + 1), false);
+        if (r) return r;
+        P.off = off;
+    }
+    int32_t bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, flags_d, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, CM_ERR_RESIDUE, (flags & CM_ASCII)
+                                                ? "non-amino-acid letter in seqs"
+                                                : "residue code >= 20 in seqs");
+    return CM_OK;
+}
+
+// ---- planning ---------------------------------------------------------------------------
+struct Plan {
+    std::vector<SwBlock> blocks;
+    std::vector<int64_t> first_slot;     // per block, ascending
+    std::vector<int32_t> ids;            // A ids then B ids
+    std::vector<int64_t> srow;           // global row table over all B subjects (+1)
+    std::vector<SwTask> tasks;           // grouped by R, cost descending inside a group
+    std::vector<int> task_R;             // R per task (parallel to tasks)
+    int64_t nslots = 0;
+    int64_t cells = 0, cells_padded = 0, pairs = 0;
+    int64_t max_warp_rows = 0;
+};
+
+void choose_R(int64_t m, int* R, int* npass)
+{
+    if (m <= 0) { *R = 4; *npass = 1; return; }
+    const int np = (int)((m + 1023) / 1024);
+    const int64_t per = (m + np - 1) / np;
+    int r = (int)((per + 31) / 32);
+    r = (r + 3) / 4 * 4;
+    r = std::max(4, std::min(32, r));
+    *R = r;
+    *npass = np;
+}
+
+// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows.
+void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
+               const int64_t* srow, int64_t target, std::vector<std::pair<int64_t, int>>& keys)
+{
+    int R, np;
+    choose_R(m_hi, &R, &np);
+    int32_t s = 0;
+    while (s < ns) {
+        const int64_t want = srow[s] + target;
+        int32_t e = (int32_t)(std::lower_bound(srow + s + 1, srow + ns + 1, want) - srow);
+        if (e > ns) e = ns;
+        SwTask t;
+        t.block = block;
+        t.k = k;
+        t.s0 = s;
+        t.s1 = e;
+        t.npass = np;
+        t.hi_valid = hi_valid ? 1 : 0;
+        const int64_t rows = srow[e] - srow[s];
+        P.cells_padded += rows * 32 * R * np * 2;
+        P.tasks.push_back(t);
+        P.task_R.push_back(R);
+        keys.push_back({rows * R * np, R});
+        s = e;
+    }
+}
+
+void order_tasks(Plan& P, const std::vector<std::pair<int64_t, int>>& keys)
+{
+    std::vector<size_t> idx(P.tasks.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+        if (keys[x].second != keys[y].second) return keys[x].second > keys[y].second;
+        return keys[x].first > keys[y].first;
+    });
+    std::vector<SwTask> t2(idx.size());
+    std::vector<int> r2(idx.size());
+    for (size_t i = 0; i < idx.size(); ++i) { t2[i] = P.tasks[idx[i]]; r2[i] = P.task_R[idx[i]]; }
+    P.tasks.swap(t2);
+    P.task_R.swap(r2);
+}
+
+// ---- execution --------------------------------------------------------------------------
+int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64_t* d_omap,
+             uint32_t flags)
+{
+    const cudaStream_t st = c->stream;
+    const int W = c->W;
+    // upload
+    SwBlock* d_blocks; SwTask* d_tasks; int32_t* d_ids; int64_t* d_srow; uint8_t* d_stream;
+    int64_t* d_first; int32_t* d_flags;
+    ENSURE(B_BLOCKS, plan.blocks.size(), d_blocks);
+    ENSURE(B_TASKS, plan.tasks.size(), d_tasks);
+    ENSURE(B_IDS, plan.ids.size(), d_ids);
+    ENSURE(B_SROW, plan.srow.size(), d_srow);
+    ENSURE(B_FIRST, plan.first_slot.size(), d_first);
+    ENSURE(B_FLAGS, 64, d_flags);
+    const int64_t nrows_total = plan.srow.back();
+    ENSURE(B_STREAM, nrows_total + 64, d_stream);
+    int r;
+    if ((r = copy_in(c, d_blocks, plan.blocks.data(), plan.blocks.size() * sizeof(SwBlock), false))) return r;
+    if ((r = copy_in(c, d_tasks, plan.tasks.data(), plan.tasks.size() * sizeof(SwTask), false))) return r;
+    if ((r = copy_in(c, d_ids, plan.ids.data(), plan.ids.size() * sizeof(int32_t), false))) return r;
+    if ((r = copy_in(c, d_srow, plan.srow.data(), plan.srow.size() * sizeof(int64_t), false))) return r;
+    if ((r = copy_in(c, d_first, plan.first_slot.data(), plan.first_slot.size() * sizeof(int64_t), false))) return r;
+    CUDA_TRY(cudaMemsetAsync(d_flags, 0, 64 * sizeof(int32_t), st));
+    // the B subjects of all blocks form one list in the id pool after the A ids
+    const int64_t nsub = (int64_t)plan.srow.size() - 1;
+    const int64_t b_first = (int64_t)plan.ids.size() - nsub;
+    CUDA_TRY(launch_gather_stream(P.db, P.off, d_ids + b_first, (int32_t)nsub, d_srow, d_stream, st));
+    c->stats.launches += 1;
+
+    SwArgs a{};
+    a.db = P.db;
+    a.off = P.off;
+    a.blocks = d_blocks;
+    a.ids = d_ids;
+    a.streams = d_stream;
+    a.srows = d_srow;
+    a.out = out;
+    a.out_map = d_omap;
+    a.err = d_flags + 1;
+    std::memcpy(a.mat, P.mat, sizeof(a.mat));
+    a.gap_open = P.g1;
+    a.gap_extend = P.ge;
+    a.beta = P.beta;
+    a.sat_thr = (flags & CM_FORCE_INT32) ? -1 : P.sat_thr;   // -1: every pair goes to int32
+
+    // boundary buffer for multi-pass queries and for the int32 rerun
+    const int64_t stride = std::max<int64_t>(plan.max_warp_rows, P.maxlen) + 64;
+    int max_ctas = 0;
+    for (int R = 4; R <= 32; R += 4)
+        max_ctas = std::max(max_ctas, c->num_sms * std::max(1, sw16_ctas_per_sm(R, W)));
+    const int64_t nwarps = std::max<int64_t>((int64_t)max_ctas * W,
+                                             (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
+    uint2* d_bnd;
+    ENSURE(B_BND, nwarps * stride, d_bnd);
+    a.bnd = d_bnd;
+    a.bnd_stride = stride;
+
+    // one persistent launch per register-tile width R, longest tasks first within it
+    CUDA_TRY(cudaEventRecord(c->ev[0], st));
+    size_t i0 = 0;
+    int bin = 0;
+    while (i0 < plan.tasks.size()) {
+        const int R = plan.task_R[i0];
+        size_t i1 = i0;
+        while (i1 < plan.tasks.size() && plan.task_R[i1] == R) ++i1;
+        a.tasks = d_tasks + i0;
+        a.ntasks = (int32_t)(i1 - i0);
+        a.task_counter = d_flags + 8 + bin;
+        const int occ = std::max(1, sw16_ctas_per_sm(R, W));
+        const int grid = (int)std::min<int64_t>(a.ntasks, (int64_t)c->num_sms * occ);
+        CUDA_TRY(launch_sw16(R, W, grid, a, st));
+        c->stats.launches += 1;
+        c->stats.sw16_launches += 1;
+        i0 = i1;
+        ++bin;
+    }
+    CUDA_TRY(cudaEventRecord(c->ev[1], st));
+
+    // int32 rescoring of every pair the int16 pass marked as possibly saturated
+    PairRef* d_pref;
+    const int32_t cap = (int32_t)std::min<int64_t>(std::max<int64_t>(plan.nslots, 1), 1 << 20);
+    ENSURE(B_PREF, cap, d_pref);
+    for (int round = 0;; ++round) {
+        CUDA_TRY(cudaMemsetAsync(d_flags + 2, 0, 2 * sizeof(int32_t), st));
+        CUDA_TRY(launch_collect_saturated(out, plan.nslots, d_blocks, (int32_t)plan.blocks.size(),
+                                          d_first, d_ids, d_omap, d_pref, d_flags + 2, cap, st));
+        int32_t cnt = 0;
+        CUDA_TRY(cudaMemcpyAsync(&cnt, d_flags + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        c->stats.launches += 1;
+        if (cnt == 0) break;
+        const int32_t n = std::min(cnt, cap);
+        c->stats.saturated += n;
+        const int grid = (int)std::min<int64_t>(n, (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
+        CUDA_TRY(launch_sw32(16, grid, a, d_pref, n, d_flags + 3, st));
+        c->stats.launches += 1;
+        if (round > 64) return fail(c, CM_ERR_INTERNAL, "int32 rerun did not converge");
+    }
+    int32_t kerr = 0;
+    CUDA_TRY(cudaMemcpyAsync(&kerr, d_flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (kerr) return fail(c, CM_ERR_INTERNAL, "kernel bounds check fired (boundary buffer)");
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    c->stats.sw16_ms += ms;
+    c->stats.pairs += plan.pairs;
+    c->stats.cells += plan.cells;
+    c->stats.cells_padded += plan.cells_padded;
+    return CM_OK;
+}
+
+}  // namespace
+
+// =========================================================================================
+extern "C" {
+
+int cm_create(cm_ctx** out, int device)
+{
+    if (!out) return CM_ERR_ARG;
+    *out = nullptr;
+    cm_ctx* c = new (std::nothrow) cm_ctx();
+    if (!c) return CM_ERR_OOM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return CM_ERR_CUDA;
+    }
+    c->stream = c->own;
+    *out = c;
+    return CM_OK;
+}
+
+void cm_destroy(cm_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& b : c->buf)
+        if (b.p) cudaFree(b.p);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+const char* cm_last_error(const cm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int cm_set_stream(cm_ctx* c, void* s)
+{
+    if (!c) return CM_ERR_ARG;
+    c->stream = s ? reinterpret_cast<cudaStream_t>(s) : c->own;
+    return CM_OK;
+}
+
+int cm_set_tuning(cm_ctx* c, int32_t warps, int32_t rows)
+{
+    if (!c) return CM_ERR_ARG;
+    if (warps && warps != 4 && warps != 8 && warps != 16)
+        return fail(c, CM_ERR_ARG, "warps_per_cta must be 4, 8 or 16");
+    if (rows && (rows < 256 || rows > 65536))
+        return fail(c, CM_ERR_ARG, "rows_per_warp must be in [256, 65536]");
+    if (warps) c->W = warps;
+    if (rows) c->rows_per_warp = rows;
+    return CM_OK;
+}
+
+int cm_get_stats(const cm_ctx* c, cm_stats* out)
+{
+    if (!c || !out) return CM_ERR_ARG;
+    *out = c->stats;
+    return CM_OK;
+}
+
+int cm_reset_stats(cm_ctx* c)
+{
+    if (!c) return CM_ERR_ARG;
+    c->stats = cm_stats{};
+    return CM_OK;
+}
+
+int sw_score_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                   const int32_t* pairs, int64_t n_pairs, const int8_t* matrix,
+                   int32_t gap_open, int32_t gap_extend, int32_t* scores_out, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !scores_out)))
+        return fail(c, CM_ERR_ARG, "bad pairs / scores_out");
+    if (n_pairs >= (int64_t)1 << 31) return fail(c, CM_ERR_ARG, "n_pairs must be < 2^31");
+    Prepared P;
+    int r = prepare(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, flags, P);
+    if (r) return r;
+    if (n_pairs == 0) return CM_OK;
+    const bool dev = (flags & CM_DEVICE_PTRS) != 0;
+    std::vector<int32_t> hp((size_t)n_pairs * 2);
+    if (dev) CUDA_TRY(cudaMemcpy(hp.data(), pairs, hp.size() * 4, cudaMemcpyDeviceToHost));
+    else std::memcpy(hp.data(), pairs, hp.size() * 4);
+    for (int64_t k = 0; k < 2 * n_pairs; ++k)
+        if (hp[k] < 0 || hp[k] >= n_seqs) return fail(c, CM_ERR_ARG, "pair index out of range");
+
+    // group pairs by their first sequence: one CROSS block {a} x {b...} per distinct a
+    std::vector<int64_t> ord((size_t)n_pairs);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
+        return hp[2 * x] < hp[2 * y];
+    });
+    Plan plan;
+    std::vector<int32_t> a_ids, b_ids;
+    std::vector<int64_t> omap((size_t)n_pairs);
+    plan.srow.push_back(0);
+    std::vector<std::pair<int64_t, int>> keys;
+    const int64_t target = (int64_t)c->W * c->rows_per_warp;
+    int64_t slot = 0;
+    for (size_t g0 = 0; g0 < ord.size();) {
+        size_t g1 = g0;
+        const int32_t a = hp[2 * ord[g0]];
+        while (g1 < ord.size() && hp[2 * ord[g1]] == a) ++g1;
+        SwBlock B{};
+        B.kind = kCross;
+        B.swap = 0;
+        B.na = 1;
+        B.nb = (int32_t)(g1 - g0);
+        B.a_ids = (int64_t)a_ids.size();
+        B.b_ids = (int64_t)b_ids.size();       // fixed up below (after the A ids)
+        B.stream = 0;
+        B.srow = (int64_t)plan.srow.size() - 1;
+        B.out_base = slot;
+        B.k0 = 0;
+        B.has_map = 1;
+        a_ids.push_back(a);
+        const int64_t ma = P.hoff[a + 1] - P.hoff[a];
+        for (size_t g = g0; g < g1; ++g) {
+            const int32_t b = hp[2 * ord[g] + 1];
+            const int64_t mb = P.hoff[b + 1] - P.hoff[b];
+            b_ids.push_back(b);
+            plan.srow.push_back(plan.srow.back() + std::max<int64_t>(mb, 1));
+            omap[(size_t)slot++] = ord[g];
+            plan.cells += ma * mb;
+        }
+        plan.first_slot.push_back(B.out_base);
+        plan.blocks.push_back(B);
+        add_tasks(plan, (int32_t)plan.blocks.size() - 1, 0, B.nb, false, ma,
+                  plan.srow.data() + B.srow, target, keys);
+        g0 = g1;
+    }
+    for (auto& B : plan.blocks) B.b_ids += (int64_t)a_ids.size();
+    plan.ids = a_ids;
+    plan.ids.insert(plan.ids.end(), b_ids.begin(), b_ids.end());
+    plan.nslots = n_pairs;
+    plan.pairs = n_pairs;
+    order_tasks(plan, keys);
+    int64_t maxlen_rows = 0;
+    for (size_t s = 0; s + 1 < plan.srow.size(); ++s)
+        maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
+    plan.max_warp_rows = c->rows_per_warp + 2 * maxlen_rows + target / c->W;
+
+    int64_t* d_omap;
+    ENSURE(B_OMAP, n_pairs, d_omap);
+    if ((r = copy_in(c, d_omap, omap.data(), omap.size() * sizeof(int64_t), false))) return r;
+    int32_t* out = scores_out;
+    if (!dev) ENSURE(B_OUT, n_pairs, out);
+    if ((r = run_plan(c, P, plan, out, d_omap, flags))) return r;
+    if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(scores_out, out, n_pairs * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return CM_OK;
+}
+
+int sw_cells_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                   const int32_t* pairs, int64_t n_pairs, const int8_t* matrix,
+                   int32_t gap_open, int32_t gap_extend, int32_t* cells_out, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !cells_out)))
+        return fail(c, CM_ERR_ARG, "bad pairs / cells_out");
+    Prepared P;
+    int r = prepare(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, flags, P);
+    if (r) return r;
+    if (n_pairs == 0) return CM_OK;
+    const bool dev = (flags & CM_DEVICE_PTRS) != 0;
+    std::vector<int32_t> hp((size_t)n_pairs * 2);
+    if (dev) CUDA_TRY(cudaMemcpy(hp.data(), pairs, hp.size() * 4, cudaMemcpyDeviceToHost));
+    else std::memcpy(hp.data(), pairs, hp.size() * 4);
+    int64_t maxb = 0;
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        if (hp[2 * k] < 0 || hp[2 * k] >= n_seqs || hp[2 * k + 1] < 0 || hp[2 * k + 1] >= n_seqs)
+            return fail(c, CM_ERR_ARG, "pair index out of range");
+        const int32_t b = hp[2 * k + 1];
+        maxb = std::max(maxb, P.hoff[b + 1] - P.hoff[b]);
+    }
+    const int64_t cols = maxb + 1;
+    const int64_t budget = (int64_t)1 << 30;   // bytes of scratch
+    int64_t nthreads = std::min<int64_t>(n_pairs, std::max<int64_t>(1024, budget / (8 * cols)));
+    int32_t *d_pairs, *d_cells, *d_scr;
+    int16_t* d_mat;
+    ENSURE(B_PAIRS, 2 * n_pairs, d_pairs);
+    ENSURE(B_SCRATCH, 2 * nthreads * cols, d_scr);
+    ENSURE(B_MAT, 400, d_mat);
+    if ((r = copy_in(c, d_pairs, hp.data(), hp.size() * 4, false))) return r;
+    if ((r = copy_in(c, d_mat, P.mat, sizeof(P.mat), false))) return r;
+    d_cells = cells_out;
+    if (!dev) ENSURE(B_CELLS, 5 * n_pairs, d_cells);
+    CUDA_TRY(launch_cells(P.db, P.off, d_pairs, n_pairs, d_mat, P.g1, P.ge, d_cells, d_scr, cols,
+                          (int32_t)nthreads, c->stream));
+    c->stats.launches += 1;
+    if (!dev)
+        CUDA_TRY(cudaMemcpyAsync(cells_out, d_cells, 5 * n_pairs * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                const int8_t* matrix, int32_t gap_open, int32_t gap_extend, int32_t T,
+                int64_t part, int64_t n_parts, int32_t* pairs_out, int32_t* scores_out,
+                int64_t capacity, int64_t* n_found, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (!n_found || n_parts < 1 || part < 0 || part >= n_parts || capacity < 0 ||
+        (capacity > 0 && (!pairs_out || !scores_out)))
+        return fail(c, CM_ERR_ARG, "bad part / capacity / output arguments");
+    *n_found = 0;
+    Prepared P;
+    int r = prepare(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, flags, P);
+    if (r) return r;
+    if (!P.symmetric) return fail(c, CM_ERR_ARG, "sw_allpairs needs a symmetric matrix");
+    const bool dev = (flags & CM_DEVICE_PTRS) != 0;
+    CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
+    // length order (ties by index): query = the longer sequence of every pair
+    std::vector<int32_t> L((size_t)n_seqs);
+    std::iota(L.begin(), L.end(), 0);
+    std::stable_sort(L.begin(), L.end(), [&](int32_t x, int32_t y) {
+        return P.hoff[x + 1] - P.hoff[x] < P.hoff[y + 1] - P.hoff[y];
+    });
+    Plan plan;
+    plan.srow.resize((size_t)n_seqs + 1);
+    plan.srow[0] = 0;
+    for (int32_t s = 0; s < n_seqs; ++s)
+        plan.srow[s + 1] = plan.srow[s] + std::max<int64_t>(P.hoff[L[s] + 1] - P.hoff[L[s]], 1);
+    // parts: equal shares of cells, boundaries on even k
+    std::vector<double> cum((size_t)n_seqs + 1, 0.0);
+    int64_t residues = 0;
+    for (int32_t k = 0; k < n_seqs; ++k) {
+        const int64_t mk = P.hoff[L[k] + 1] - P.hoff[L[k]];
+        cum[k + 1] = cum[k] + (double)mk * (double)residues;
+        residues += mk;
+    }
+    auto kb = [&](int64_t p) -> int32_t {
+        if (p <= 0) return 0;
+        if (p >= n_parts) return n_seqs;
+        const double want = cum[n_seqs] * (double)p / (double)n_parts;
+        int32_t k = (int32_t)(std::lower_bound(cum.begin(), cum.end(), want) - cum.begin());
+        k &= ~1;
+        return std::min(k, n_seqs);
+    };
+    const int32_t k0 = kb(part), k1 = kb(part + 1);
+    SwBlock B{};
+    B.kind = kTri;
+    B.swap = 0;
+    B.na = n_seqs;
+    B.nb = n_seqs;
+    B.a_ids = 0;
+    B.b_ids = 0;
+    B.stream = 0;
+    B.srow = 0;
+    B.out_base = 0;
+    B.k0 = k0;
+    B.has_map = 0;
+    plan.blocks.push_back(B);
+    plan.first_slot.push_back(0);
+    plan.ids = L;
+    auto tri = [](int64_t k) { return k * (k - 1) / 2; };
+    plan.nslots = tri(k1) - tri(k0);
+    plan.pairs = plan.nslots;
+    std::vector<std::pair<int64_t, int>> keys;
+    const int64_t target = (int64_t)c->W * c->rows_per_warp;
+    for (int32_t k = k0; k < k1; k += 2) {
+        const bool hi = (k + 1 < k1);
+        const int32_t ns = hi ? k + 1 : k;
+        const int64_t m_hi = P.hoff[L[hi ? k + 1 : k] + 1] - P.hoff[L[hi ? k + 1 : k]];
+        if (ns > 0) add_tasks(plan, 0, k, ns, hi, m_hi, plan.srow.data(), target, keys);
+    }
+    {   // cells = sum over pairs of len(a) * len(b)
+        int64_t acc = 0, pre = 0;
+        for (int32_t k = 0; k < k1; ++k) {
+            const int64_t mk = P.hoff[L[k] + 1] - P.hoff[L[k]];
+            if (k >= k0) acc += mk * pre;
+            pre += mk;
+        }
+        plan.cells = acc;
+    }
+    order_tasks(plan, keys);
+    int64_t maxlen_rows = 1;
+    for (int32_t s = 0; s < n_seqs; ++s)
+        maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
+    plan.max_warp_rows = c->rows_per_warp + 2 * maxlen_rows + target / c->W;
+
+    int32_t* out;
+    ENSURE(B_OUT, plan.nslots, out);
+    if (!plan.tasks.empty())
+        if ((r = run_plan(c, P, plan, out, nullptr, flags))) return r;
+
+    // compaction of f > T (deterministic order: slot order)
+    const int64_t nch = compact_chunks(plan.nslots);
+    int64_t* d_chunk;
+    ENSURE(B_CHUNK, nch + 2, d_chunk);
+    int32_t* d_order;
+    ENSURE(B_IDS, plan.ids.size(), d_order);   // already uploaded by run_plan (same pool)
+    if (plan.tasks.empty())
+        if ((r = copy_in(c, d_order, L.data(), L.size() * 4, false))) return r;
+    CUDA_TRY(launch_compact_tri(out, plan.nslots, k0, d_order, T, nullptr, nullptr, d_chunk, nch,
+                                0, c->stream));
+    CUDA_TRY(launch_scan_chunks(d_chunk, nch, d_chunk + nch, c->stream));
+    int64_t total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, d_chunk + nch, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->stats.launches += 2;
+    *n_found = total;
+    if (total > capacity) return fail(c, CM_ERR_CAPACITY, "capacity too small for the significant pairs");
+    int32_t *po = pairs_out, *so = scores_out;
+    if (!dev) {
+        ENSURE(B_POUT, 2 * std::max<int64_t>(total, 1), po);
+        ENSURE(B_SOUT, std::max<int64_t>(total, 1), so);
+    }
+    CUDA_TRY(launch_compact_tri(out, plan.nslots, k0, d_order, T, po, so, d_chunk, nch, 1,
+                                c->stream));
+    c->stats.launches += 1;
+    if (!dev && total > 0) {
+        CUDA_TRY(cudaMemcpyAsync(pairs_out, po, 2 * total * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaMemcpyAsync(scores_out, so, total * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    }
+    CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+    c->stats.total_ms += ms;
+    return CM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Internal declarations shared by the libcm CUDA sources (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/cm.h"
+
+namespace cm {
+
+// ---- residue streams -------------------------------------------------------------------
+// A block's subjects are concatenated into one byte stream, one byte per DP row:
+// bits 0-4 residue code (0..19, 20 = pad row whose scores are all non-positive),
+// bit 7 = first row of a subject, bit 6 = last row of a subject.  An empty subject is one
+// pad row carrying both flags, so its score comes out 0.
+constexpr uint8_t kFirst = 0x80;
+constexpr uint8_t kLast = 0x40;
+constexpr uint8_t kPadCode = 20;
+constexpr int kProfRows = 21;          // 20 residues + pad row
+
+// ---- pair blocks -----------------------------------------------------------------------
+// A block is a set of pairs between queries A (held in registers, one column per residue)
+// and subjects B (streamed row by row).  CROSS: query k pairs with every subject s < nb.
+// TRI: A == B sorted by length; query k pairs with subjects s < k.
+enum BlockKind : int32_t { kCross = 0, kTri = 1 };
+
+struct SwBlock {
+    int32_t kind;       // BlockKind
+    int32_t swap;       // 0: cell score M[q][x] (query = pair's first); 1: M[x][q]
+    int32_t na, nb;     // |A|, |B|
+    int64_t a_ids;      // offset of A's sequence ids in the id pool
+    int64_t b_ids;      // offset of B's sequence ids in the id pool
+    int64_t stream;     // byte offset of B's row stream in the stream pool
+    int64_t srow;       // offset of B's row table (nb+1 entries) in the row pool
+    int64_t out_base;   // output slot of the block's first pair
+    int32_t k0;         // first query index covered (TRI: slot = tri(k) - tri(k0) + s)
+    int32_t has_map;    // 1: slot -> user index through out_map[]
+};
+
+// One CTA task: the query pair (k, k+1) of a block against subjects [s0, s1).
+struct SwTask {
+    int32_t block;
+    int32_t k;          // lo query index; hi = k+1 (if hi_valid)
+    int32_t s0, s1;     // subjects covered (rows split over the CTA's warps)
+    int32_t npass;      // column passes of 32*R columns
+    int32_t hi_valid;   // 0 when the lo query has no partner
+};
+
+struct SwArgs {
+    const uint8_t* db;          // residue codes of all sequences
+    const int64_t* off;         // n_seqs+1 offsets
+    const SwBlock* blocks;
+    const SwTask* tasks;
+    int32_t ntasks;
+    int32_t* task_counter;      // zeroed before launch
+    const int32_t* ids;         // id pool
+    const uint8_t* streams;     // stream pool
+    const int64_t* srows;       // row pool
+    int32_t* out;               // output slots (int32 scores, kSat = needs int32 rerun)
+    const int64_t* out_map;     // slot -> user index (blocks with has_map)
+    uint2* bnd;                 // multi-pass boundary columns, bnd_stride rows per warp
+    int64_t bnd_stride;
+    int32_t* err;               // set non-zero by a kernel's own bounds checks
+    int16_t mat[400];           // substitution matrix
+    int32_t gap_open;           // first-gap cost (already includes extend for BLAST mode)
+    int32_t gap_extend;
+    int32_t beta;               // int16 bias: stored = true + beta
+    int32_t sat_thr;            // stored best >= sat_thr -> rerun in int32
+};
+
+constexpr int32_t kSat = INT32_MIN;   // output slot marker: saturated in int16, rerun pending
+
+// One pair for the int32 rerun / cells kernels.
+struct PairRef {
+    int32_t q, x;       // query (columns) and subject (rows) sequence ids
+    int32_t swap;       // as SwBlock::swap
+    int32_t pad;
+    int64_t slot;       // output slot (final index)
+};
+
+// ---- launchers (sw16.cu) ---------------------------------------------------------------
+int sw16_smem_bytes(int R);
+cudaError_t launch_sw16(int R, int W, int grid, const SwArgs& a, cudaStream_t st);
+cudaError_t launch_sw32(int R, int grid, const SwArgs& a, const PairRef* pr, int32_t npairs,
+                        int32_t* counter, cudaStream_t st);
+int sw32_smem_bytes(int R);
+
+// ---- pack.cu ---------------------------------------------------------------------------
+cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t* bad,
+                                  cudaStream_t st);
+cudaError_t launch_check_codes(const uint8_t* in, int64_t n, int32_t* bad, cudaStream_t st);
+cudaError_t launch_gather_stream(const uint8_t* db, const int64_t* off, const int32_t* ids,
+                                 int32_t nb, const int64_t* srow, uint8_t* stream,
+                                 cudaStream_t st);
+cudaError_t launch_collect_saturated(const int32_t* out, int64_t nslots, const SwBlock* blocks,
+                                     int32_t nblocks, const int64_t* block_first_slot,
+                                     const int32_t* ids, const int64_t* out_map,
+                                     PairRef* list, int32_t* count, int32_t cap,
+                                     cudaStream_t st);
+cudaError_t launch_compact_tri(const int32_t* out, int64_t nslots, int32_t k0,
+                               const int32_t* order, int32_t T, int32_t* pairs_out,
+                               int32_t* scores_out, int64_t* chunk_counts, int64_t nchunks,
+                               int phase, cudaStream_t st);
+cudaError_t launch_scan_chunks(int64_t* counts, int64_t nchunks, int64_t* total,
+                               cudaStream_t st);
+
+// ---- cells kernel (sw_cells.cu) ----------------------------------------------------------
+cudaError_t launch_cells(const uint8_t* db, const int64_t* off, const int32_t* pairs,
+                         int64_t npairs, const int16_t* mat, int32_t g1, int32_t ge,
+                         int32_t* cells_out, int32_t* scratch, int64_t scratch_cols,
+                         int32_t nthreads, cudaStream_t st);
+
+}  // namespace cm

@@ -1,0 +1,176 @@
+"""GPU parity of the Smith-Waterman path against the CPU oracle (exact integer equality).
+
+Every test calls the CUDA path through the C ABI (ctypes binding) and the oracle on the same
+seeded inputs.  Sizes span several query tiles (R bins), multi-pass queries (> 1024 residues),
+ragged tails, empty and 1-residue sequences, int16 saturation (int32 rerun), both gap
+conventions and an asymmetric matrix.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1908_10574_gb300 as cm
+from paper_1908_10574_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+S62 = synth.BLOSUM62
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return cm.Context(0)
+
+
+def _lognormal_set(n, stream, hi=5000):
+    rng = np.random.default_rng(stream)
+    lens = synth.lognormal_lengths(rng, n, hi=hi)
+    return synth.SeqSet.from_list([synth.random_seq(rng, int(L)) for L in lens])
+
+
+def test_small_allpairs_scores_exact(ctx):
+    ss = synth.small_families()
+    pairs = oracle.triangle_pairs(len(ss))
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got, want)
+
+
+def test_random_pairs_lognormal_exact(ctx):
+    ss = _lognormal_set(600, 1)
+    pairs = synth.random_pairs(len(ss), 4000, stream=5)
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got, want)
+
+
+def test_long_queries_multipass_and_ragged(ctx):
+    rng = np.random.default_rng(2)
+    lens = [1, 2, 31, 32, 33, 127, 128, 129, 1023, 1024, 1025, 1100, 2049, 3000, 4999]
+    seqs = [synth.random_seq(rng, L) for L in lens]
+    # homologous partners so scores are large and alignments long
+    seqs += [synth.mutate(rng, s) for s in seqs]
+    ss = synth.SeqSet.from_list(seqs)
+    n = len(ss)
+    pairs = np.array([(i, j) for i in range(n) for j in range(n)], dtype=np.int32)
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got, want)
+
+
+def test_empty_sequences(ctx):
+    rng = np.random.default_rng(3)
+    seqs = [np.zeros(0, np.uint8), synth.random_seq(rng, 50), np.zeros(0, np.uint8),
+            synth.random_seq(rng, 1)]
+    ss = synth.SeqSet.from_list(seqs)
+    pairs = np.array([(i, j) for i in range(4) for j in range(4)], dtype=np.int32)
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got, want)
+    assert len(ctx.sw_score_batch(ss.seqs, ss.offsets, np.zeros((0, 2), np.int32), S62, 11, 1)) == 0
+
+
+def test_int16_saturation_rerun_exact(ctx):
+    rng = np.random.default_rng(4)
+    w = synth.encode("W" * 3100)                      # self score 34100 > int16
+    motif = synth.tandem_repeat(rng, 6000)             # self-similar, large scores
+    seqs = [w, w[:2900], motif, synth.mutate(rng, motif), synth.random_seq(rng, 300)]
+    ss = synth.SeqSet.from_list(seqs)
+    pairs = np.array([(i, j) for i in range(5) for j in range(5)], dtype=np.int32)
+    ctx.reset_stats()
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert want.max() > 32767
+    assert np.array_equal(got, want)
+    assert ctx.stats()["saturated"] > 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gap_conventions_and_asymmetric_matrix(ctx, mode):
+    rng = np.random.default_rng(10 + mode)
+    S = rng.integers(-5, 9, size=(20, 20)).astype(np.int8)
+    ss = _lognormal_set(120, 20 + mode, hi=1500)
+    pairs = synth.random_pairs(len(ss), 800, stream=7 + mode)
+    flags = cm.CM_GAP_BLAST if mode else 0
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S, 7, 2, flags=flags)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S, 7, 2, gap_mode=mode)
+    assert np.array_equal(got, want)
+
+
+def test_force_int32_path_exact(ctx):
+    ss = _lognormal_set(200, 30, hi=2500)
+    pairs = synth.random_pairs(len(ss), 600, stream=9)
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1, flags=cm.CM_FORCE_INT32)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got, want)
+
+
+def test_device_pointer_path(ctx):
+    import torch
+    ss = synth.small_families()
+    pairs = oracle.triangle_pairs(len(ss))[::7].copy()
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    got = ctx.sw_score_batch(d(ss.seqs), d(ss.offsets), d(pairs), d(S62.reshape(-1)), 11, 1)
+    torch.cuda.synchronize()
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_allpairs_significant_set(ctx):
+    ss = synth.small_families()
+    truth, scores = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=60)
+    p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, T=60)
+    got = sorted(zip(p[:, 0].tolist(), p[:, 1].tolist(), s.tolist()))
+    assert got == sorted(map(tuple, truth.tolist()))
+    # every pair significant at T = -1, scores exact
+    p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, T=-1, capacity=1 << 15)
+    n = len(ss)
+    assert len(p) == n * (n - 1) // 2
+    M = np.zeros((n, n), np.int64)
+    M[np.triu_indices(n, 1)] = scores
+    assert np.array_equal(s, M[p[:, 0], p[:, 1]])
+
+
+def test_allpairs_parts_union(ctx):
+    ss = _lognormal_set(300, 40, hi=3000)
+    truth, _ = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=35)
+    got = []
+    for part in range(5):
+        p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, T=35, part=part, n_parts=5)
+        got += list(zip(p[:, 0].tolist(), p[:, 1].tolist(), s.tolist()))
+    assert sorted(got) == sorted(map(tuple, truth.tolist()))
+
+
+def test_cells_match_oracle(ctx):
+    ss = synth.small_families()
+    rng = np.random.default_rng(12)
+    pairs = synth.random_pairs(len(ss), 300, stream=12)
+    fam = ss.family
+    same = np.nonzero(fam[:, None] == fam[None, :])
+    pick = rng.choice(len(same[0]), 200, replace=False)
+    pairs = np.concatenate([pairs, np.stack([same[0][pick], same[1][pick]], 1)]).astype(np.int32)
+    got = ctx.sw_cells_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    for k, (a, b) in enumerate(pairs):
+        assert tuple(got[k]) == oracle.sw_cells(ss[a], ss[b], S62, 11, 1), (k, a, b)
+
+
+def test_invalid_residue_and_arguments(ctx):
+    ss = synth.small_families()
+    bad = ss.seqs.copy()
+    bad[5] = 25
+    with pytest.raises(cm.CMError) as ei:
+        ctx.sw_score_batch(bad, ss.offsets, np.array([[0, 1]], np.int32), S62, 11, 1)
+    assert ei.value.code == -2
+    with pytest.raises(cm.CMError) as ei:
+        ctx.sw_score_batch(ss.seqs, ss.offsets, np.array([[0, 999]], np.int32), S62, 11, 1)
+    assert ei.value.code == -1
+    with pytest.raises(cm.CMError):
+        ctx.sw_score_batch(ss.seqs, ss.offsets, np.array([[0, 1]], np.int32), S62, 0, 1)
+
+
+def test_ascii_input(ctx):
+    txt = ["HEAGAWGHEE", "PAWHEAE", "mkwvtfisll"]
+    seqs = np.frombuffer("".join(txt).encode(), np.uint8)
+    off = np.cumsum([0] + [len(t) for t in txt]).astype(np.int64)
+    got = ctx.sw_score_batch(seqs, off, np.array([[0, 1], [2, 2]], np.int32), S62, 11, 1,
+                             flags=cm.CM_ASCII)
+    assert got.tolist() == [17, 52]
