@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark: Smith-Waterman GCUPS (bit-exact) on the all-against-all of 20,000 synthetic
+proteins (lognormal lengths, median 350, sigma 0.6, clipped 30-5000; 2,000 planted families of
+10; BLOSUM62, gap open 11 / extend 1; significant pairs f > T = 60).
+
+A step is one part (1/16 of the cells) of the all-against-all triangle through sw_allpairs:
+packing, the int16x2 DPX kernel, the int32 rerun of saturated pairs and threshold compaction.
+`value` times steps on device-resident inputs (CUDA events on the library's stream, L2 flushed
+between steps); `e2e` times the same steps through the C ABI with pinned host buffers (the
+sequences go host->device and the significant pairs device->host inside every step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank scores its own parts (weak scaling, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1908_10574_gb300 import synth  # noqa: E402
+
+METRIC = "SW GCUPS (bit-exact)"
+N_SEQS = 20000
+FAMILY = 10
+T_SIG = 60
+GAP_OPEN, GAP_EXT = 11, 1
+PARTS_PER_GPU = 16
+CELLS_PER_CLK_PER_SM = 64.0 * 2.0 / 4.5   # half-rate DPX/ALU pipe, 2 cells / 4.5 ops
+
+
+def workload_desc(n_parts):
+    return ("all-against-all Smith-Waterman of %d synthetic proteins (lognormal lengths median "
+            "350 sigma 0.6 clipped 30-5000, %d planted families of %d, 30%% substitution + 5%% "
+            "indel members), BLOSUM62 gap 11/1, significant pairs f > %d; one step = 1/%d of "
+            "the triangle's cells" % (N_SEQS, N_SEQS // FAMILY, FAMILY, T_SIG, n_parts))
+
+
+def make_set():
+    return synth.proteome(N_SEQS, FAMILY)
+
+
+def total_cells(ss):
+    L = ss.lengths.astype(np.float64)
+    return int((L.sum() ** 2 - (L ** 2).sum()) / 2)
+
+
+def part_sequence(n_parts, count, offset=0):
+    return [((3 + 5 * (i + offset)) % n_parts) for i in range(count)]
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(ss, target_s=10.0):
+    """The oracle as it stands (scalar Gotoh in C, all host cores) on a bounded random sample
+    of the same workload's pairs."""
+    import oracle
+    rng = np.random.default_rng(77)
+    n = len(ss)
+    cores = os.cpu_count() or 1
+    L = ss.lengths.astype(np.int64)
+
+    def sample(k):
+        i = rng.integers(0, n, size=k)
+        j = rng.integers(0, n - 1, size=k)
+        j = np.where(j >= i, j + 1, j)
+        return np.stack([np.minimum(i, j), np.maximum(i, j)], 1).astype(np.int32)
+
+    p = sample(2000)
+    t0 = time.perf_counter()
+    oracle.sw_batch(ss.seqs, ss.offsets, p, synth.BLOSUM62, GAP_OPEN, GAP_EXT, threads=cores)
+    dt = time.perf_counter() - t0
+    rate = (L[p[:, 0]] * L[p[:, 1]]).sum() / max(dt, 1e-6)
+    k = int(min(max(2000, target_s * rate / (L.mean() ** 2)), 2_000_000))
+    p = sample(k)
+    cells = int((L[p[:, 0]] * L[p[:, 1]]).sum())
+    t0 = time.perf_counter()
+    oracle.sw_batch(ss.seqs, ss.offsets, p, synth.BLOSUM62, GAP_OPEN, GAP_EXT, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d uniformly random pairs of the all-against-all (%.3g cells), scalar "
+                      "int64 Gotoh on %d POSIX threads, %.1f s" % (k, cells, cores, dt)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    ss = make_set()
+    import oracle
+    cores = os.cpu_count() or 1
+    L = ss.lengths.astype(np.int64)
+    rng = np.random.default_rng(5)
+    n = len(ss)
+    per_step = 4000     # pairs per step: a bounded sample of the workload (~seconds of CPU)
+    cells_t, time_t = 0, 0.0
+    for step in range(args.warmup + args.steps):
+        i = rng.integers(0, n, size=per_step)
+        j = rng.integers(0, n - 1, size=per_step)
+        j = np.where(j >= i, j + 1, j)
+        p = np.stack([np.minimum(i, j), np.maximum(i, j)], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.sw_batch(ss.seqs, ss.offsets, p, synth.BLOSUM62, GAP_OPEN, GAP_EXT, threads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            cells_t += int((L[p[:, 0]] * L[p[:, 1]]).sum())
+            time_t += dt
+    v = cells_t / time_t / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": time_t * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": workload_desc(PARTS_PER_GPU), "n_seqs": N_SEQS},
+           "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                            "sample": "%d uniformly random pairs per step of the same "
+                                      "all-against-all, scalar int64 Gotoh on %d threads"
+                                      % (per_step, cores)},
+           "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=0)
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import paper_1908_10574_gb300 as cm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = cm.Context(local)
+    if args.warps or args.rows:
+        ctx.set_tuning(args.warps, args.rows)
+    ss = make_set()
+    n_parts = PARTS_PER_GPU * world
+    seq = part_sequence(n_parts, (args.warmup + args.steps) * world)
+    my_parts = seq[rank::world]
+    d_seqs = torch.from_numpy(ss.seqs).to(dev)
+    d_off = torch.from_numpy(ss.offsets).to(dev)
+    d_mat = torch.from_numpy(synth.BLOSUM62.reshape(-1).copy()).to(dev)
+    cap = 1 << 21
+    d_pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    d_scores = torch.empty(cap, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(part):
+        return ctx.sw_allpairs(d_seqs, d_off, d_mat, GAP_OPEN, GAP_EXT, T_SIG, part, n_parts,
+                               capacity=cap, pairs_out=d_pairs, scores_out=d_scores)
+
+    for i in range(args.warmup):
+        step(my_parts[i])
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ms_total = 0.0
+    found = 0
+    for i in range(args.steps):
+        flush.zero_()                                  # L2 flush between timed steps
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p, s = step(my_parts[args.warmup + i])
+        e1.record()
+        e1.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        found += len(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    st = ctx.stats()
+    ms_max = max_over_ranks(world, ms_total, dev)
+    cells_all = sum_over_ranks(world, float(st["cells"]), dev)
+    value = cells_all / (ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (int16x2 DPX Smith-Waterman), from the library's own
+    # CUDA events around its launches on this stream
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    clk_mhz = clocks["sm_mhz"] if clocks else None
+    achieved = st["cells"] / (st["sw16_ms"] * 1e-3) / 1e9 if st["sw16_ms"] > 0 else None
+    peak = n_sm * (clk_mhz * 1e6) * CELLS_PER_CLK_PER_SM / 1e9 if clk_mhz else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "kernel": "sw16_kernel (int16x2 DPX wavefront)",
+            "peak_basis": "%d SMs x median SM clock under load x 64 DPX/ALU-pipe lane-ops per "
+                          "clk per SM x 2 cells per 4.5 ops (derived, see DESIGN.md)" % n_sm,
+            "sw16_ms_per_launch": st["sw16_ms"] / max(st["sw16_launches"], 1),
+            "cells_per_launch": st["cells"] / max(st["sw16_launches"], 1),
+            "padded_cell_fraction": (st["cells"] / st["cells_padded"]) if st["cells_padded"] else None}
+
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        h_seqs, h_off, h_mat = pin(ss.seqs), pin(ss.offsets), pin(synth.BLOSUM62.reshape(-1).copy())
+        h_pairs = pin(np.empty((cap, 2), np.int32))
+        h_scores = pin(np.empty(cap, np.int32))
+        ctx.reset_stats()
+        barrier(world)
+        t0 = time.perf_counter()
+        nf = 0
+        for i in range(args.steps):
+            p, s = ctx.sw_allpairs(h_seqs, h_off, h_mat, GAP_OPEN, GAP_EXT, T_SIG,
+                                   my_parts[args.warmup + i], n_parts, capacity=cap,
+                                   pairs_out=h_pairs, scores_out=h_scores)
+            nf += len(s)
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(world, dt, dev)
+        cells_e = sum_over_ranks(world, float(ctx.stats()["cells"]), dev)
+        e2e = {"value": cells_e / dt / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": int(ss.seqs.nbytes + ss.offsets.nbytes + 400),
+               "d2h_bytes_per_step": int(nf * 12 / args.steps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ss)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "int16", "data": "synthetic",
+               "config": {"workload": workload_desc(n_parts), "n_seqs": N_SEQS,
+                          "families": N_SEQS // FAMILY, "cells_all_pairs": total_cells(ss),
+                          "cells_timed": int(cells_all), "significant_pairs_timed": found,
+                          "parts_timed": my_parts[args.warmup:], "n_parts": n_parts,
+                          "l2": "flushed between timed steps (256 MiB write)",
+                          "tuning": {"warps_per_cta": args.warps or 8,
+                                     "rows_per_warp": args.rows or 4096}},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": int(st["launches"]), "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,35 +146,24 @@ def _mutate_fast(rng, root, sub_rate=0.30, indel_rate=0.05):
     ins = rng.random(n) < 0.5
     sub = rng.random(n) < sub_rate
     base = root.copy()
-    if sub.any():
-        # different residue: draw from background conditioned on != original
-        cand = random_seq(rng, int(sub.sum()) * 2 + 8)
-        k = 0
-        idx = np.nonzero(sub)[0]
-        for pos in idx:
-            while cand[k] == base[pos]:
-                k += 1
-                if k >= len(cand):
-                    cand = random_seq(rng, len(idx) * 2 + 8)
-                    k = 0
-            base[pos] = cand[k]
-            k += 1
-    keep = ~(ev & ~ins)
-    insert_here = ev & ins
-    parts = []
-    ins_res = random_seq(rng, int(insert_here.sum()) + 1)
-    j = 0
-    out = np.empty(n + int(insert_here.sum()), dtype=np.uint8)
-    o = 0
-    for pos in range(n):
-        if insert_here[pos]:
-            out[o] = ins_res[j]; j += 1; o += 1
-        if keep[pos]:
-            out[o] = base[pos]; o += 1
-    out = out[:o]
-    if o == 0:
+    idx = np.nonzero(sub)[0]
+    if len(idx):
+        # substitute to a different residue drawn from the background
+        cand = random_seq(rng, len(idx))
+        same = cand == base[idx]
+        while same.any():
+            cand[same] = random_seq(rng, int(same.sum()))
+            same = cand == base[idx]
+        base[idx] = cand
+    keep = ~(ev & ~ins)            # deletion events drop the residue
+    insert_here = ev & ins         # insertion events add a residue before it
+    counts = insert_here.astype(np.int64) + keep
+    start = np.cumsum(counts) - counts
+    out = np.empty(int(counts.sum()), dtype=np.uint8)
+    out[start[insert_here]] = random_seq(rng, int(insert_here.sum()))
+    out[start[keep] + insert_here[keep]] = base[keep]
+    if len(out) == 0:
         out = root[:1].copy()
-    del parts
     return out
 
 
