@@ -128,6 +128,28 @@ int sw_allpairs(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_
                 int64_t part, int64_t n_parts, int32_t *pairs_out, int32_t *scores_out,
                 int64_t capacity, int64_t *n_found, uint32_t flags);
 
+/* sw_cells_batch_noalloc -- the same results as sw_cells_batch, for callers that cannot
+ * allocate device memory when they call (for example a service whose GPU memory is reserved
+ * up front by another framework's caching allocator, or a latency-bound loop that must avoid
+ * the device synchronisation cudaMalloc/cudaFree can cause).  The paper has no counterpart:
+ * this is a deployment variant of the alignment-cells pass.
+ *   seqs, offsets, pairs, cells_out: DEVICE pointers on the current CUDA device (no context);
+ *   matrix: HOST pointer (400 int8, as above); cuda_stream: the stream to run on (NULL = the
+ *   legacy default stream); flags: 0 or CM_GAP_BLAST; err_msg/err_len: optional caller buffer
+ *   that receives a message on error (may be NULL).
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the per-pair DP rows use one
+ * fixed 32 MiB array compiled into the library, which every GPU that loads the library keeps
+ * until the process exits.  Limit: the second sequence of every pair must have at most 4095
+ * residues; larger pairs are rejected with CM_ERR_ARG before anything is written.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls share the array: calls whose work overlaps
+ * on the GPU (other streams or threads) race and must be serialised by the caller.  The call
+ * returns after the results are written. */
+int sw_cells_batch_noalloc(const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                           const int32_t *pairs, int64_t n_pairs, const int8_t *matrix,
+                           int32_t gap_open, int32_t gap_extend, int32_t *cells_out,
+                           void *cuda_stream, uint32_t flags, char *err_msg, int32_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ from . import _lib as _L
 from ._lib import CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS  # noqa: F401
 
 __all__ = ["Context", "sw_score_batch", "sw_cells_batch", "sw_allpairs", "CMError",
-           "default_context"]
+           "default_context", "sw_cells_batch_noalloc"]
 
 
 def _is_torch_cuda(x):
@@ -199,3 +199,20 @@ def sw_allpairs(seqs, offsets, matrix, gap_open, gap_extend, T, part=0, n_parts=
                 capacity=None):
     return default_context().sw_allpairs(seqs, offsets, matrix, gap_open, gap_extend, T, part,
                                          n_parts, flags, capacity)
+
+
+def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, cells_out,
+                           flags=0):
+    """Allocation-free alignment cells (see include/cm.h): every array except `matrix` is a
+    torch CUDA tensor on the current device, `cells_out` is a caller-allocated (n, 5) int32
+    CUDA tensor, and the current torch stream is used.  Nothing is allocated by the call."""
+    import torch
+    m = np.ascontiguousarray(np.asarray(matrix), dtype=np.int8).reshape(400)
+    buf = ctypes.create_string_buffer(256)
+    code = _L.lib().sw_cells_batch_noalloc(
+        _ptr(seqs), _ptr(offsets), int(offsets.shape[0]) - 1, _ptr(pairs), int(pairs.shape[0]),
+        ctypes.c_void_p(m.ctypes.data), int(gap_open), int(gap_extend), _ptr(cells_out),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), int(flags), buf, 256)
+    if code != 0:
+        raise CMError(code, buf.value.decode(errors="replace"))
+    return cells_out

@@ -57,6 +57,8 @@ def lib():
         "sw_cells_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
         "sw_allpairs": (ctypes.c_int, [p, p, p, i32, p, i32, i32, i32, i64, i64, p, p, i64,
                                        ctypes.POINTER(i64), u32]),
+        "sw_cells_batch_noalloc": (ctypes.c_int, [p, p, i32, p, i64, p, i32, i32, p, p, u32,
+                                                  ctypes.c_char_p, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
