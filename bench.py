@@ -223,6 +223,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--parts-per-gpu", type=int, default=PARTS_PER_GPU,
+                    help="split of the triangle; a larger value gives shorter steps (profiling)")
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -240,7 +242,7 @@ def main():
     if args.warps or args.rows:
         ctx.set_tuning(args.warps, args.rows)
     ss = make_set()
-    n_parts = PARTS_PER_GPU * world
+    n_parts = args.parts_per_gpu * world
     seq = part_sequence(n_parts, (args.warmup + args.steps) * world)
     my_parts = seq[rank::world]
     d_seqs = torch.from_numpy(ss.seqs).to(dev)
@@ -259,6 +261,8 @@ def main():
         step(my_parts[i])
     torch.cuda.synchronize()
     ctx.reset_stats()
+    if args.steps < 1:
+        return
     clk = ClockSampler(local)
     clk.start()
     barrier(world)
