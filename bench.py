@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: Smith-Waterman GCUPS (bit-exact) on the all-against-all of 20,000 synthetic
 proteins (lognormal lengths, median 350, sigma 0.6, clipped 30-5000; 2,000 planted families of
-10; BLOSUM62, gap open 11 / extend 1; significant pairs f > T = 60).
+10; BLOSUM62, gap open 11 / extend 1; significant pairs f > T = 80).
 
 A step is one part (1/16 of the cells) of the all-against-all triangle through sw_allpairs:
 packing, the int16x2 DPX kernel, the int32 rerun of saturated pairs and threshold compaction.
@@ -34,7 +34,7 @@ from paper_1908_10574_gb300 import synth  # noqa: E402
 METRIC = "SW GCUPS (bit-exact)"
 N_SEQS = 20000
 FAMILY = 10
-T_SIG = 60
+T_SIG = 80
 GAP_OPEN, GAP_EXT = 11, 1
 PARTS_PER_GPU = 16
 CELLS_PER_CLK_PER_SM = 64.0 * 2.0 / 4.5   # half-rate DPX/ALU pipe, 2 cells / 4.5 ops

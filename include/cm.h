@@ -128,6 +128,42 @@ int sw_allpairs(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_
                 int64_t part, int64_t n_parts, int32_t *pairs_out, int32_t *scores_out,
                 int64_t capacity, int64_t *n_found, uint32_t flags);
 
+/* ---- ClusterMerge (Algorithm 1 Merge, Algorithm 2 BottomUpMerge, Sec. 4 transitivity) ---- */
+typedef struct {
+    int32_t T;      /* significance: a pair is similar when its score > T (Sec. 3) */
+    int32_t mT;     /* full-merge threshold: representatives' score > mT (Sec. 4) */
+    int32_t mU;     /* full merge needs fewer than mU uncovered residues in the absorbed rep */
+    int32_t reserved[5];   /* must be 0 */
+} cm_params;
+
+typedef struct {
+    int32_t n_seqs;
+    int32_t n_clusters;
+    int32_t *reps;             /* n_clusters representatives (final set order) */
+    int64_t *cl_offsets;       /* n_clusters+1 offsets into members */
+    int32_t *members;          /* members of every cluster, insertion order, rep first */
+    int64_t n_pairs;           /* similar pairs found: i < j, score > T, sorted by (i, j) */
+    int32_t *pairs;            /* 2*n_pairs */
+    int32_t *scores;           /* n_pairs */
+    int64_t rep_comparisons;       /* representative comparisons of Algorithm 1 */
+    int64_t exchange_comparisons;  /* member-vs-representative comparisons of ExchangeSimilar */
+    int64_t intra_comparisons;     /* distinct intra-cluster pairs aligned (Sec. 6.1) */
+    int64_t comparisons_scored;    /* alignments run on the GPU (speculation and duplicates incl.) */
+    int64_t cells_pairs;           /* alignments re-run for their cells (candidate full merges) */
+    int64_t full_merges, exchanges, merges, rounds, gpu_batches, exchange_waves;
+    double seconds;                /* wall time of the call */
+} cm_result;
+
+/* cluster_merge -- precise clustering of a protein set (Sec. 3-4) followed by the
+ * intra-cluster all-against-all (Sec. 6.1).  Deterministic: clusters, member order, similar
+ * pairs and the three logical comparison counts equal those of the plain sequential
+ * Algorithms 1 and 2 (FIFO in input order).  The matrix must be symmetric.  *out is owned by
+ * the library; release it with cm_result_free. */
+int cluster_merge(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                  const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                  const cm_params *params, cm_result **out, uint32_t flags);
+void cm_result_free(cm_result *result);
+
 /* sw_cells_batch_noalloc -- the same results as sw_cells_batch, for callers that cannot
  * allocate device memory when they call (for example a service whose GPU memory is reserved
  * up front by another framework's caching allocator, or a latency-bound loop that must avoid

@@ -16,7 +16,7 @@ from . import _lib as _L
 from ._lib import CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS  # noqa: F401
 
 __all__ = ["Context", "sw_score_batch", "sw_cells_batch", "sw_allpairs", "CMError",
-           "default_context", "sw_cells_batch_noalloc"]
+           "default_context", "sw_cells_batch_noalloc", "cluster_merge"]
 
 
 def _is_torch_cuda(x):
@@ -176,6 +176,38 @@ class Context:
         raise CMError(_L.CM_ERR_CAPACITY, "capacity retry failed")
 
 
+    def cluster_merge(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0):
+        """ClusterMerge (Algorithms 1 and 2 with the Sec. 4 transitivity test) plus the
+        intra-cluster all-against-all.  Returns a dict: clusters [(rep, [members])], pairs
+        (k, 3) int64 (i, j, score) sorted, and the comparison counters."""
+        seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
+        flags |= self._prep([seqs, offsets, matrix])
+        n = int(offsets.shape[0]) - 1
+        prm = _L.cm_params(int(T), int(mT), int(mU))
+        res = ctypes.POINTER(_L.cm_result)()
+        _L.check(self._h, _L.lib().cluster_merge(self._h, _ptr(seqs), _ptr(offsets), n,
+                                                 _ptr(matrix), int(gap_open), int(gap_extend),
+                                                 ctypes.byref(prm), ctypes.byref(res), flags))
+        try:
+            R = res.contents
+            nc = R.n_clusters
+            off = np.ctypeslib.as_array(R.cl_offsets, shape=(nc + 1,)).copy()
+            mem = (np.ctypeslib.as_array(R.members, shape=(int(off[-1]),)).copy()
+                   if off[-1] > 0 else np.zeros(0, np.int32))
+            reps = np.ctypeslib.as_array(R.reps, shape=(nc,)).copy() if nc else np.zeros(0, np.int32)
+            k = int(R.n_pairs)
+            pairs = np.zeros((k, 3), dtype=np.int64)
+            if k:
+                pairs[:, :2] = np.ctypeslib.as_array(R.pairs, shape=(k, 2))
+                pairs[:, 2] = np.ctypeslib.as_array(R.scores, shape=(k,))
+            stats = {f: getattr(R, f) for f, _ in R._fields_
+                     if f not in ("reps", "cl_offsets", "members", "pairs", "scores")}
+        finally:
+            _L.lib().cm_result_free(res)
+        clusters = [(int(reps[i]), mem[off[i]:off[i + 1]].tolist()) for i in range(nc)]
+        return {"clusters": clusters, "pairs": pairs, "stats": stats}
+
+
 _default = {}
 
 
@@ -216,3 +248,8 @@ def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, c
     if code != 0:
         raise CMError(code, buf.value.decode(errors="replace"))
     return cells_out
+
+
+def cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0):
+    return default_context().cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT,
+                                           mU, flags)

@@ -33,6 +33,27 @@ class cm_stats(ctypes.Structure):
                 ("sw16_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
+class cm_params(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("mT", ctypes.c_int32), ("mU", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class cm_result(ctypes.Structure):
+    _fields_ = [("n_seqs", ctypes.c_int32), ("n_clusters", ctypes.c_int32),
+                ("reps", ctypes.POINTER(ctypes.c_int32)),
+                ("cl_offsets", ctypes.POINTER(ctypes.c_int64)),
+                ("members", ctypes.POINTER(ctypes.c_int32)),
+                ("n_pairs", ctypes.c_int64),
+                ("pairs", ctypes.POINTER(ctypes.c_int32)),
+                ("scores", ctypes.POINTER(ctypes.c_int32)),
+                ("rep_comparisons", ctypes.c_int64), ("exchange_comparisons", ctypes.c_int64),
+                ("intra_comparisons", ctypes.c_int64), ("comparisons_scored", ctypes.c_int64),
+                ("cells_pairs", ctypes.c_int64), ("full_merges", ctypes.c_int64),
+                ("exchanges", ctypes.c_int64), ("merges", ctypes.c_int64),
+                ("rounds", ctypes.c_int64), ("gpu_batches", ctypes.c_int64),
+                ("exchange_waves", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -57,6 +78,9 @@ def lib():
         "sw_cells_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
         "sw_allpairs": (ctypes.c_int, [p, p, p, i32, p, i32, i32, i32, i64, i64, p, p, i64,
                                        ctypes.POINTER(i64), u32]),
+        "cluster_merge": (ctypes.c_int, [p, p, p, i32, p, i32, i32, ctypes.POINTER(cm_params),
+                                         ctypes.POINTER(ctypes.POINTER(cm_result)), u32]),
+        "cm_result_free": (None, [ctypes.POINTER(cm_result)]),
         "sw_cells_batch_noalloc": (ctypes.c_int, [p, p, i32, p, i64, p, i32, i32, p, p, u32,
                                                   ctypes.c_char_p, i32]),
     }

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "cm_internal.h"
+#include "ctx.h"
 
 namespace cm {
 int64_t compact_chunks(int64_t nslots);
@@ -18,35 +18,7 @@ int sw32_ctas_per_sm();
 
 using namespace cm;
 
-namespace {
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-};
-
-enum BufId {
-    B_DB, B_RAW, B_OFF, B_BLOCKS, B_TASKS, B_IDS, B_STREAM, B_SROW, B_OUT, B_OMAP, B_BND,
-    B_FLAGS, B_PREF, B_FIRST, B_PAIRS, B_CELLS, B_SCRATCH, B_CHUNK, B_POUT, B_SOUT, B_MAT,
-    B_COUNT
-};
-
-}  // namespace
-
-struct cm_ctx {
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t own = nullptr;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    cm_stats stats{};
-    int W = 8;
-    int rows_per_warp = 4096;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    DevBuf buf[B_COUNT];
-};
-
-namespace {
+namespace cm {
 
 int fail(cm_ctx* c, int code, const std::string& msg)
 {
@@ -54,19 +26,10 @@ int fail(cm_ctx* c, int code, const std::string& msg)
     return code;
 }
 
-#define CUDA_TRY(call)                                                                      \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess)                                                              \
-            return fail(c, e_ == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA,      \
-                        std::string(#call " failed: ") + cudaGetErrorString(e_));           \
-    } while (0)
-
-template <class T>
-int ensure(cm_ctx* c, BufId id, size_t count, T** out)
+int ensure_bytes(cm_ctx* c, BufId id, size_t bytes_in, void** out)
 {
     DevBuf& b = c->buf[id];
-    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    const size_t bytes = std::max<size_t>(bytes_in, 16);
     if (bytes > b.cap) {
         if (b.p) {
             cudaStreamSynchronize(c->stream);
@@ -78,31 +41,15 @@ int ensure(cm_ctx* c, BufId id, size_t count, T** out)
         cudaError_t e = cudaMalloc(&b.p, want);
         if (e != cudaSuccess) {
             cudaGetLastError();
+            b.p = nullptr;
             return fail(c, CM_ERR_OOM, "device allocation of " + std::to_string(want) +
                                            " bytes failed: " + cudaGetErrorString(e));
         }
         b.cap = want;
     }
-    *out = reinterpret_cast<T*>(b.p);
+    *out = b.p;
     return CM_OK;
 }
-
-#define ENSURE(id, n, ptr)                                                                  \
-    do {                                                                                    \
-        int r_ = ensure(c, id, (size_t)(n), &(ptr));                                        \
-        if (r_) return r_;                                                                  \
-    } while (0)
-
-struct Prepared {
-    const uint8_t* db = nullptr;     // device residue codes
-    const int64_t* off = nullptr;    // device offsets
-    std::vector<int64_t> hoff;       // host offsets
-    int16_t mat[400];
-    int32_t g1 = 0, ge = 0;          // first-gap cost, extension cost
-    int32_t beta = 0, sat_thr = 0;
-    bool symmetric = true;
-    int64_t maxlen = 0;
-};
 
 int copy_in(cm_ctx* c, void* dst, const void* src, size_t bytes, bool dev)
 {
@@ -201,18 +148,6 @@ int prepare(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_se
 }
 
 // ---- planning ---------------------------------------------------------------------------
-struct Plan {
-    std::vector<SwBlock> blocks;
-    std::vector<int64_t> first_slot;     // per block, ascending
-    std::vector<int32_t> ids;            // A ids then B ids
-    std::vector<int64_t> srow;           // global row table over all B subjects (+1)
-    std::vector<SwTask> tasks;           // grouped by R, cost descending inside a group
-    std::vector<int> task_R;             // R per task (parallel to tasks)
-    int64_t nslots = 0;
-    int64_t cells = 0, cells_padded = 0, pairs = 0;
-    int64_t max_warp_rows = 0;
-};
-
 void choose_R(int64_t m, int* R, int* npass)
 {
     if (m <= 0) { *R = 4; *npass = 1; return; }
@@ -227,7 +162,7 @@ void choose_R(int64_t m, int* R, int* npass)
 
 // Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows.
 void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
-               const int64_t* srow, int64_t target, std::vector<std::pair<int64_t, int>>& keys)
+               const int64_t* srow, int64_t target)
 {
     int R, np;
     choose_R(m_hi, &R, &np);
@@ -247,13 +182,14 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
         P.cells_padded += rows * 32 * R * np * 2;
         P.tasks.push_back(t);
         P.task_R.push_back(R);
-        keys.push_back({rows * R * np, R});
+        P.keys.push_back({rows * R * np, R});
         s = e;
     }
 }
 
-void order_tasks(Plan& P, const std::vector<std::pair<int64_t, int>>& keys)
+void order_tasks(Plan& P)
 {
+    const auto& keys = P.keys;
     std::vector<size_t> idx(P.tasks.size());
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
@@ -379,7 +315,119 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     return CM_OK;
 }
 
-}  // namespace
+int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
+                 const std::vector<BlockReq>& req, std::vector<int32_t>& scores,
+                 std::vector<int64_t>& base, uint32_t flags)
+{
+    Plan plan;
+    base.assign(req.size() + 1, 0);
+    int64_t slots = 0;
+    std::vector<int32_t> a_ids, b_ids;
+    plan.srow.push_back(0);
+    const int64_t target = (int64_t)c->W * c->rows_per_warp;
+    for (size_t bi = 0; bi < req.size(); ++bi) {
+        const BlockReq& r = req[bi];
+        base[bi] = slots;
+        SwBlock B{};
+        B.kind = r.kind;
+        B.swap = r.swap;
+        B.na = (int32_t)r.a_count;
+        B.nb = (int32_t)r.b_count;
+        B.stream = 0;
+        B.srow = (int64_t)plan.srow.size() - 1;
+        B.b_ids = (int64_t)b_ids.size();
+        B.a_ids = (r.kind == kTri) ? -1 : (int64_t)a_ids.size();   // TRI: fixed up below
+        B.out_base = slots;
+        B.k0 = 0;
+        B.has_map = 0;
+        for (int64_t s = 0; s < r.b_count; ++s) {
+            const int32_t id = ids[r.b_begin + s];
+            b_ids.push_back(id);
+            plan.srow.push_back(plan.srow.back() + std::max<int64_t>(P.len(id), 1));
+        }
+        if (r.kind != kTri)
+            for (int64_t k = 0; k < r.a_count; ++k) a_ids.push_back(ids[r.a_begin + k]);
+        const int64_t nslots = (r.kind == kTri) ? r.a_count * (r.a_count - 1) / 2
+                                                : r.a_count * r.b_count;
+        slots += nslots;
+        plan.first_slot.push_back(B.out_base);
+        plan.blocks.push_back(B);
+        const int32_t bidx = (int32_t)plan.blocks.size() - 1;
+        const int64_t* srow = plan.srow.data() + B.srow;
+        for (int64_t k = 0; k < r.a_count; k += 2) {
+            const bool hi = k + 1 < r.a_count;
+            const int32_t qhi = ids[r.a_begin + (hi ? k + 1 : k)];
+            int32_t ns = (int32_t)r.b_count;
+            if (r.kind == kTri) ns = (int32_t)(hi ? k + 1 : k);
+            for (int64_t q = k; q < k + (hi ? 2 : 1); ++q) {
+                const int64_t mq = P.len(ids[r.a_begin + q]);
+                const int64_t nsq = (r.kind == kTri) ? q : r.b_count;
+                for (int64_t s = 0; s < nsq; ++s) plan.cells += mq * P.len(ids[r.b_begin + s]);
+            }
+            if (ns > 0) add_tasks(plan, bidx, (int32_t)k, ns, hi, P.len(qhi), srow, target);
+        }
+        if (nslots == 0) {   // keep first_slot strictly usable by the saturated-pair scan
+            plan.first_slot.pop_back();
+            plan.blocks.pop_back();
+            plan.srow.resize(B.srow + 1);
+            b_ids.resize(B.b_ids);
+            if (r.kind != kTri) a_ids.resize(B.a_ids);
+            plan.keys.erase(plan.keys.begin() + plan.tasks.size(), plan.keys.end());
+        }
+    }
+    base[req.size()] = slots;
+    scores.assign((size_t)slots, 0);
+    if (slots == 0) return CM_OK;
+    for (auto& B : plan.blocks) {
+        B.b_ids += (int64_t)a_ids.size();
+        B.a_ids = (B.a_ids < 0) ? B.b_ids : B.a_ids;
+    }
+    plan.ids = a_ids;
+    plan.ids.insert(plan.ids.end(), b_ids.begin(), b_ids.end());
+    plan.nslots = slots;
+    plan.pairs = slots;
+    order_tasks(plan);
+    int64_t maxlen_rows = 1;
+    for (size_t s = 0; s + 1 < plan.srow.size(); ++s)
+        maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
+    plan.max_warp_rows = c->rows_per_warp + 2 * maxlen_rows + target / c->W;
+    int32_t* out;
+    ENSURE(B_OUT, slots, out);
+    int r = run_plan(c, P, plan, out, nullptr, flags);
+    if (r) return r;
+    CUDA_TRY(cudaMemcpyAsync(scores.data(), out, slots * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, int32_t* hcells)
+{
+    if (n_pairs == 0) return CM_OK;
+    int64_t maxb = 0;
+    for (int64_t k = 0; k < n_pairs; ++k) maxb = std::max(maxb, P.len(hp[2 * k + 1]));
+    const int64_t cols = maxb + 1;
+    const int64_t budget = (int64_t)1 << 30;   // bytes of scratch
+    const int64_t nthreads = std::min<int64_t>(n_pairs, std::max<int64_t>(1024, budget / (8 * cols)));
+    int32_t *d_pairs, *d_cells, *d_scr;
+    int16_t* d_mat;
+    ENSURE(B_PAIRS, 2 * n_pairs, d_pairs);
+    ENSURE(B_SCRATCH, 2 * nthreads * cols, d_scr);
+    ENSURE(B_MAT, 400, d_mat);
+    ENSURE(B_CELLS, 5 * n_pairs, d_cells);
+    int r;
+    if ((r = copy_in(c, d_pairs, hp, 2 * n_pairs * sizeof(int32_t), false))) return r;
+    if ((r = copy_in(c, d_mat, P.mat, sizeof(P.mat), false))) return r;
+    CUDA_TRY(launch_cells(P.db, P.off, d_pairs, n_pairs, d_mat, P.g1, P.ge, d_cells, d_scr, cols,
+                          (int32_t)nthreads, c->stream));
+    c->stats.launches += 1;
+    CUDA_TRY(cudaMemcpyAsync(hcells, d_cells, 5 * n_pairs * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+}  // namespace cm
 
 // =========================================================================================
 extern "C" {
@@ -483,7 +531,6 @@ int sw_score_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
     std::vector<int32_t> a_ids, b_ids;
     std::vector<int64_t> omap((size_t)n_pairs);
     plan.srow.push_back(0);
-    std::vector<std::pair<int64_t, int>> keys;
     const int64_t target = (int64_t)c->W * c->rows_per_warp;
     int64_t slot = 0;
     for (size_t g0 = 0; g0 < ord.size();) {
@@ -515,7 +562,7 @@ int sw_score_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
         plan.first_slot.push_back(B.out_base);
         plan.blocks.push_back(B);
         add_tasks(plan, (int32_t)plan.blocks.size() - 1, 0, B.nb, false, ma,
-                  plan.srow.data() + B.srow, target, keys);
+                  plan.srow.data() + B.srow, target);
         g0 = g1;
     }
     for (auto& B : plan.blocks) B.b_ids += (int64_t)a_ids.size();
@@ -523,7 +570,7 @@ int sw_score_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
     plan.ids.insert(plan.ids.end(), b_ids.begin(), b_ids.end());
     plan.nslots = n_pairs;
     plan.pairs = n_pairs;
-    order_tasks(plan, keys);
+    order_tasks(plan);
     int64_t maxlen_rows = 0;
     for (size_t s = 0; s + 1 < plan.srow.size(); ++s)
         maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
@@ -651,13 +698,12 @@ int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t 
     auto tri = [](int64_t k) { return k * (k - 1) / 2; };
     plan.nslots = tri(k1) - tri(k0);
     plan.pairs = plan.nslots;
-    std::vector<std::pair<int64_t, int>> keys;
     const int64_t target = (int64_t)c->W * c->rows_per_warp;
     for (int32_t k = k0; k < k1; k += 2) {
         const bool hi = (k + 1 < k1);
         const int32_t ns = hi ? k + 1 : k;
         const int64_t m_hi = P.hoff[L[hi ? k + 1 : k] + 1] - P.hoff[L[hi ? k + 1 : k]];
-        if (ns > 0) add_tasks(plan, 0, k, ns, hi, m_hi, plan.srow.data(), target, keys);
+        if (ns > 0) add_tasks(plan, 0, k, ns, hi, m_hi, plan.srow.data(), target);
     }
     {   // cells = sum over pairs of len(a) * len(b)
         int64_t acc = 0, pre = 0;
@@ -668,7 +714,7 @@ int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t 
         }
         plan.cells = acc;
     }
-    order_tasks(plan, keys);
+    order_tasks(plan);
     int64_t maxlen_rows = 1;
     for (int32_t s = 0; s < n_seqs; ++s)
         maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);

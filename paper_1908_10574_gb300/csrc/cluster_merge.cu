@@ -1,0 +1,448 @@
+// ClusterMerge driver: Algorithm 2 (BottomUpMerge) over Algorithm 1 (Merge) with the protein
+// transitivity test of Sec. 4, then the intra-cluster all-against-all of Sec. 6.1, with every
+// alignment scored on the GPU in device batches.
+//
+// Determinism.  Algorithm 2's FIFO fixes which sets each merge combines, independently of the
+// data, so the merges form a DAG; merges whose inputs are ready form one round and are
+// independent (the paper's tree-level parallelism, Sec. 5).  Inside a merge, Algorithm 1 is
+// sequential, but
+//   * its control flow (which cluster pairs are compared, which ones fully merge, which ones
+//     exchange) depends only on the representatives' scores and alignment cells, and a
+//     cluster's representative never changes, so every rep x rep score of a merge can be
+//     computed up front (one CROSS block per merge) and the control flow replayed on the host;
+//   * membership changes only by appends, so the (member, rep) scores an exchange needs are
+//     requested for the members known so far; a replay that finds every score it needs is the
+//     exact sequential result.  A few such waves resolve a round.
+// The result (clusters, member order, similar pairs, logical comparison counts) equals the
+// plain sequential algorithm's; speculation only adds alignments that are never looked at.
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <numeric>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "ctx.h"
+
+namespace cm {
+namespace {
+
+struct Cluster {
+    int32_t rep;
+    std::vector<int32_t> objs;           // insertion order, rep first
+    std::unordered_set<int32_t> mem;
+    void add(int32_t x)
+    {
+        if (mem.insert(x).second) objs.push_back(x);
+    }
+};
+
+struct Merge {
+    int32_t left, right, out;
+};
+
+enum EvKind : int32_t { kAbsorbInto2 = 0, kAbsorbInto1 = 1, kExchange = 2 };
+
+struct Event {
+    int32_t kind, i1, i2, s;
+};
+
+inline uint64_t key2(int32_t a, int32_t b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
+
+struct Driver {
+    cm_ctx* c;
+    const Prepared& P;
+    cm_params prm;
+    uint32_t flags;
+    std::vector<Cluster> arena;                      // all clusters ever created
+    std::vector<std::vector<int32_t>> sets;          // set id -> cluster indices
+    std::unordered_map<uint64_t, int32_t> memo;      // (member, rep) -> score
+    int64_t rep_cmp = 0, exch_cmp = 0, full_merges = 0, exchanges = 0, scored = 0;
+    int64_t cells_pairs = 0, batches = 0, rounds = 0, merges = 0, waves = 0;
+
+    Driver(cm_ctx* c_, const Prepared& P_, const cm_params& p, uint32_t f)
+        : c(c_), P(P_), prm(p), flags(f) {}
+
+    std::vector<int32_t> by_length(std::vector<int32_t> v) const
+    {
+        std::stable_sort(v.begin(), v.end(),
+                         [&](int32_t x, int32_t y) { return P.len(x) < P.len(y); });
+        return v;
+    }
+
+    int run_round(const std::vector<Merge>& ms);
+    int finish(std::vector<int32_t>& final_set, cm_result* res);
+};
+
+int Driver::run_round(const std::vector<Merge>& ms)
+{
+    const size_t nm = ms.size();
+    // ---- wave 1: every merge's rep x rep cross product (queries = cs1 reps by length) ----
+    std::vector<int32_t> ids;
+    std::vector<BlockReq> req(nm);
+    std::vector<std::vector<int32_t>> rowpos(nm);    // cs1 index -> row k in the block
+    for (size_t m = 0; m < nm; ++m) {
+        const auto& cs1 = sets[ms[m].left];
+        const auto& cs2 = sets[ms[m].right];
+        std::vector<int32_t> order(cs1.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
+        });
+        rowpos[m].assign(cs1.size(), 0);
+        req[m].kind = kCross;
+        req[m].swap = 0;                              // pair (rep1, rep2)
+        req[m].a_begin = (int64_t)ids.size();
+        req[m].a_count = (int64_t)cs1.size();
+        for (size_t k = 0; k < order.size(); ++k) {
+            rowpos[m][order[k]] = (int32_t)k;
+            ids.push_back(arena[cs1[order[k]]].rep);
+        }
+        req[m].b_begin = (int64_t)ids.size();
+        req[m].b_count = (int64_t)cs2.size();
+        for (int32_t ci : cs2) ids.push_back(arena[ci].rep);
+    }
+    std::vector<int32_t> S;
+    std::vector<int64_t> base;
+    int r = score_blocks(c, P, ids, req, S, base, flags);
+    if (r) return r;
+    scored += (int64_t)S.size();
+    ++batches;
+    auto score_of = [&](size_t m, int32_t i1, int32_t i2) {
+        return S[base[m] + (int64_t)rowpos[m][i1] * (int64_t)sets[ms[m].right].size() + i2];
+    };
+
+    // ---- wave 2: alignment cells of every candidate full merge (s > mT and s > T) ----
+    std::vector<int32_t> cp;
+    std::vector<std::vector<std::pair<uint64_t, int64_t>>> cidx(nm);
+    for (size_t m = 0; m < nm; ++m) {
+        const auto& cs1 = sets[ms[m].left];
+        const auto& cs2 = sets[ms[m].right];
+        for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1)
+            for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2) {
+                const int32_t s = score_of(m, i1, i2);
+                if (s > prm.T && s > prm.mT) {
+                    cidx[m].push_back({key2(i1, i2), (int64_t)cp.size() / 2});
+                    cp.push_back(arena[cs1[i1]].rep);
+                    cp.push_back(arena[cs2[i2]].rep);
+                }
+            }
+    }
+    std::vector<int32_t> cells(cp.size() / 2 * 5);
+    if (!cp.empty()) {
+        r = run_cells(c, P, cp.data(), (int64_t)cp.size() / 2, cells.data());
+        if (r) return r;
+        cells_pairs += (int64_t)cp.size() / 2;
+        ++batches;
+    }
+
+    // ---- Algorithm 1 control flow per merge -> event list ----
+    std::vector<std::vector<Event>> events(nm);
+    std::vector<std::vector<int32_t>> out_sets(nm);
+    for (size_t m = 0; m < nm; ++m) {
+        const auto& cs1 = sets[ms[m].left];
+        const auto& cs2 = sets[ms[m].right];
+        std::unordered_map<uint64_t, int64_t> cmap(cidx[m].begin(), cidx[m].end());
+        std::vector<char> merged1(cs1.size(), 0), merged2(cs2.size(), 0);
+        for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
+            for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2) {
+                if (merged2[i2]) continue;
+                const int32_t s = score_of(m, i1, i2);
+                ++rep_cmp;
+                if (s <= prm.T) continue;
+                bool t21 = false, t12 = false;
+                if (s > prm.mT) {
+                    const int32_t* cl = &cells[cmap.at(key2(i1, i2)) * 5];
+                    const int64_t la = P.len(arena[cs1[i1]].rep), lb = P.len(arena[cs2[i2]].rep);
+                    const int64_t ua = cl[0] ? la - (cl[2] - cl[1] + 1) : la;
+                    const int64_t ub = cl[0] ? lb - (cl[4] - cl[3] + 1) : lb;
+                    t21 = ua < prm.mU;
+                    t12 = ub < prm.mU;
+                }
+                if (t21) {
+                    events[m].push_back({kAbsorbInto2, i1, i2, s});
+                    merged1[i1] = 1;
+                    ++full_merges;
+                    break;
+                } else if (t12) {
+                    events[m].push_back({kAbsorbInto1, i1, i2, s});
+                    merged2[i2] = 1;
+                    ++full_merges;
+                } else {
+                    events[m].push_back({kExchange, i1, i2, s});
+                    ++exchanges;
+                }
+            }
+        }
+        for (size_t i1 = 0; i1 < cs1.size(); ++i1)
+            if (!merged1[i1]) out_sets[m].push_back(cs1[i1]);
+        for (size_t i2 = 0; i2 < cs2.size(); ++i2)
+            if (!merged2[i2]) out_sets[m].push_back(cs2[i2]);
+    }
+
+    // ---- membership: replay the events until no (member, rep) score is missing ----
+    std::vector<int32_t> involved;
+    for (size_t m = 0; m < nm; ++m) {
+        if (events[m].empty()) continue;
+        for (int32_t ci : sets[ms[m].left]) involved.push_back(ci);
+        for (int32_t ci : sets[ms[m].right]) involved.push_back(ci);
+    }
+    std::vector<std::vector<int32_t>> snap(involved.size());
+    for (size_t i = 0; i < involved.size(); ++i) snap[i] = arena[involved[i]].objs;
+    for (int wave = 0;; ++wave) {
+        if (wave > 0) {
+            for (size_t i = 0; i < involved.size(); ++i) {
+                Cluster& cl = arena[involved[i]];
+                cl.objs = snap[i];
+                cl.mem.clear();
+                cl.mem.insert(cl.objs.begin(), cl.objs.end());
+            }
+        }
+        std::unordered_map<int32_t, std::vector<int32_t>> need;   // rep -> members to score
+        std::unordered_set<uint64_t> needed;
+        int64_t lookups = 0;
+        for (size_t m = 0; m < nm; ++m) {
+            const auto& cs1 = sets[ms[m].left];
+            const auto& cs2 = sets[ms[m].right];
+            for (const Event& ev : events[m]) {
+                Cluster& c1 = arena[cs1[ev.i1]];
+                Cluster& c2 = arena[cs2[ev.i2]];
+                if (ev.kind == kAbsorbInto2) {
+                    const std::vector<int32_t> o = c1.objs;
+                    for (int32_t x : o) c2.add(x);
+                } else if (ev.kind == kAbsorbInto1) {
+                    const std::vector<int32_t> o = c2.objs;
+                    for (int32_t x : o) c1.add(x);
+                } else {
+                    const std::vector<int32_t> s1 = c1.objs, s2 = c2.objs;
+                    for (int pass = 0; pass < 2; ++pass) {
+                        const std::vector<int32_t>& snapv = pass ? s2 : s1;
+                        Cluster& self = pass ? c2 : c1;
+                        Cluster& other = pass ? c1 : c2;
+                        for (int32_t x : snapv) {
+                            if (other.mem.count(x)) continue;
+                            int32_t sm;
+                            if (x == self.rep) {
+                                sm = ev.s;
+                            } else {
+                                ++lookups;
+                                auto it = memo.find(key2(x, other.rep));
+                                if (it == memo.end()) {
+                                    if (needed.insert(key2(x, other.rep)).second)
+                                        need[other.rep].push_back(x);
+                                    continue;
+                                }
+                                sm = it->second;
+                            }
+                            if (sm > prm.T) other.add(x);
+                        }
+                    }
+                }
+            }
+        }
+        if (need.empty()) {
+            exch_cmp += lookups;
+            waves += wave + 1;
+            break;
+        }
+        // score the missing (member, rep) pairs: one block per rep, pair = (member, rep)
+        std::vector<int32_t> eids;
+        std::vector<BlockReq> ereq;
+        std::vector<int32_t> reps;
+        for (auto& kv : need) reps.push_back(kv.first);
+        std::sort(reps.begin(), reps.end());
+        for (int32_t rp : reps) {
+            auto& mv = need[rp];
+            BlockReq b{};
+            b.kind = kCross;
+            b.swap = 1;
+            b.a_begin = (int64_t)eids.size();
+            b.a_count = 1;
+            eids.push_back(rp);
+            b.b_begin = (int64_t)eids.size();
+            b.b_count = (int64_t)mv.size();
+            eids.insert(eids.end(), mv.begin(), mv.end());
+            ereq.push_back(b);
+        }
+        std::vector<int32_t> ES;
+        std::vector<int64_t> ebase;
+        r = score_blocks(c, P, eids, ereq, ES, ebase, flags);
+        if (r) return r;
+        scored += (int64_t)ES.size();
+        ++batches;
+        for (size_t b = 0; b < ereq.size(); ++b) {
+            const int32_t rp = eids[ereq[b].a_begin];
+            for (int64_t s = 0; s < ereq[b].b_count; ++s)
+                memo[key2(eids[ereq[b].b_begin + s], rp)] = ES[ebase[b] + s];
+        }
+        if (wave > 4096) return fail(c, CM_ERR_INTERNAL, "exchange replay did not converge");
+    }
+    for (size_t m = 0; m < nm; ++m) sets[ms[m].out] = std::move(out_sets[m]);
+    merges += (int64_t)nm;
+    return CM_OK;
+}
+
+int Driver::finish(std::vector<int32_t>& final_set, cm_result* res)
+{
+    // intra-cluster all-against-all: one TRI block per cluster (members in length order)
+    std::vector<int32_t> ids;
+    std::vector<BlockReq> req;
+    for (int32_t ci : final_set) {
+        const Cluster& cl = arena[ci];
+        if (cl.objs.size() < 2) continue;
+        std::vector<int32_t> mem = by_length(cl.objs);
+        BlockReq b{};
+        b.kind = kTri;
+        b.swap = 0;
+        b.a_begin = b.b_begin = (int64_t)ids.size();
+        b.a_count = b.b_count = (int64_t)mem.size();
+        ids.insert(ids.end(), mem.begin(), mem.end());
+        req.push_back(b);
+    }
+    std::vector<int32_t> S;
+    std::vector<int64_t> base;
+    int r = score_blocks(c, P, ids, req, S, base, flags);
+    if (r) return r;
+    scored += (int64_t)S.size();
+    ++batches;
+    std::vector<uint64_t> all;
+    std::vector<std::pair<uint64_t, int32_t>> sig;
+    all.reserve(S.size());
+    for (size_t b = 0; b < req.size(); ++b) {
+        const int32_t* A = ids.data() + req[b].a_begin;
+        const int64_t na = req[b].a_count;
+        int64_t slot = base[b];
+        for (int64_t k = 1; k < na; ++k)
+            for (int64_t s = 0; s < k; ++s, ++slot) {
+                const int32_t i = std::min(A[k], A[s]), j = std::max(A[k], A[s]);
+                all.push_back(key2(i, j));
+                if (S[slot] > prm.T) sig.push_back({key2(i, j), S[slot]});
+            }
+    }
+    std::sort(all.begin(), all.end());
+    const int64_t intra = std::unique(all.begin(), all.end()) - all.begin();
+    std::sort(sig.begin(), sig.end());
+    sig.erase(std::unique(sig.begin(), sig.end(),
+                          [](const std::pair<uint64_t, int32_t>& x,
+                             const std::pair<uint64_t, int32_t>& y) { return x.first == y.first; }),
+              sig.end());
+
+    // result arrays (library-owned, freed by cm_result_free)
+    res->n_clusters = (int32_t)final_set.size();
+    int64_t total = 0;
+    for (int32_t ci : final_set) total += (int64_t)arena[ci].objs.size();
+    res->reps = (int32_t*)std::malloc(sizeof(int32_t) * std::max<size_t>(final_set.size(), 1));
+    res->cl_offsets = (int64_t*)std::malloc(sizeof(int64_t) * (final_set.size() + 1));
+    res->members = (int32_t*)std::malloc(sizeof(int32_t) * std::max<int64_t>(total, 1));
+    res->n_pairs = (int64_t)sig.size();
+    res->pairs = (int32_t*)std::malloc(sizeof(int32_t) * 2 * std::max<size_t>(sig.size(), 1));
+    res->scores = (int32_t*)std::malloc(sizeof(int32_t) * std::max<size_t>(sig.size(), 1));
+    if (!res->reps || !res->cl_offsets || !res->members || !res->pairs || !res->scores)
+        return fail(c, CM_ERR_OOM, "host allocation of the result failed");
+    int64_t pos = 0;
+    res->cl_offsets[0] = 0;
+    for (size_t k = 0; k < final_set.size(); ++k) {
+        const Cluster& cl = arena[final_set[k]];
+        res->reps[k] = cl.rep;
+        std::memcpy(res->members + pos, cl.objs.data(), cl.objs.size() * sizeof(int32_t));
+        pos += (int64_t)cl.objs.size();
+        res->cl_offsets[k + 1] = pos;
+    }
+    for (size_t k = 0; k < sig.size(); ++k) {
+        res->pairs[2 * k] = (int32_t)(sig[k].first >> 32);
+        res->pairs[2 * k + 1] = (int32_t)(sig[k].first & 0xffffffffu);
+        res->scores[k] = sig[k].second;
+    }
+    res->rep_comparisons = rep_cmp;
+    res->exchange_comparisons = exch_cmp;
+    res->intra_comparisons = intra;
+    res->comparisons_scored = scored;
+    res->cells_pairs = cells_pairs;
+    res->full_merges = full_merges;
+    res->exchanges = exchanges;
+    res->merges = merges;
+    res->rounds = rounds;
+    res->gpu_batches = batches;
+    res->exchange_waves = waves;
+    return CM_OK;
+}
+
+}  // namespace
+}  // namespace cm
+
+using namespace cm;
+
+extern "C" {
+
+int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                  const int8_t* matrix, int32_t gap_open, int32_t gap_extend,
+                  const cm_params* params, cm_result** out, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    if (!out || !params) return fail(c, CM_ERR_ARG, "null params / out");
+    *out = nullptr;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    Prepared P;
+    int r = prepare(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, flags, P);
+    if (r) return r;
+    if (!P.symmetric)
+        return fail(c, CM_ERR_ARG, "cluster_merge needs a symmetric substitution matrix");
+    const uint32_t dflags = flags & CM_FORCE_INT32;     // device data is resident from here on
+    cm_result* res = (cm_result*)std::calloc(1, sizeof(cm_result));
+    if (!res) return fail(c, CM_ERR_OOM, "host allocation failed");
+    res->n_seqs = n_seqs;
+    Driver D(c, P, *params, dflags);
+
+    // Algorithm 2: FIFO of singleton sets -> merge DAG -> dependency rounds
+    D.arena.resize((size_t)n_seqs);
+    D.sets.resize((size_t)std::max(1, 2 * n_seqs));
+    for (int32_t e = 0; e < n_seqs; ++e) {
+        D.arena[e].rep = e;
+        D.arena[e].objs = {e};
+        D.arena[e].mem = {e};
+        D.sets[e] = {e};
+    }
+    std::deque<int32_t> q;
+    std::vector<int32_t> round_of((size_t)std::max(1, 2 * n_seqs), 0);
+    std::vector<std::vector<Merge>> rounds;
+    for (int32_t e = 0; e < n_seqs; ++e) q.push_back(e);
+    int32_t next = n_seqs;
+    while (q.size() > 1) {
+        const int32_t a = q.front(); q.pop_front();
+        const int32_t b = q.front(); q.pop_front();
+        const int32_t o = next++;
+        const int32_t rd = 1 + std::max(round_of[a], round_of[b]);
+        round_of[o] = rd;
+        if ((int32_t)rounds.size() < rd) rounds.resize(rd);
+        rounds[rd - 1].push_back({a, b, o});
+        q.push_back(o);
+    }
+    for (auto& ms : rounds) {
+        r = D.run_round(ms);
+        if (r) { cm_result_free(res); return r; }
+        ++D.rounds;
+    }
+    std::vector<int32_t> final_set;
+    if (!q.empty()) final_set = D.sets[q.front()];
+    r = D.finish(final_set, res);
+    if (r) { cm_result_free(res); return r; }
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = res;
+    return CM_OK;
+}
+
+void cm_result_free(cm_result* r)
+{
+    if (!r) return;
+    std::free(r->reps);
+    std::free(r->cl_offsets);
+    std::free(r->members);
+    std::free(r->pairs);
+    std::free(r->scores);
+    std::free(r);
+}
+
+}  // extern "C"

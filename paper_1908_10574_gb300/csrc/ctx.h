@@ -1,0 +1,124 @@
+// Host-side runtime shared by the C ABI entry points: the context, device buffers, input
+// preparation, the planner (pair blocks -> length-binned CTA tasks) and plan execution.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "cm_internal.h"
+
+namespace cm {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+enum BufId {
+    B_DB, B_RAW, B_OFF, B_BLOCKS, B_TASKS, B_IDS, B_STREAM, B_SROW, B_OUT, B_OMAP, B_BND,
+    B_FLAGS, B_PREF, B_FIRST, B_PAIRS, B_CELLS, B_SCRATCH, B_CHUNK, B_POUT, B_SOUT, B_MAT,
+    B_COUNT
+};
+
+}  // namespace cm
+
+struct cm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    cm_stats stats{};
+    int W = 8;
+    int rows_per_warp = 4096;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cm::DevBuf buf[cm::B_COUNT];
+};
+
+namespace cm {
+
+int fail(cm_ctx* c, int code, const std::string& msg);
+
+#define CUDA_TRY(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ::cm::fail(c, e_ == cudaErrorMemoryAllocation ? CM_ERR_OOM : CM_ERR_CUDA, \
+                              std::string(#call " failed: ") + cudaGetErrorString(e_));     \
+    } while (0)
+
+int ensure_bytes(cm_ctx* c, BufId id, size_t bytes, void** out);
+
+template <class T>
+int ensure(cm_ctx* c, BufId id, size_t count, T** out)
+{
+    void* p = nullptr;
+    int r = ensure_bytes(c, id, count * sizeof(T), &p);
+    *out = reinterpret_cast<T*>(p);
+    return r;
+}
+
+#define ENSURE(id, n, ptr)                                                                  \
+    do {                                                                                    \
+        int r_ = ::cm::ensure(c, id, (size_t)(n), &(ptr));                                  \
+        if (r_) return r_;                                                                  \
+    } while (0)
+
+struct Prepared {
+    const uint8_t* db = nullptr;     // device residue codes
+    const int64_t* off = nullptr;    // device offsets
+    std::vector<int64_t> hoff;       // host offsets
+    int16_t mat[400];
+    int32_t g1 = 0, ge = 0;          // first-gap cost, extension cost
+    int32_t beta = 0, sat_thr = 0;
+    bool symmetric = true;
+    int64_t maxlen = 0;
+    int64_t len(int32_t i) const { return hoff[i + 1] - hoff[i]; }
+};
+
+int copy_in(cm_ctx* c, void* dst, const void* src, size_t bytes, bool dev);
+int prepare(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+            const int8_t* matrix, int32_t gap_open, int32_t gap_extend, uint32_t flags,
+            Prepared& P);
+
+struct Plan {
+    std::vector<SwBlock> blocks;
+    std::vector<int64_t> first_slot;     // per block, ascending
+    std::vector<int32_t> ids;            // A ids then B ids
+    std::vector<int64_t> srow;           // global row table over all B subjects (+1)
+    std::vector<SwTask> tasks;           // grouped by R, cost descending inside a group
+    std::vector<int> task_R;             // R per task (parallel to tasks)
+    std::vector<std::pair<int64_t, int>> keys;   // (cost, R) per task, for ordering
+    int64_t nslots = 0;
+    int64_t cells = 0, cells_padded = 0, pairs = 0;
+    int64_t max_warp_rows = 0;
+};
+
+void choose_R(int64_t m, int* R, int* npass);
+void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
+               const int64_t* srow, int64_t target);
+void order_tasks(Plan& P);
+int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64_t* d_omap,
+             uint32_t flags);
+
+// A block request for score_blocks: queries A and subjects B are ranges of `ids`.
+// kind kCross: every (A[k], B[s]); kind kTri (A must equal B): (A[k], A[s]), s < k.
+// swap 0 scores the pair as (query, subject), swap 1 as (subject, query).
+struct BlockReq {
+    int32_t kind;
+    int32_t swap;
+    int64_t a_begin, a_count;
+    int64_t b_begin, b_count;
+};
+
+// Scores every pair of every block; slot order: block after block, CROSS k*nb + s, TRI
+// k(k-1)/2 + s.  base[b] = first slot of block b.  Results land in `scores` (host).
+int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
+                 const std::vector<BlockReq>& req, std::vector<int32_t>& scores,
+                 std::vector<int64_t>& base, uint32_t flags);
+
+// Score and alignment cells (5 int32 per pair) of host pairs, on the device data of P.
+int run_cells(cm_ctx* c, const Prepared& P, const int32_t* host_pairs, int64_t n_pairs,
+              int32_t* host_cells);
+
+}  // namespace cm

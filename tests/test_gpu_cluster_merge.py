@@ -1,0 +1,84 @@
+"""GPU ClusterMerge (device batches per merge round) against the oracle's plain sequential
+Algorithms 1 and 2: clusters with their member order, the similar-pair set with scores, and the
+logical comparison counts must be identical."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1908_10574_gb300 as cm
+from paper_1908_10574_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+S62 = synth.BLOSUM62
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return cm.Context(0)
+
+
+def _oracle_cm(ss, T, mT, mU):
+    _, scores = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=T)
+    n = len(ss)
+    M = np.zeros((n, n), np.int64)
+    M[np.triu_indices(n, 1)] = scores
+    M = M + M.T
+    return oracle.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T=T, mT=mT, mU=mU,
+                                score_matrix=M)
+
+
+def _check(got, want):
+    assert got["clusters"] == want["clusters"]
+    assert got["pairs"].tolist() == want["pairs"].tolist()
+    st, ws = got["stats"], want["stats"]
+    assert st["rep_comparisons"] == ws["rep"]
+    assert st["exchange_comparisons"] == ws["exchange"]
+    assert st["intra_comparisons"] == ws["intra"]
+    assert st["full_merges"] == ws["full_merges"]
+    assert st["exchanges"] == ws["exchanges"]
+    assert st["merges"] == ws["merges"]
+
+
+@pytest.mark.parametrize("T,mT,mU", [(80, 110, 15), (60, 83, 15), (40, 83, 30),
+                                     (60, 10 ** 6, 15), (-1, 150, 15)])
+def test_small_families_exact(ctx, T, mT, mU):
+    ss = synth.small_families()
+    want = _oracle_cm(ss, T, mT, mU)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T, mT, mU)
+    _check(got, want)
+
+
+def test_tiny_sets_and_empty_sequences(ctx):
+    rng = np.random.default_rng(1)
+    root = synth.random_seq(rng, 120)
+    cases = [[], [root], [root, synth.mutate(rng, root)],
+             [root, np.zeros(0, np.uint8), synth.mutate(rng, root)],
+             [synth.mutate(rng, root) for _ in range(7)]]
+    for seqs in cases:
+        ss = synth.SeqSet.from_list(seqs)
+        want = _oracle_cm(ss, 60, 83, 15) if len(ss) > 1 else \
+            oracle.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T=60, mT=83, mU=15)
+        got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 60, 83, 15)
+        _check(got, want)
+
+
+def test_proteome_subset_with_singletons_exact_and_recall(ctx):
+    full = synth.proteome(5000, family_size=8, singleton_frac=0.2, stream=7)
+    ss = full.subset(np.arange(900))
+    T, mT, mU = 80, 110, 15
+    truth, scores = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=T)
+    n = len(ss)
+    M = np.zeros((n, n), np.int64)
+    M[np.triu_indices(n, 1)] = scores
+    M = M + M.T
+    want = oracle.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T=T, mT=mT, mU=mU,
+                                score_matrix=M)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T, mT, mU)
+    _check(got, want)
+    r = oracle.recall(got["pairs"], truth)
+    assert r == oracle.recall(want["pairs"], truth)
+    assert r > 0.99
+    # the GPU's own all-against-all gives the same truth
+    p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, T=T)
+    assert sorted(zip(p[:, 0].tolist(), p[:, 1].tolist(), s.tolist())) == \
+        sorted(map(tuple, truth.tolist()))
