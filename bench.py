@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: Smith-Waterman GCUPS (bit-exact) on the all-against-all of 20,000 synthetic
 proteins (lognormal lengths, median 350, sigma 0.6, clipped 30-5000; 2,000 planted families of
-10; BLOSUM62, gap open 11 / extend 1; significant pairs f > T = 80).
+10; BLOSUM62, gap open 11 / extend 1; significant pairs f > T = 100).
 
 A step is one part (1/16 of the cells) of the all-against-all triangle through sw_allpairs:
 packing, the int16x2 DPX kernel, the int32 rerun of saturated pairs and threshold compaction.
@@ -34,7 +34,8 @@ from paper_1908_10574_gb300 import synth  # noqa: E402
 METRIC = "SW GCUPS (bit-exact)"
 N_SEQS = 20000
 FAMILY = 10
-T_SIG = 80
+T_SIG = 100
+M_T, M_U = 138, 15
 GAP_OPEN, GAP_EXT = 11, 1
 PARTS_PER_GPU = 16
 CELLS_PER_CLK_PER_SM = 64.0 * 2.0 / 4.5   # half-rate DPX/ALU pipe, 2 cells / 4.5 ops
@@ -215,6 +216,43 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_cluster_merge(args):
+    """ClusterMerge end to end on the 100k proteome set (80,000 proteins in 10,000 families of
+    8 plus 20,000 singletons); recall against the GPU all-against-all when --recall."""
+    import torch
+    import paper_1908_10574_gb300 as cm
+    n = args.cm_seqs
+    ss = synth.proteome(n, family_size=8, singleton_frac=0.2, stream=3)
+    ctx = cm.Context(0)
+    T, mT, mU = T_SIG, M_T, M_U
+    t0 = time.perf_counter()
+    res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT, mU)
+    dt = time.perf_counter() - t0
+    out = {"metric": "ClusterMerge seconds", "value": dt, "unit": "s", "n_gpus": 1,
+           "higher_is_better": False, "data": "synthetic", "dtype": "int16",
+           "config": {"workload": "ClusterMerge of %d synthetic proteins (lognormal lengths, "
+                                  "families of 8 + 20%% singletons), BLOSUM62 11/1, T=%d, mT=%d, "
+                                  "mU=%d" % (n, T, mT, mU)},
+           "clusters": len(res["clusters"]), "similar_pairs": len(res["pairs"]),
+           "stats": res["stats"]}
+    if args.recall:
+        t1 = time.perf_counter()
+        truth = set()
+        parts = max(1, int(total_cells(ss) / 2e12))
+        for part in range(parts):
+            p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T,
+                                   part, parts, capacity=1 << 22)
+            truth.update(zip(p[:, 0].tolist(), p[:, 1].tolist()))
+        found = set(zip(res["pairs"][:, 0].tolist(), res["pairs"][:, 1].tolist()))
+        out["all_pairs_seconds"] = time.perf_counter() - t1
+        out["truth_pairs"] = len(truth)
+        out["recall"] = len(found & truth) / max(len(truth), 1)
+        out["comparisons_fraction"] = (res["stats"]["rep_comparisons"] +
+                                       res["stats"]["exchange_comparisons"] +
+                                       res["stats"]["intra_comparisons"]) / (n * (n - 1) / 2)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,12 +260,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "cm"],
+                    help="allpairs: SW GCUPS (default); cm: ClusterMerge seconds")
+    ap.add_argument("--cm-seqs", type=int, default=100000)
+    ap.add_argument("--recall", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--parts-per-gpu", type=int, default=PARTS_PER_GPU,
                     help="split of the triangle; a larger value gives shorter steps (profiling)")
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
+    if args.workload == "cm":
+        run_cluster_merge(args)
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -152,6 +152,7 @@ typedef struct {
     int64_t cells_pairs;           /* alignments re-run for their cells (candidate full merges) */
     int64_t full_merges, exchanges, merges, rounds, gpu_batches, exchange_waves;
     double seconds;                /* wall time of the call */
+    double t_rep, t_cells, t_exchange, t_intra;   /* wall time of the device batches by kind */
 } cm_result;
 
 /* cluster_merge -- precise clustering of a protein set (Sec. 3-4) followed by the

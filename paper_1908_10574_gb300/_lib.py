@@ -51,7 +51,9 @@ class cm_result(ctypes.Structure):
                 ("cells_pairs", ctypes.c_int64), ("full_merges", ctypes.c_int64),
                 ("exchanges", ctypes.c_int64), ("merges", ctypes.c_int64),
                 ("rounds", ctypes.c_int64), ("gpu_batches", ctypes.c_int64),
-                ("exchange_waves", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("exchange_waves", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("t_rep", ctypes.c_double), ("t_cells", ctypes.c_double),
+                ("t_exchange", ctypes.c_double), ("t_intra", ctypes.c_double)]
 
 
 _lib = None

@@ -404,26 +404,71 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
 int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, int32_t* hcells)
 {
     if (n_pairs == 0) return CM_OK;
-    int64_t maxb = 0;
-    for (int64_t k = 0; k < n_pairs; ++k) maxb = std::max(maxb, P.len(hp[2 * k + 1]));
-    const int64_t cols = maxb + 1;
-    const int64_t budget = (int64_t)1 << 30;   // bytes of scratch
-    const int64_t nthreads = std::min<int64_t>(n_pairs, std::max<int64_t>(1024, budget / (8 * cols)));
-    int32_t *d_pairs, *d_cells, *d_scr;
-    int16_t* d_mat;
-    ENSURE(B_PAIRS, 2 * n_pairs, d_pairs);
-    ENSURE(B_SCRATCH, 2 * nthreads * cols, d_scr);
-    ENSURE(B_MAT, 400, d_mat);
-    ENSURE(B_CELLS, 5 * n_pairs, d_cells);
-    int r;
-    if ((r = copy_in(c, d_pairs, hp, 2 * n_pairs * sizeof(int32_t), false))) return r;
-    if ((r = copy_in(c, d_mat, P.mat, sizeof(P.mat), false))) return r;
-    CUDA_TRY(launch_cells(P.db, P.off, d_pairs, n_pairs, d_mat, P.g1, P.ge, d_cells, d_scr, cols,
-                          (int32_t)nthreads, c->stream));
-    c->stats.launches += 1;
-    CUDA_TRY(cudaMemcpyAsync(hcells, d_cells, 5 * n_pairs * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (n_pairs >= ((int64_t)1 << 31)) return fail(c, CM_ERR_ARG, "n_pairs must be < 2^31");
+    const cudaStream_t st = c->stream;
+    std::vector<CellJob> jobs((size_t)n_pairs);
+    for (int64_t k = 0; k < n_pairs; ++k) {
+        const int32_t x = hp[2 * k], y = hp[2 * k + 1];
+        jobs[k] = CellJob{x, y, (int32_t)P.len(x), (int32_t)P.len(y), 0, 0};
+    }
+    CellJob* d_jobs;
+    int32_t *d_res, *d_flags;
+    uint2* d_bnd;
+    ENSURE(B_JOBS, n_pairs, d_jobs);
+    ENSURE(B_RES, 3 * n_pairs, d_res);
+    ENSURE(B_FLAGS, 64, d_flags);
+    const int occ = std::max(1, cells_wf_ctas_per_sm());
+    const int grid = (int)std::min<int64_t>(n_pairs, (int64_t)c->num_sms * occ);
+    const int64_t stride = P.maxlen + 64;
+    ENSURE(B_BND, (int64_t)grid * stride, d_bnd);
+    SwArgs a{};
+    a.db = P.db;
+    a.off = P.off;
+    a.bnd = d_bnd;
+    a.bnd_stride = stride;
+    a.err = d_flags + 1;
+    std::memcpy(a.mat, P.mat, sizeof(a.mat));
+    a.gap_open = P.g1;
+    a.gap_extend = P.ge;
+    std::vector<int32_t> fwd((size_t)n_pairs * 3);
+    for (int dir = 0; dir < 2; ++dir) {
+        int r = copy_in(c, d_jobs, jobs.data(), jobs.size() * sizeof(CellJob), false);
+        if (r) return r;
+        CUDA_TRY(cudaMemsetAsync(d_flags, 0, 64 * sizeof(int32_t), st));
+        CUDA_TRY(launch_cells_wf(grid, a, d_jobs, (int32_t)jobs.size(), d_flags + 4, d_res, st));
+        c->stats.launches += 1;
+        std::vector<int32_t> res(jobs.size() * 3);
+        int32_t kerr = 0;
+        CUDA_TRY(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(&kerr, d_flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (kerr) return fail(c, CM_ERR_INTERNAL, "cells kernel bounds check fired");
+        if (dir == 0) {
+            fwd = res;
+            std::vector<CellJob> rev;
+            for (int64_t k = 0; k < n_pairs; ++k) {
+                int32_t* cl = hcells + 5 * k;
+                cl[0] = fwd[3 * k];
+                cl[1] = cl[2] = cl[3] = cl[4] = 0;
+                if (fwd[3 * k] > 0)
+                    rev.push_back(CellJob{jobs[k].a, jobs[k].b, fwd[3 * k + 1] + 1,
+                                          fwd[3 * k + 2] + 1, 1, (int32_t)k});
+            }
+            if (rev.empty()) break;
+            jobs.swap(rev);
+        } else {
+            for (size_t q = 0; q < jobs.size(); ++q) {
+                const int64_t k = jobs[q].pad;
+                int32_t* cl = hcells + 5 * k;
+                const int32_t ie = jobs[q].m, je = jobs[q].n;
+                cl[1] = ie - (res[3 * q + 1] + 1) + 1;
+                cl[2] = ie;
+                cl[3] = je - (res[3 * q + 2] + 1) + 1;
+                cl[4] = je;
+            }
+        }
+    }
     return CM_OK;
 }
 
@@ -613,24 +658,11 @@ int sw_cells_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
         const int32_t b = hp[2 * k + 1];
         maxb = std::max(maxb, P.hoff[b + 1] - P.hoff[b]);
     }
-    const int64_t cols = maxb + 1;
-    const int64_t budget = (int64_t)1 << 30;   // bytes of scratch
-    int64_t nthreads = std::min<int64_t>(n_pairs, std::max<int64_t>(1024, budget / (8 * cols)));
-    int32_t *d_pairs, *d_cells, *d_scr;
-    int16_t* d_mat;
-    ENSURE(B_PAIRS, 2 * n_pairs, d_pairs);
-    ENSURE(B_SCRATCH, 2 * nthreads * cols, d_scr);
-    ENSURE(B_MAT, 400, d_mat);
-    if ((r = copy_in(c, d_pairs, hp.data(), hp.size() * 4, false))) return r;
-    if ((r = copy_in(c, d_mat, P.mat, sizeof(P.mat), false))) return r;
-    d_cells = cells_out;
-    if (!dev) ENSURE(B_CELLS, 5 * n_pairs, d_cells);
-    CUDA_TRY(launch_cells(P.db, P.off, d_pairs, n_pairs, d_mat, P.g1, P.ge, d_cells, d_scr, cols,
-                          (int32_t)nthreads, c->stream));
-    c->stats.launches += 1;
-    if (!dev)
-        CUDA_TRY(cudaMemcpyAsync(cells_out, d_cells, 5 * n_pairs * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, c->stream));
+    (void)maxb;
+    std::vector<int32_t> hc((size_t)n_pairs * 5);
+    if ((r = run_cells(c, P, hp.data(), n_pairs, hc.data()))) return r;
+    CUDA_TRY(cudaMemcpyAsync(cells_out, hc.data(), hc.size() * sizeof(int32_t),
+                             dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return CM_OK;
 }

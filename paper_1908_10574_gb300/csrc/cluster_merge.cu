@@ -51,6 +51,11 @@ struct Event {
 
 inline uint64_t key2(int32_t a, int32_t b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
 
+inline double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 struct Driver {
     cm_ctx* c;
     const Prepared& P;
@@ -61,6 +66,7 @@ struct Driver {
     std::unordered_map<uint64_t, int32_t> memo;      // (member, rep) -> score
     int64_t rep_cmp = 0, exch_cmp = 0, full_merges = 0, exchanges = 0, scored = 0;
     int64_t cells_pairs = 0, batches = 0, rounds = 0, merges = 0, waves = 0;
+    double t_rep = 0, t_cells = 0, t_exch = 0, t_intra = 0;
 
     Driver(cm_ctx* c_, const Prepared& P_, const cm_params& p, uint32_t f)
         : c(c_), P(P_), prm(p), flags(f) {}
@@ -106,8 +112,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
     }
     std::vector<int32_t> S;
     std::vector<int64_t> base;
+    double t0 = now_s();
     int r = score_blocks(c, P, ids, req, S, base, flags);
     if (r) return r;
+    t_rep += now_s() - t0;
     scored += (int64_t)S.size();
     ++batches;
     auto score_of = [&](size_t m, int32_t i1, int32_t i2) {
@@ -132,8 +140,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
     }
     std::vector<int32_t> cells(cp.size() / 2 * 5);
     if (!cp.empty()) {
+        t0 = now_s();
         r = run_cells(c, P, cp.data(), (int64_t)cp.size() / 2, cells.data());
         if (r) return r;
+        t_cells += now_s() - t0;
         cells_pairs += (int64_t)cp.size() / 2;
         ++batches;
     }
@@ -268,8 +278,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
         }
         std::vector<int32_t> ES;
         std::vector<int64_t> ebase;
+        t0 = now_s();
         r = score_blocks(c, P, eids, ereq, ES, ebase, flags);
         if (r) return r;
+        t_exch += now_s() - t0;
         scored += (int64_t)ES.size();
         ++batches;
         for (size_t b = 0; b < ereq.size(); ++b) {
@@ -303,8 +315,10 @@ int Driver::finish(std::vector<int32_t>& final_set, cm_result* res)
     }
     std::vector<int32_t> S;
     std::vector<int64_t> base;
+    const double t0 = now_s();
     int r = score_blocks(c, P, ids, req, S, base, flags);
     if (r) return r;
+    t_intra += now_s() - t0;
     scored += (int64_t)S.size();
     ++batches;
     std::vector<uint64_t> all;
@@ -366,6 +380,10 @@ int Driver::finish(std::vector<int32_t>& final_set, cm_result* res)
     res->rounds = rounds;
     res->gpu_batches = batches;
     res->exchange_waves = waves;
+    res->t_rep = t_rep;
+    res->t_cells = t_cells;
+    res->t_exchange = t_exch;
+    res->t_intra = t_intra;
     return CM_OK;
 }
 

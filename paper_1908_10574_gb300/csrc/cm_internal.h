@@ -81,12 +81,24 @@ struct PairRef {
     int64_t slot;       // output slot (final index)
 };
 
+// One job of the alignment-cells kernel: rows a[0..m), columns b[0..n) (both reversed when
+// `reverse`), result = (best, first row, first column) in row-major order, 0-based.
+struct CellJob {
+    int32_t a, b;
+    int32_t m, n;
+    int32_t reverse;
+    int32_t pad;
+};
+
 // ---- launchers (sw16.cu) ---------------------------------------------------------------
 int sw16_smem_bytes(int R);
 cudaError_t launch_sw16(int R, int W, int grid, const SwArgs& a, cudaStream_t st);
 cudaError_t launch_sw32(int R, int grid, const SwArgs& a, const PairRef* pr, int32_t npairs,
                         int32_t* counter, cudaStream_t st);
 int sw32_smem_bytes(int R);
+int cells_wf_ctas_per_sm();
+cudaError_t launch_cells_wf(int grid, const SwArgs& a, const CellJob* jobs, int32_t njobs,
+                            int32_t* counter, int32_t* res, cudaStream_t st);
 
 // ---- pack.cu ---------------------------------------------------------------------------
 cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t* bad,
@@ -106,11 +118,5 @@ cudaError_t launch_compact_tri(const int32_t* out, int64_t nslots, int32_t k0,
                                int phase, cudaStream_t st);
 cudaError_t launch_scan_chunks(int64_t* counts, int64_t nchunks, int64_t* total,
                                cudaStream_t st);
-
-// ---- cells kernel (sw_cells.cu) ----------------------------------------------------------
-cudaError_t launch_cells(const uint8_t* db, const int64_t* off, const int32_t* pairs,
-                         int64_t npairs, const int16_t* mat, int32_t g1, int32_t ge,
-                         int32_t* cells_out, int32_t* scratch, int64_t scratch_cols,
-                         int32_t nthreads, cudaStream_t st);
 
 }  // namespace cm

@@ -17,7 +17,7 @@ struct DevBuf {
 enum BufId {
     B_DB, B_RAW, B_OFF, B_BLOCKS, B_TASKS, B_IDS, B_STREAM, B_SROW, B_OUT, B_OMAP, B_BND,
     B_FLAGS, B_PREF, B_FIRST, B_PAIRS, B_CELLS, B_SCRATCH, B_CHUNK, B_POUT, B_SOUT, B_MAT,
-    B_COUNT
+    B_JOBS, B_RES, B_COUNT
 };
 
 }  // namespace cm

@@ -351,6 +351,139 @@ __global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs
     }
 }
 
+// ---- alignment cells: score plus the first row-major cell reaching it, one warp per job ----
+// Rows stream the job's first sequence a[0..m) (reversed when J.reverse), columns hold its
+// second sequence b[0..n) (reversed likewise); cell scores are matrix[a residue][b residue].
+// Every lane keeps the first (row, column) of its own best in row-major order (strict >); the
+// warp and the column passes then keep the largest score, then the smallest row, then the
+// smallest column.
+template <int R>
+__global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ SwArgs a,
+                                                     const CellJob* __restrict__ jobs,
+                                                     int32_t njobs, int32_t* counter,
+                                                     int32_t* __restrict__ res)
+{
+    using G = Geo<R>;
+    extern __shared__ __align__(16) uint8_t smem[];
+    int32_t* prof = reinterpret_cast<int32_t*>(smem);
+    uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;
+    __shared__ int16_t s_mat[400];
+    const int lane = threadIdx.x;
+    for (int i = lane; i < 400; i += 32) s_mat[i] = a.mat[i];
+    __syncwarp();
+    const int o = a.gap_open, ge = a.gap_extend;
+    int2* bnd = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * a.bnd_stride);
+
+    for (;;) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(counter, 1);
+        p = __shfl_sync(kFull, p, 0);
+        if (p >= njobs) break;
+        const CellJob J = jobs[p];
+        const uint8_t* ra = a.db + a.off[J.a];
+        const uint8_t* cb = a.db + a.off[J.b];
+        int64_t m = J.m;
+        const int64_t n = J.n;
+        const int npass = (n <= G::COLS) ? 1 : (int)((n + G::COLS - 1) / G::COLS);
+        if (npass > 1 && m > a.bnd_stride) {
+            if (lane == 0) atomicExch(a.err, 1);
+            m = 0;
+        }
+        int32_t gbest = 0, grow = -1, gcol = -1;
+        for (int pass = 0; pass < npass && m > 0 && n > 0; ++pass) {
+            const int64_t c0 = (int64_t)pass * G::COLS;
+            __syncwarp();
+            for (int c = lane; c < G::COLS; c += 32) {
+                const int64_t cc = c0 + c;
+                qres[c] = (cc < n) ? (J.reverse ? cb[n - 1 - cc] : cb[cc]) : kPadCode;
+            }
+            __syncwarp();
+            for (int i = lane; i < kProfRows * G::COLS; i += 32) {
+                const int x = i / G::COLS, c = i - x * G::COLS;
+                const int ln = c / R, k = c - ln * R;
+                const int q = qres[c];
+                prof[x * G::ROWW + ln * G::LS + k] =
+                    (x != kPadCode && q != kPadCode) ? s_mat[x * 20 + q] : kSpad;
+            }
+            __syncwarp();
+            int32_t hp[R], fp[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) { hp[k] = 0; fp[k] = -o; }
+            int32_t out_h = 0, out_e = -o, diag0 = 0;
+            int32_t lbest = 0, lrow = -1, lcol = -1;
+            uint32_t cur = kPadCode, prev = kPadCode;
+            int32_t bh = 0, be = -o;
+            const int32_t* plane = prof + lane * G::LS;
+            const int32_t col0 = (int32_t)c0 + lane * R;
+            for (int64_t t = 0; t < m + 31; ++t) {
+                const int j = (int)(t & 31);
+                if (j == 0) {
+                    prev = cur;
+                    const int64_t r = t + lane;
+                    cur = (r < m) ? (uint32_t)(J.reverse ? ra[m - 1 - r] : ra[r]) : (uint32_t)kPadCode;
+                    if (pass > 0) {
+                        if (r < m) { const int2 v = bnd[r]; bh = v.x; be = v.y; }
+                        else { bh = 0; be = -o; }
+                    }
+                }
+                const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
+                int32_t hl = __shfl_up_sync(kFull, out_h, 1);
+                int32_t el = __shfl_up_sync(kFull, out_e, 1);
+                if (pass > 0) {
+                    const int32_t x = __shfl_sync(kFull, bh, j), y = __shfl_sync(kFull, be, j);
+                    if (lane == 0) { hl = x; el = y; }
+                } else if (lane == 0) {
+                    hl = 0; el = -o;
+                }
+                int32_t dg = diag0;
+                diag0 = hl;
+                const int32_t row = (int32_t)(t - lane);
+                const int32_t* prow = plane + (int)min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
+                int32_t h = hl, e = el;
+#pragma unroll
+                for (int j4 = 0; j4 < R / 4; ++j4) {
+                    const int4 sv = *reinterpret_cast<const int4*>(prow + 4 * j4);
+                    const int32_t s4[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = 4 * j4 + u;
+                        e = __viaddmax_s32(h, -o, e - ge);
+                        const int32_t f = __viaddmax_s32(hp[k], -o, fp[k] - ge);
+                        fp[k] = f;
+                        const int32_t d = __viaddmax_s32(dg, s4[u], 0);
+                        dg = hp[k];
+                        h = __vimax3_s32(d, e, f);
+                        hp[k] = h;
+                        if (h > lbest) { lbest = h; lrow = row; lcol = col0 + k; }
+                    }
+                }
+                out_h = h;
+                out_e = e;
+                if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_int2(out_h, out_e);
+            }
+            // cells of pad rows / pad columns stay below the maximum over real cells, so the
+            // warp's maximum (and its first cell) lies in a real row and column
+            for (int d = 16; d >= 1; d >>= 1) {
+                const int32_t ob = __shfl_xor_sync(kFull, lbest, d);
+                const int32_t orw = __shfl_xor_sync(kFull, lrow, d);
+                const int32_t oc = __shfl_xor_sync(kFull, lcol, d);
+                const bool better = ob > lbest ||
+                                    (ob == lbest && (orw < lrow || (orw == lrow && oc < lcol)));
+                if (better) { lbest = ob; lrow = orw; lcol = oc; }
+            }
+            const bool better = lbest > gbest ||
+                                (lbest == gbest && lbest > 0 &&
+                                 (lrow < grow || (lrow == grow && lcol < gcol)));
+            if (better) { gbest = lbest; grow = lrow; gcol = lcol; }
+        }
+        if (lane == 0) {
+            res[3 * (int64_t)p] = gbest;
+            res[3 * (int64_t)p + 1] = gbest > 0 ? grow : -1;
+            res[3 * (int64_t)p + 2] = gbest > 0 ? gcol : -1;
+        }
+    }
+}
+
 template <int R, int W>
 cudaError_t launch_one(int grid, const SwArgs& a, cudaStream_t st)
 {
@@ -464,6 +597,36 @@ cudaError_t launch_sw32(int R, int grid, const SwArgs& a, const PairRef* pr, int
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     sw32_kernel<16><<<grid, 32, smem, st>>>(a, pr, npairs, counter);
+    return cudaGetLastError();
+}
+
+}  // namespace cm
+
+namespace cm {
+
+int cells_wf_smem_bytes() { return kProfRows * 32 * lane_stride(8) * 4 + 32 * 8; }
+
+int cells_wf_ctas_per_sm()
+{
+    const int smem = cells_wf_smem_bytes();
+    if (cudaFuncSetAttribute(cells_wf_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess)
+        return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cells_wf_kernel<8>, 32, smem) !=
+        cudaSuccess)
+        return 1;
+    return n;
+}
+
+cudaError_t launch_cells_wf(int grid, const SwArgs& a, const CellJob* jobs, int32_t njobs,
+                            int32_t* counter, int32_t* res, cudaStream_t st)
+{
+    const int smem = cells_wf_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(cells_wf_kernel<8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cells_wf_kernel<8><<<grid, 32, smem, st>>>(a, jobs, njobs, counter, res);
     return cudaGetLastError();
 }
 

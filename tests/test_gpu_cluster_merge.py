@@ -39,7 +39,7 @@ def _check(got, want):
     assert st["merges"] == ws["merges"]
 
 
-@pytest.mark.parametrize("T,mT,mU", [(80, 110, 15), (60, 83, 15), (40, 83, 30),
+@pytest.mark.parametrize("T,mT,mU", [(100, 138, 15), (80, 110, 15), (60, 83, 15), (40, 83, 30),
                                      (60, 10 ** 6, 15), (-1, 150, 15)])
 def test_small_families_exact(ctx, T, mT, mU):
     ss = synth.small_families()
@@ -65,7 +65,7 @@ def test_tiny_sets_and_empty_sequences(ctx):
 def test_proteome_subset_with_singletons_exact_and_recall(ctx):
     full = synth.proteome(5000, family_size=8, singleton_frac=0.2, stream=7)
     ss = full.subset(np.arange(900))
-    T, mT, mU = 80, 110, 15
+    T, mT, mU = 100, 138, 15
     truth, scores = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=T)
     n = len(ss)
     M = np.zeros((n, n), np.int64)
@@ -77,7 +77,7 @@ def test_proteome_subset_with_singletons_exact_and_recall(ctx):
     _check(got, want)
     r = oracle.recall(got["pairs"], truth)
     assert r == oracle.recall(want["pairs"], truth)
-    assert r > 0.99
+    assert r > 0.998
     # the GPU's own all-against-all gives the same truth
     p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, T=T)
     assert sorted(zip(p[:, 0].tolist(), p[:, 1].tolist(), s.tolist())) == \
