@@ -133,7 +133,11 @@ typedef struct {
     int32_t T;      /* significance: a pair is similar when its score > T (Sec. 3) */
     int32_t mT;     /* full-merge threshold: representatives' score > mT (Sec. 4) */
     int32_t mU;     /* full merge needs fewer than mU uncovered residues in the absorbed rep */
-    int32_t reserved[5];   /* must be 0 */
+    int32_t use_ranker;    /* 1: the learned ranker orders and prunes rep x rep comparisons */
+    float prune_logit;     /* with the ranker: rep pairs whose logit is below this are not
+                              aligned (treated as dissimilar); the rest are visited in
+                              descending logit order inside Algorithm 1's inner loop */
+    int32_t reserved[3];   /* must be 0 */
 } cm_params;
 
 typedef struct {
@@ -153,17 +157,55 @@ typedef struct {
     int64_t full_merges, exchanges, merges, rounds, gpu_batches, exchange_waves;
     double seconds;                /* wall time of the call */
     double t_rep, t_cells, t_exchange, t_intra;   /* wall time of the device batches by kind */
+    double t_rank;                 /* ranker inference and pair selection */
+    int64_t ranker_selected;       /* rep pairs the ranker kept */
 } cm_result;
 
 /* cluster_merge -- precise clustering of a protein set (Sec. 3-4) followed by the
- * intra-cluster all-against-all (Sec. 6.1).  Deterministic: clusters, member order, similar
- * pairs and the three logical comparison counts equal those of the plain sequential
- * Algorithms 1 and 2 (FIFO in input order).  The matrix must be symmetric.  *out is owned by
- * the library; release it with cm_result_free. */
+ * intra-cluster all-against-all (Sec. 6.1).  Deterministic: without the ranker, clusters,
+ * member order, similar pairs and the three logical comparison counts equal those of the
+ * plain sequential Algorithms 1 and 2 (FIFO in input order); with it, the same algorithm runs
+ * on the ranker's pruned and ordered representative comparisons.  The matrix must be
+ * symmetric.  *out is owned by the library; release it with cm_result_free. */
 int cluster_merge(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
                   const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
                   const cm_params *params, cm_result **out, uint32_t flags);
 void cm_result_free(cm_result *result);
+
+/* ---- learned representative ranker (orders and prunes rep x rep comparisons) ----
+ * The paper has no learned component; this network only decides which representative pairs
+ * are aligned (and in which order) inside Algorithm 1 — the exact Smith-Waterman score stays
+ * the sole judge of similarity.  Model: residue embedding (20 x 32) -> conv1d 32->128 (width
+ * 9) + ReLU -> conv1d 128->128 + ReLU -> conv1d 128->128 -> mean over the sequence -> v (128-d);
+ * logit(a, b) = alpha * cos(v_a, v_b) + beta, cos = <a,b> / sqrt((|a|^2+1e-6)(|b|^2+1e-6)),
+ * trained with binary cross-entropy on labels
+ * [score(a, b) > T].  Parameters are one flat float array of cm_ranker_num_params() values in
+ * the order E[20][32], W1[9][32][128], b1[128], W2[9][128][128], b2[128], W3[9][128][128],
+ * b3[128], alpha, beta (W[k][c][n]: tap k, input channel c, output channel n).  Sequence and
+ * pair arguments follow the conventions above (host pointers; CM_ASCII accepted). */
+int64_t cm_ranker_num_params(void);
+int cm_ranker_init(cm_ctx *ctx, uint64_t seed);
+int cm_ranker_set_params(cm_ctx *ctx, const float *params, int64_t n);
+/* data-dependent init: rescale W3, b3 so every channel of v has zero mean and unit variance
+ * over an evenly spaced sample of at most max_sample of the sequences */
+int cm_ranker_standardize(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets,
+                          int32_t n_seqs, int32_t max_sample, uint32_t flags);
+int cm_ranker_get_params(cm_ctx *ctx, float *params, int64_t n);
+/* mean BCE loss of the pairs and its gradient w.r.t. every parameter (grad may be NULL) */
+int cm_ranker_loss_grad(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                        const int32_t *pairs, const float *labels, int64_t n_pairs,
+                        float *loss, float *grad, uint32_t flags);
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) over shuffled mini-batches of batch_pairs pairs */
+int cm_ranker_train(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                    const int32_t *pairs, const float *labels, int64_t n_pairs, int32_t epochs,
+                    int32_t batch_pairs, float lr, uint64_t seed, float *last_loss,
+                    uint32_t flags);
+/* v of every sequence: out is n_seqs x 128 floats (device memory with CM_DEVICE_PTRS) */
+int cm_ranker_embed(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                    float *out, uint32_t flags);
+/* logits of pairs (n_pairs floats, host) */
+int cm_ranker_logits(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                     const int32_t *pairs, int64_t n_pairs, float *out, uint32_t flags);
 
 /* sw_cells_batch_noalloc -- the same results as sw_cells_batch, for callers that cannot
  * allocate device memory when they call (for example a service whose GPU memory is reserved

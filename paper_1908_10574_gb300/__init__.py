@@ -176,14 +176,15 @@ class Context:
         raise CMError(_L.CM_ERR_CAPACITY, "capacity retry failed")
 
 
-    def cluster_merge(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0):
+    def cluster_merge(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
+                      use_ranker=False, prune_logit=0.0):
         """ClusterMerge (Algorithms 1 and 2 with the Sec. 4 transitivity test) plus the
         intra-cluster all-against-all.  Returns a dict: clusters [(rep, [members])], pairs
         (k, 3) int64 (i, j, score) sorted, and the comparison counters."""
         seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
         flags |= self._prep([seqs, offsets, matrix])
         n = int(offsets.shape[0]) - 1
-        prm = _L.cm_params(int(T), int(mT), int(mU))
+        prm = _L.cm_params(int(T), int(mT), int(mU), int(bool(use_ranker)), float(prune_logit))
         res = ctypes.POINTER(_L.cm_result)()
         _L.check(self._h, _L.lib().cluster_merge(self._h, _ptr(seqs), _ptr(offsets), n,
                                                  _ptr(matrix), int(gap_open), int(gap_extend),
@@ -206,6 +207,74 @@ class Context:
             _L.lib().cm_result_free(res)
         clusters = [(int(reps[i]), mem[off[i]:off[i + 1]].tolist()) for i in range(nc)]
         return {"clusters": clusters, "pairs": pairs, "stats": stats}
+
+
+    # ---- learned representative ranker -------------------------------------------------
+    def ranker_num_params(self):
+        return int(_L.lib().cm_ranker_num_params())
+
+    def ranker_init(self, seed=1908):
+        _L.check(self._h, _L.lib().cm_ranker_init(self._h, int(seed)))
+
+    def ranker_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _L.check(self._h, _L.lib().cm_ranker_set_params(self._h, _ptr(p), len(p)))
+
+    def ranker_get_params(self):
+        out = np.empty(self.ranker_num_params(), dtype=np.float32)
+        _L.check(self._h, _L.lib().cm_ranker_get_params(self._h, _ptr(out), len(out)))
+        return out
+
+    def ranker_standardize(self, seqs, offsets, max_sample=1024, flags=0):
+        seqs, offsets = self._host_seqs(seqs, offsets)
+        self._prep([seqs])
+        _L.check(self._h, _L.lib().cm_ranker_standardize(self._h, _ptr(seqs), _ptr(offsets),
+                                                         len(offsets) - 1, int(max_sample), flags))
+
+    def _host_seqs(self, seqs, offsets):
+        return self._host(seqs, np.uint8), self._host(offsets, np.int64)
+
+    def ranker_loss_grad(self, seqs, offsets, pairs, labels, flags=0):
+        seqs, offsets = self._host_seqs(seqs, offsets)
+        pairs = self._host(pairs, np.int32, (-1, 2))
+        labels = self._host(labels, np.float32)
+        self._prep([seqs])
+        loss = np.zeros(1, np.float32)
+        grad = np.empty(self.ranker_num_params(), np.float32)
+        _L.check(self._h, _L.lib().cm_ranker_loss_grad(
+            self._h, _ptr(seqs), _ptr(offsets), len(offsets) - 1, _ptr(pairs), _ptr(labels),
+            len(pairs), _ptr(loss), _ptr(grad), flags))
+        return float(loss[0]), grad
+
+    def ranker_train(self, seqs, offsets, pairs, labels, epochs=1, batch_pairs=256, lr=1e-3,
+                     seed=1908, flags=0):
+        seqs, offsets = self._host_seqs(seqs, offsets)
+        pairs = self._host(pairs, np.int32, (-1, 2))
+        labels = self._host(labels, np.float32)
+        self._prep([seqs])
+        loss = np.zeros(1, np.float32)
+        _L.check(self._h, _L.lib().cm_ranker_train(
+            self._h, _ptr(seqs), _ptr(offsets), len(offsets) - 1, _ptr(pairs), _ptr(labels),
+            len(pairs), int(epochs), int(batch_pairs), float(lr), int(seed), _ptr(loss), flags))
+        return float(loss[0])
+
+    def ranker_embed(self, seqs, offsets, flags=0):
+        seqs, offsets = self._host_seqs(seqs, offsets)
+        self._prep([seqs])
+        out = np.empty((len(offsets) - 1, 128), np.float32)
+        _L.check(self._h, _L.lib().cm_ranker_embed(self._h, _ptr(seqs), _ptr(offsets),
+                                                   len(offsets) - 1, _ptr(out), flags))
+        return out
+
+    def ranker_logits(self, seqs, offsets, pairs, flags=0):
+        seqs, offsets = self._host_seqs(seqs, offsets)
+        pairs = self._host(pairs, np.int32, (-1, 2))
+        self._prep([seqs])
+        out = np.empty(len(pairs), np.float32)
+        _L.check(self._h, _L.lib().cm_ranker_logits(self._h, _ptr(seqs), _ptr(offsets),
+                                                    len(offsets) - 1, _ptr(pairs), len(pairs),
+                                                    _ptr(out), flags))
+        return out
 
 
 _default = {}
@@ -250,6 +319,7 @@ def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, c
     return cells_out
 
 
-def cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0):
+def cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
+                  use_ranker=False, prune_logit=0.0):
     return default_context().cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT,
-                                           mU, flags)
+                                           mU, flags, use_ranker, prune_logit)

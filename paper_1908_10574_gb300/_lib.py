@@ -35,7 +35,8 @@ class cm_stats(ctypes.Structure):
 
 class cm_params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("mT", ctypes.c_int32), ("mU", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("use_ranker", ctypes.c_int32), ("prune_logit", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class cm_result(ctypes.Structure):
@@ -53,7 +54,8 @@ class cm_result(ctypes.Structure):
                 ("rounds", ctypes.c_int64), ("gpu_batches", ctypes.c_int64),
                 ("exchange_waves", ctypes.c_int64), ("seconds", ctypes.c_double),
                 ("t_rep", ctypes.c_double), ("t_cells", ctypes.c_double),
-                ("t_exchange", ctypes.c_double), ("t_intra", ctypes.c_double)]
+                ("t_exchange", ctypes.c_double), ("t_intra", ctypes.c_double),
+                ("t_rank", ctypes.c_double), ("ranker_selected", ctypes.c_int64)]
 
 
 _lib = None
@@ -83,6 +85,16 @@ def lib():
         "cluster_merge": (ctypes.c_int, [p, p, p, i32, p, i32, i32, ctypes.POINTER(cm_params),
                                          ctypes.POINTER(ctypes.POINTER(cm_result)), u32]),
         "cm_result_free": (None, [ctypes.POINTER(cm_result)]),
+        "cm_ranker_num_params": (i64, []),
+        "cm_ranker_init": (ctypes.c_int, [p, ctypes.c_uint64]),
+        "cm_ranker_set_params": (ctypes.c_int, [p, p, i64]),
+        "cm_ranker_get_params": (ctypes.c_int, [p, p, i64]),
+        "cm_ranker_standardize": (ctypes.c_int, [p, p, p, i32, i32, u32]),
+        "cm_ranker_loss_grad": (ctypes.c_int, [p, p, p, i32, p, p, i64, p, p, u32]),
+        "cm_ranker_train": (ctypes.c_int, [p, p, p, i32, p, p, i64, i32, i32, ctypes.c_float,
+                                           ctypes.c_uint64, p, u32]),
+        "cm_ranker_embed": (ctypes.c_int, [p, p, p, i32, p, u32]),
+        "cm_ranker_logits": (ctypes.c_int, [p, p, p, i32, p, i64, p, u32]),
         "sw_cells_batch_noalloc": (ctypes.c_int, [p, p, i32, p, i64, p, i32, i32, p, p, u32,
                                                   ctypes.c_char_p, i32]),
     }

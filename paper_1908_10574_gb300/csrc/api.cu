@@ -66,7 +66,7 @@ int prepare(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_se
     const bool dev = (flags & CM_DEVICE_PTRS) != 0;
     if (!c) return CM_ERR_ARG;
     c->err.clear();
-    if (n_seqs < 0 || !offsets || !matrix) return fail(c, CM_ERR_ARG, "null argument or n_seqs < 0");
+    if (!matrix) return fail(c, CM_ERR_ARG, "null matrix");
     // gaps
     const int64_t g1 = (flags & CM_GAP_BLAST) ? (int64_t)gap_open + gap_extend : gap_open;
     if (g1 < 1 || g1 > 1000 || gap_extend < 0 || gap_extend > g1)
@@ -89,6 +89,16 @@ int prepare(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_se
             if (hm[x * 20 + y] != hm[y * 20 + x]) P.symmetric = false;
     P.beta = std::max<int32_t>(P.g1 + P.ge, -mn) + 1;
     P.sat_thr = 32767 - std::max(mx, 0);
+    return prepare_seqs(c, seqs, offsets, n_seqs, flags, P);
+}
+
+int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                 uint32_t flags, Prepared& P)
+{
+    const bool dev = (flags & CM_DEVICE_PTRS) != 0;
+    if (!c) return CM_ERR_ARG;
+    c->err.clear();
+    if (n_seqs < 0 || !offsets) return fail(c, CM_ERR_ARG, "null offsets or n_seqs < 0");
     // offsets
     P.hoff.resize((size_t)n_seqs + 1);
     if (dev) CUDA_TRY(cudaMemcpy(P.hoff.data(), offsets, sizeof(int64_t) * (n_seqs + 1),
@@ -505,6 +515,7 @@ void cm_destroy(cm_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& b : c->buf)
         if (b.p) cudaFree(b.p);
+    if (c->ranker && c->ranker_free) c->ranker_free(c->ranker);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->own) cudaStreamDestroy(c->own);

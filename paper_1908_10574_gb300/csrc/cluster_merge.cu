@@ -66,7 +66,9 @@ struct Driver {
     std::unordered_map<uint64_t, int32_t> memo;      // (member, rep) -> score
     int64_t rep_cmp = 0, exch_cmp = 0, full_merges = 0, exchanges = 0, scored = 0;
     int64_t cells_pairs = 0, batches = 0, rounds = 0, merges = 0, waves = 0;
-    double t_rep = 0, t_cells = 0, t_exch = 0, t_intra = 0;
+    double t_rep = 0, t_cells = 0, t_exch = 0, t_intra = 0, t_rank = 0;
+    void* U = nullptr;                               // ranker unit vectors (device), or null
+    int64_t selected = 0;
 
     Driver(cm_ctx* c_, const Prepared& P_, const cm_params& p, uint32_t f)
         : c(c_), P(P_), prm(p), flags(f) {}
@@ -85,38 +87,112 @@ struct Driver {
 int Driver::run_round(const std::vector<Merge>& ms)
 {
     const size_t nm = ms.size();
-    // ---- wave 1: every merge's rep x rep cross product (queries = cs1 reps by length) ----
-    std::vector<int32_t> ids;
-    std::vector<BlockReq> req(nm);
-    std::vector<std::vector<int32_t>> rowpos(nm);    // cs1 index -> row k in the block
-    for (size_t m = 0; m < nm; ++m) {
-        const auto& cs1 = sets[ms[m].left];
-        const auto& cs2 = sets[ms[m].right];
-        std::vector<int32_t> order(cs1.size());
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-            return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
-        });
-        rowpos[m].assign(cs1.size(), 0);
-        req[m].kind = kCross;
-        req[m].swap = 0;                              // pair (rep1, rep2)
-        req[m].a_begin = (int64_t)ids.size();
-        req[m].a_count = (int64_t)cs1.size();
-        for (size_t k = 0; k < order.size(); ++k) {
-            rowpos[m][order[k]] = (int32_t)k;
-            ids.push_back(arena[cs1[order[k]]].rep);
-        }
-        req[m].b_begin = (int64_t)ids.size();
-        req[m].b_count = (int64_t)cs2.size();
-        for (int32_t ci : cs2) ids.push_back(arena[ci].rep);
-    }
+    // ---- wave 1: rep x rep scores.  Plain: every merge's full cross product (one CROSS block
+    // per merge, queries = cs1 reps by length).  Ranker: only the pairs whose ranker logit
+    // reaches prune_logit, each cs1 rep's candidates in descending logit order. ----
     std::vector<int32_t> S;
     std::vector<int64_t> base;
+    std::vector<std::vector<int32_t>> rowpos(nm);    // cs1 index -> row k in the block
+    // ranker mode: per merge, per cs1 index, the ranked candidates (i2, score)
+    std::vector<std::vector<std::vector<std::pair<int32_t, int32_t>>>> cand(nm);
     double t0 = now_s();
-    int r = score_blocks(c, P, ids, req, S, base, flags);
-    if (r) return r;
+    int r;
+    if (!U) {
+        std::vector<int32_t> ids;
+        std::vector<BlockReq> req(nm);
+        for (size_t m = 0; m < nm; ++m) {
+            const auto& cs1 = sets[ms[m].left];
+            const auto& cs2 = sets[ms[m].right];
+            std::vector<int32_t> order(cs1.size());
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+                return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
+            });
+            rowpos[m].assign(cs1.size(), 0);
+            req[m].kind = kCross;
+            req[m].swap = 0;                              // pair (rep1, rep2)
+            req[m].a_begin = (int64_t)ids.size();
+            req[m].a_count = (int64_t)cs1.size();
+            for (size_t k = 0; k < order.size(); ++k) {
+                rowpos[m][order[k]] = (int32_t)k;
+                ids.push_back(arena[cs1[order[k]]].rep);
+            }
+            req[m].b_begin = (int64_t)ids.size();
+            req[m].b_count = (int64_t)cs2.size();
+            for (int32_t ci : cs2) ids.push_back(arena[ci].rep);
+        }
+        r = score_blocks(c, P, ids, req, S, base, flags);
+        if (r) return r;
+        scored += (int64_t)S.size();
+    } else {
+        std::vector<int32_t> rows;
+        std::vector<SelTile> tiles;
+        for (size_t m = 0; m < nm; ++m) {
+            const auto& cs1 = sets[ms[m].left];
+            const auto& cs2 = sets[ms[m].right];
+            const int32_t a0 = (int32_t)rows.size();
+            for (int32_t ci : cs1) rows.push_back(arena[ci].rep);
+            const int32_t b0 = (int32_t)rows.size();
+            for (int32_t ci : cs2) rows.push_back(arena[ci].rep);
+            for (int32_t i0 = 0; i0 < (int32_t)cs1.size(); i0 += 128)
+                for (int32_t j0 = 0; j0 < (int32_t)cs2.size(); j0 += 128) {
+                    SelTile t{};
+                    t.block = (int32_t)m;
+                    t.i0 = i0;
+                    t.j0 = j0;
+                    t.na = std::min<int32_t>(128, (int32_t)cs1.size() - i0);
+                    t.nb = std::min<int32_t>(128, (int32_t)cs2.size() - j0);
+                    t.a = a0 + i0;
+                    t.b = b0 + j0;
+                    tiles.push_back(t);
+                }
+        }
+        std::vector<SelPair> sel;
+        const double tr = now_s();
+        r = ranker_select(c, U, rows, tiles, prm.prune_logit, sel);
+        if (r) return r;
+        t_rank += now_s() - tr;
+        ++batches;
+        selected += (int64_t)sel.size();
+        std::sort(sel.begin(), sel.end(), [](const SelPair& x, const SelPair& y) {
+            if (x.block != y.block) return x.block < y.block;
+            if (x.i != y.i) return x.i < y.i;
+            if (x.logit != y.logit) return x.logit > y.logit;
+            return x.j < y.j;
+        });
+        // score the selected pairs: one CROSS block {rep1} x {its candidates}
+        std::vector<int32_t> ids;
+        std::vector<BlockReq> req;
+        std::vector<std::pair<int32_t, int32_t>> owner;     // (merge, i1) of each block
+        for (size_t q0 = 0; q0 < sel.size();) {
+            size_t q1 = q0;
+            while (q1 < sel.size() && sel[q1].block == sel[q0].block && sel[q1].i == sel[q0].i) ++q1;
+            const size_t m = (size_t)sel[q0].block;
+            BlockReq b{};
+            b.kind = kCross;
+            b.swap = 0;
+            b.a_begin = (int64_t)ids.size();
+            b.a_count = 1;
+            ids.push_back(arena[sets[ms[m].left][sel[q0].i]].rep);
+            b.b_begin = (int64_t)ids.size();
+            b.b_count = (int64_t)(q1 - q0);
+            for (size_t q = q0; q < q1; ++q) ids.push_back(arena[sets[ms[m].right][sel[q].j]].rep);
+            req.push_back(b);
+            owner.push_back({sel[q0].block, sel[q0].i});
+            q0 = q1;
+        }
+        r = score_blocks(c, P, ids, req, S, base, flags);
+        if (r) return r;
+        scored += (int64_t)S.size();
+        for (size_t m = 0; m < nm; ++m) cand[m].assign(sets[ms[m].left].size(), {});
+        size_t q = 0;
+        for (size_t bi = 0; bi < req.size(); ++bi) {
+            auto& lst = cand[owner[bi].first][owner[bi].second];
+            for (int64_t s2 = 0; s2 < req[bi].b_count; ++s2, ++q)
+                lst.push_back({sel[q].j, S[base[bi] + s2]});
+        }
+    }
     t_rep += now_s() - t0;
-    scored += (int64_t)S.size();
     ++batches;
     auto score_of = [&](size_t m, int32_t i1, int32_t i2) {
         return S[base[m] + (int64_t)rowpos[m][i1] * (int64_t)sets[ms[m].right].size() + i2];
@@ -128,15 +204,20 @@ int Driver::run_round(const std::vector<Merge>& ms)
     for (size_t m = 0; m < nm; ++m) {
         const auto& cs1 = sets[ms[m].left];
         const auto& cs2 = sets[ms[m].right];
-        for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1)
-            for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2) {
-                const int32_t s = score_of(m, i1, i2);
-                if (s > prm.T && s > prm.mT) {
-                    cidx[m].push_back({key2(i1, i2), (int64_t)cp.size() / 2});
-                    cp.push_back(arena[cs1[i1]].rep);
-                    cp.push_back(arena[cs2[i2]].rep);
-                }
+        auto add = [&](int32_t i1, int32_t i2, int32_t s) {
+            if (s > prm.T && s > prm.mT) {
+                cidx[m].push_back({key2(i1, i2), (int64_t)cp.size() / 2});
+                cp.push_back(arena[cs1[i1]].rep);
+                cp.push_back(arena[cs2[i2]].rep);
             }
+        };
+        for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
+            if (U) {
+                for (const auto& js : cand[m][i1]) add(i1, js.first, js.second);
+            } else {
+                for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2) add(i1, i2, score_of(m, i1, i2));
+            }
+        }
     }
     std::vector<int32_t> cells(cp.size() / 2 * 5);
     if (!cp.empty()) {
@@ -157,9 +238,11 @@ int Driver::run_round(const std::vector<Merge>& ms)
         std::unordered_map<uint64_t, int64_t> cmap(cidx[m].begin(), cidx[m].end());
         std::vector<char> merged1(cs1.size(), 0), merged2(cs2.size(), 0);
         for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
-            for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2) {
+            const int32_t nvisit = U ? (int32_t)cand[m][i1].size() : (int32_t)cs2.size();
+            for (int32_t q = 0; q < nvisit; ++q) {
+                const int32_t i2 = U ? cand[m][i1][q].first : q;
                 if (merged2[i2]) continue;
-                const int32_t s = score_of(m, i1, i2);
+                const int32_t s = U ? cand[m][i1][q].second : score_of(m, i1, i2);
                 ++rep_cmp;
                 if (s <= prm.T) continue;
                 bool t21 = false, t12 = false;
@@ -384,6 +467,8 @@ int Driver::finish(std::vector<int32_t>& final_set, cm_result* res)
     res->t_cells = t_cells;
     res->t_exchange = t_exch;
     res->t_intra = t_intra;
+    res->t_rank = t_rank;
+    res->ranker_selected = selected;
     return CM_OK;
 }
 
@@ -413,6 +498,12 @@ int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_
     if (!res) return fail(c, CM_ERR_OOM, "host allocation failed");
     res->n_seqs = n_seqs;
     Driver D(c, P, *params, dflags);
+    if (params->use_ranker) {
+        const double tr = now_s();
+        r = ranker_unit_vectors(c, P, n_seqs, &D.U);
+        if (r) { cm_result_free(res); return r; }
+        D.t_rank += now_s() - tr;
+    }
 
     // Algorithm 2: FIFO of singleton sets -> merge DAG -> dependency rounds
     D.arena.resize((size_t)n_seqs);

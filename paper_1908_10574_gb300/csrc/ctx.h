@@ -33,6 +33,8 @@ struct cm_ctx {
     int rows_per_warp = 4096;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cm::DevBuf buf[cm::B_COUNT];
+    void* ranker = nullptr;                 // learned ranker state (ranker.cu)
+    void (*ranker_free)(void*) = nullptr;
 };
 
 namespace cm {
@@ -80,6 +82,26 @@ int copy_in(cm_ctx* c, void* dst, const void* src, size_t bytes, bool dev);
 int prepare(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
             const int8_t* matrix, int32_t gap_open, int32_t gap_extend, uint32_t flags,
             Prepared& P);
+// sequences only (no matrix / gaps): validation and device staging
+int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                 uint32_t flags, Prepared& P);
+int ranker_embed_device(cm_ctx* c, const Prepared& P, const int32_t* ids, int64_t n, float* V);
+// one 128 x 128 tile of a pair-selection block: rows[a + i] x rows[b + j], i < na, j < nb
+struct SelTile {
+    int32_t block;
+    int32_t i0, j0;        // offsets of the tile inside its block
+    int32_t na, nb;        // valid rows / columns of the tile (<= 128)
+    int32_t a, b;          // first A row / B row of the tile in the row list
+    int32_t pad;
+};
+struct SelPair {
+    int32_t block, i, j;
+    float logit;
+};
+int ranker_unit_vectors(cm_ctx* c, const Prepared& P, int64_t n, void** U_out);
+int ranker_select(cm_ctx* c, const void* U, const std::vector<int32_t>& rows,
+                  const std::vector<SelTile>& tiles, float thr, std::vector<SelPair>& out);
+int ranker_alpha_beta(cm_ctx* c, float* ab);
 
 struct Plan {
     std::vector<SwBlock> blocks;

@@ -1,0 +1,1154 @@
+// Learned representative ranker: a small 1-D convolutional sequence embedding whose dot
+// products order and prune the representative comparisons of ClusterMerge; the exact
+// Smith-Waterman score remains the only judge of similarity.
+//
+// Network (per sequence of length L, rows = residues):
+//   X0 = E[code]                       (20 x 32 embedding)
+//   Z1 = relu(conv9(X0; W1 32->128) + b1)
+//   Z2 = relu(conv9(Z1; W2 128->128) + b2)
+//   Z3 = conv9(Z2; W3 128->128) + b3
+//   v  = mean over the L rows of Z3     (128-d)
+//   logit(a, b) = alpha * cos(v_a, v_b) + beta,  loss = BCE(sigmoid(logit), [score > T])
+// cm_ranker_standardize rescales W3, b3 so that every output channel of v has zero mean and
+// unit variance over a sample of the data (a data-dependent initialisation; without it the
+// pooled vectors share one large common component and the cosine hardly separates pairs).
+// conv9 is a width-9 "same" convolution.  A batch concatenates its sequences with kGap = 4
+// zero rows before, between and after them, so no output row ever reads another sequence.
+//
+// The convolutions run as implicit GEMMs on BF16 tensor cores with FP32 accumulation
+// (mma.sync m16n8k16, operands staged by cp.async double buffering and read with ldmatrix):
+//   forward      C[r, n]        = sum_k sum_c X[r+k-4, c] * W[k][c][n]
+//   backward dX  C[r, c]        = sum_k sum_n dY[r+k-4, n] * W[8-k][c][n]   (flipped weights)
+//   backward dW  C[(k, c), n]   = sum_r X[r+k-4, c] * dY[r, n]             (split over rows)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <random>
+
+#include <cuda_bf16.h>
+
+#include "ctx.h"
+
+namespace cm {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kGap = 4;
+constexpr int kEmb = 32, kCh = 128, kTaps = 9;
+// flat fp32 parameter vector layout
+constexpr int64_t kOffE = 0;
+constexpr int64_t kOffW1 = kOffE + 20 * kEmb;
+constexpr int64_t kOffB1 = kOffW1 + (int64_t)kTaps * kEmb * kCh;
+constexpr int64_t kOffW2 = kOffB1 + kCh;
+constexpr int64_t kOffB2 = kOffW2 + (int64_t)kTaps * kCh * kCh;
+constexpr int64_t kOffW3 = kOffB2 + kCh;
+constexpr int64_t kOffB3 = kOffW3 + (int64_t)kTaps * kCh * kCh;
+constexpr int64_t kOffAlpha = kOffB3 + kCh;
+constexpr int64_t kOffBeta = kOffAlpha + 1;
+constexpr int64_t kNumParams = kOffBeta + 1;
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
+                                        const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
+                                          const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------------------
+// Row-convolution GEMM (forward and backward-data).  One CTA = 128 rows x BN channels.
+enum Epi : int { kEpiRelu = 0, kEpiLinear = 1, kEpiGate = 2, kEpiF32 = 3 };
+
+constexpr int kBM = 128, kBK = 32, kAStr = kBK + 8;   // A tile row stride (halves)
+
+template <int CIN, int BN, int EPI>
+__global__ void __launch_bounds__(256) conv_rows_kernel(const bf16* __restrict__ X, int64_t R,
+                                                        const bf16* __restrict__ Wt,
+                                                        const float* __restrict__ bias,
+                                                        const int32_t* __restrict__ rowseq,
+                                                        const bf16* __restrict__ gate,
+                                                        bf16* __restrict__ out,
+                                                        float* __restrict__ out32)
+{
+    constexpr int WM = (BN == 128) ? 4 : 8, WN = 8 / WM;
+    constexpr int TM = kBM / WM, TN = BN / WN;          // warp tile
+    constexpr int MT = TM / 16, NT = TN / 8;
+    constexpr int BStr = BN + 8;
+    constexpr int KSTEPS = kTaps * (CIN / kBK);
+    __shared__ __align__(16) bf16 sA[2][kBM * kAStr];
+    __shared__ __align__(16) bf16 sB[2][kBK * BStr];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm0 = (warp % WM) * TM, wn0 = (warp / WM) * TN;
+    const int64_t row0 = (int64_t)blockIdx.x * kBM;
+
+    auto load = [&](int st, int s) {
+        const int k = s / (CIN / kBK), cb = (s % (CIN / kBK)) * kBK;
+        for (int id = tid; id < kBM * 4; id += 256) {
+            const int i = id >> 2, part = id & 3;
+            const int64_t src = row0 + i + k - 4;
+            const bool ok = src >= 0 && src < R;
+            const bf16* g = X + (ok ? src : 0) * CIN + cb + part * 8;
+            cp_async16(&sA[st][i * kAStr + part * 8], g, ok);
+        }
+        constexpr int CPR = BN / 8;                      // 16-byte chunks per B row
+        for (int id = tid; id < kBK * CPR; id += 256) {
+            const int kk = id / CPR, part = id % CPR;
+            const bf16* g = Wt + ((int64_t)(k * CIN + cb + kk)) * BN + part * 8;
+            cp_async16(&sB[st][kk * BStr + part * 8], g, true);
+        }
+        cp_commit();
+    };
+
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int b = 0; b < NT; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+
+    load(0, 0);
+    for (int s = 0; s < KSTEPS; ++s) {
+        const int st = s & 1;
+        if (s + 1 < KSTEPS) { load(st ^ 1, s + 1); cp_wait1(); } else { cp_wait0(); }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kBK; ks += 16) {
+            uint32_t af[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const bf16* p = &sA[st][(wm0 + mt * 16 + (lane & 15)) * kAStr + ks + (lane >> 4) * 8];
+                ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], p);
+            }
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {
+                uint32_t b0, b1, b2, b3;
+                const bf16* p = &sB[st][(ks + (lane & 7) + ((lane >> 3) & 1) * 8) * BStr +
+                                        wn0 + np * 16 + (lane >> 4) * 8];
+                ldsm_x4_t(b0, b1, b2, b3, p);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    mma_bf16(acc[mt][2 * np], af[mt], b0, b1);
+                    mma_bf16(acc[mt][2 * np + 1], af[mt], b2, b3);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t r = row0 + wm0 + mt * 16 + g + hh * 8;
+            if (r >= R) continue;
+            const bool real = rowseq[r] >= 0;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int n = wn0 + nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][2 * hh], v1 = acc[mt][nt][2 * hh + 1];
+                if (EPI == kEpiRelu || EPI == kEpiLinear) {
+                    v0 += bias[n];
+                    v1 += bias[n + 1];
+                    if (EPI == kEpiRelu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                } else if (EPI == kEpiGate) {
+                    const __nv_bfloat162 gz = *reinterpret_cast<const __nv_bfloat162*>(gate + r * BN + n);
+                    if (!(__bfloat162float(gz.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(gz.y) > 0.f)) v1 = 0.f;
+                }
+                if (!real) { v0 = 0.f; v1 = 0.f; }
+                if (EPI == kEpiF32) {
+                    *reinterpret_cast<float2*>(out32 + r * BN + n) = make_float2(v0, v1);
+                } else {
+                    *reinterpret_cast<__nv_bfloat162*>(out + r * BN + n) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+}
+
+// Weight gradient: part[chunk][(k, c)][n] = sum over the chunk's rows r of X[r+k-4, c] * dY[r, n].
+// One CTA = a 128-wide slice of the (k, c) axis x all 128 n, over `rows_per_chunk` rows.
+template <int CIN>
+__global__ void __launch_bounds__(256) conv_wgrad_kernel(const bf16* __restrict__ X,
+                                                         const bf16* __restrict__ dY, int64_t R,
+                                                         int64_t rows_per_chunk,
+                                                         float* __restrict__ part, int MPAD)
+{
+    constexpr int Str = 128 + 8;
+    __shared__ __align__(16) bf16 sA[2][kBK * Str];     // [rows][m]
+    __shared__ __align__(16) bf16 sB[2][kBK * Str];     // [rows][n]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm0 = (warp % 4) * 32, wn0 = (warp / 4) * 64;
+    const int mtile = blockIdx.x;
+    const int64_t chunk = blockIdx.y;
+    const int64_t rbeg = chunk * rows_per_chunk;
+    const int64_t rend = min(R, rbeg + rows_per_chunk);
+    const int nsteps = (int)((rend - rbeg + kBK - 1) / kBK);
+
+    auto load = [&](int st, int s) {
+        const int64_t r0 = rbeg + (int64_t)s * kBK;
+        for (int id = tid; id < kBK * 16; id += 256) {
+            const int i = id >> 4, part16 = id & 15;
+            // A: column m = mtile*128 + part16*8 .. +8 -> tap k, channel c
+            const int m = mtile * 128 + part16 * 8;
+            const int k = m / CIN, c = m % CIN;
+            const int64_t rr = r0 + i;
+            const int64_t src = rr + k - 4;
+            const bool okA = k < kTaps && rr < rend && src >= 0 && src < R;
+            cp_async16(&sA[st][i * Str + part16 * 8], X + (okA ? src : 0) * CIN + (okA ? c : 0), okA);
+            const bool okB = rr < rend;
+            cp_async16(&sB[st][i * Str + part16 * 8], dY + (okB ? rr : 0) * kCh + part16 * 8, okB);
+        }
+        cp_commit();
+    };
+
+    float acc[2][8][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+
+    if (nsteps > 0) load(0, 0);
+    for (int s = 0; s < nsteps; ++s) {
+        const int st = s & 1;
+        if (s + 1 < nsteps) { load(st ^ 1, s + 1); cp_wait1(); } else { cp_wait0(); }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kBK; ks += 16) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const bf16* p = &sA[st][(ks + (lane & 7) + (lane >> 4) * 8) * Str + wm0 + mt * 16 +
+                                        ((lane >> 3) & 1) * 8];
+                ldsm_x4_t(af[mt][0], af[mt][1], af[mt][2], af[mt][3], p);
+            }
+#pragma unroll
+            for (int np = 0; np < 4; ++np) {
+                uint32_t b0, b1, b2, b3;
+                const bf16* p = &sB[st][(ks + (lane & 7) + ((lane >> 3) & 1) * 8) * Str + wn0 +
+                                        np * 16 + (lane >> 4) * 8];
+                ldsm_x4_t(b0, b1, b2, b3, p);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_bf16(acc[mt][2 * np], af[mt], b0, b1);
+                    mma_bf16(acc[mt][2 * np + 1], af[mt], b2, b3);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+    float* dst = part + chunk * (int64_t)MPAD * kCh;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int m = mtile * 128 + wm0 + mt * 16 + g + hh * 8;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int n = wn0 + nt * 8 + 2 * t;
+                *reinterpret_cast<float2*>(dst + (int64_t)m * kCh + n) =
+                    make_float2(acc[mt][nt][2 * hh], acc[mt][nt][2 * hh + 1]);
+            }
+        }
+}
+
+// sum the per-chunk partials into the gradient vector (first M rows of the padded tile)
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int64_t nchunks, int MPAD,
+                                    int M, float* __restrict__ grad)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * kCh) return;
+    float s = 0.f;
+    for (int64_t c = 0; c < nchunks; ++c) s += part[c * (int64_t)MPAD * kCh + i];
+    grad[i] += s;
+}
+
+// column sums of dY over rows (bias gradient); rows of padding are zero already
+__global__ void bias_grad_kernel(const bf16* __restrict__ dY, int64_t R, float* __restrict__ db)
+{
+    const int n = threadIdx.x;
+    float s = 0.f;
+    for (int64_t r = blockIdx.x; r < R; r += gridDim.x) s += __bfloat162float(dY[r * kCh + n]);
+    atomicAdd(&db[n], s);
+}
+
+__global__ void embed_fwd_kernel(const uint8_t* __restrict__ codes, int64_t R,
+                                 const bf16* __restrict__ E, bf16* __restrict__ X0)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= R * kEmb) return;
+    const int64_t r = i / kEmb;
+    const int c = (int)(i % kEmb);
+    const uint8_t code = codes[r];
+    X0[i] = (code < 20) ? E[code * kEmb + c] : __float2bfloat16(0.f);
+}
+
+__global__ void embed_bwd_kernel(const uint8_t* __restrict__ codes, int64_t R,
+                                 const float* __restrict__ dX0, float* __restrict__ dE)
+{
+    __shared__ float h[20 * kEmb];
+    for (int i = threadIdx.x; i < 20 * kEmb; i += blockDim.x) h[i] = 0.f;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R * kEmb;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t code = codes[i / kEmb];
+        if (code < 20) atomicAdd(&h[code * kEmb + (int)(i % kEmb)], dX0[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 20 * kEmb; i += blockDim.x) atomicAdd(&dE[i], h[i]);
+}
+
+// v[s][n] = mean over the sequence's rows of Z3
+__global__ void pool_fwd_kernel(const bf16* __restrict__ Z3, const int64_t* __restrict__ srow,
+                                const int32_t* __restrict__ slen, float* __restrict__ v)
+{
+    const int s = blockIdx.x, n = threadIdx.x;
+    const int64_t r0 = srow[s];
+    const int L = slen[s];
+    float acc = 0.f;
+    for (int i = 0; i < L; ++i) acc += __bfloat162float(Z3[(r0 + i) * kCh + n]);
+    v[(int64_t)s * kCh + n] = L > 0 ? acc / (float)L : 0.f;
+}
+
+__global__ void pool_bwd_kernel(const float* __restrict__ dv, const int32_t* __restrict__ rowseq,
+                                const int32_t* __restrict__ slen, int64_t R, bf16* __restrict__ dZ)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= R * kCh) return;
+    const int32_t s = rowseq[i / kCh];
+    const int n = (int)(i % kCh);
+    dZ[i] = __float2bfloat16(s >= 0 ? dv[(int64_t)s * kCh + n] / (float)slen[s] : 0.f);
+}
+
+// one warp per pair: logit = alpha * cos(v_a, v_b) + beta, the loss and the gradients of v,
+// alpha and beta; cos = <a, b> / sqrt((|a|^2 + eps)(|b|^2 + eps))
+constexpr float kCosEps = 1e-6f;
+
+__global__ void head_kernel(const float* __restrict__ v, const int32_t* __restrict__ pidx,
+                            const float* __restrict__ y, int32_t npairs, const float* __restrict__ ab,
+                            float* __restrict__ logits, float* __restrict__ dv,
+                            float* __restrict__ gab, float* __restrict__ loss, int backward)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= npairs) return;
+    const int32_t ia = pidx[2 * p], ib = pidx[2 * p + 1];
+    const float* va = v + (int64_t)ia * kCh;
+    const float* vb = v + (int64_t)ib * kCh;
+    float d = 0.f, na = 0.f, nb = 0.f;
+    for (int n = lane; n < kCh; n += 32) {
+        d += va[n] * vb[n];
+        na += va[n] * va[n];
+        nb += vb[n] * vb[n];
+    }
+    for (int o = 16; o; o >>= 1) {
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+        na += __shfl_xor_sync(0xffffffffu, na, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    }
+    const float qa = na + kCosEps, qb = nb + kCosEps;
+    const float inv = rsqrtf(qa * qb);
+    const float cs = d * inv;
+    const float alpha = ab[0], beta = ab[1];
+    const float z = alpha * cs + beta;
+    if (lane == 0 && logits) logits[p] = z;
+    if (!backward) return;
+    const float yy = y[p];
+    const float pr = 1.f / (1.f + expf(-z));
+    const float l = fmaxf(z, 0.f) - z * yy + log1pf(expf(-fabsf(z)));   // stable BCE
+    const float gz = (pr - yy) / (float)npairs;
+    if (lane == 0) {
+        atomicAdd(loss, l / (float)npairs);
+        atomicAdd(&gab[0], gz * cs);
+        atomicAdd(&gab[1], gz);
+    }
+    // d cos / d a = b * inv - cos * a / qa   (and symmetrically for b)
+    const float ga = gz * alpha;
+    for (int n = lane; n < kCh; n += 32) {
+        atomicAdd(&dv[(int64_t)ia * kCh + n], ga * (vb[n] * inv - cs * va[n] / qa));
+        atomicAdd(&dv[(int64_t)ib * kCh + n], ga * (va[n] * inv - cs * vb[n] / qb));
+    }
+}
+
+__global__ void gather_rows_kernel(const uint8_t* __restrict__ db, const int64_t* __restrict__ off,
+                                   const int32_t* __restrict__ sid, const int64_t* __restrict__ srow,
+                                   const int32_t* __restrict__ slen, int32_t nseq,
+                                   uint8_t* __restrict__ codes, int32_t* __restrict__ rowseq)
+{
+    const int s = blockIdx.x;
+    if (s >= nseq) return;
+    const uint8_t* src = db + off[sid[s]];
+    const int64_t r0 = srow[s];
+    for (int i = threadIdx.x; i < slen[s]; i += blockDim.x) {
+        codes[r0 + i] = src[i];
+        rowseq[r0 + i] = s;
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
+                            float b1, float b2, float eps, float bc1, float bc2)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// bf16 operand copies: W[k][c][n] as stored, and flipped-transposed WTF[k][n][c] = W[8-k][c][n]
+__global__ void cast_weights_kernel(const float* __restrict__ W, int cin, bf16* __restrict__ Wb,
+                                    bf16* __restrict__ WTF)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)kTaps * cin * kCh;
+    if (i >= total) return;
+    const int k = (int)(i / ((int64_t)cin * kCh));
+    const int c = (int)((i / kCh) % cin);
+    const int n = (int)(i % kCh);
+    const bf16 b = __float2bfloat16(W[i]);
+    Wb[i] = b;
+    WTF[((int64_t)(kTaps - 1 - k) * kCh + n) * cin + c] = b;
+}
+
+__global__ void cast_kernel(const float* __restrict__ x, bf16* __restrict__ y, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// U[i] = bf16(v_i / sqrt(|v_i|^2 + eps)), so that alpha * <U_a, U_b> + beta is the logit
+__global__ void unit_rows_kernel(const float* __restrict__ V, int64_t n, bf16* __restrict__ U)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    float q = 0.f;
+    for (int c = lane; c < kCh; c += 32) q += V[i * kCh + c] * V[i * kCh + c];
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const float inv = rsqrtf(q + kCosEps);
+    for (int c = lane; c < kCh; c += 32) U[i * kCh + c] = __float2bfloat16(V[i * kCh + c] * inv);
+}
+
+// Pair selection: for every tile (block, 128 A rows x 128 B rows) compute the logits
+// alpha * <U_a, U_b> + beta on tensor cores and append the pairs at or above `thr`.
+__global__ void __launch_bounds__(256) pairsel_kernel(const bf16* __restrict__ U,
+                                                      const int32_t* __restrict__ rows,
+                                                      const SelTile* __restrict__ tiles,
+                                                      const float* __restrict__ ab, float thr,
+                                                      SelPair* __restrict__ out, int32_t cap,
+                                                      int32_t* __restrict__ count)
+{
+    constexpr int Str = kCh + 8;
+    __shared__ __align__(16) bf16 sA[128 * Str];
+    __shared__ __align__(16) bf16 sB[128 * Str];
+    const SelTile T = tiles[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int id = tid; id < 128 * 16; id += 256) {
+        const int i = id >> 4, part = id & 15;
+        const bool oka = i < T.na, okb = i < T.nb;
+        const int32_t ra = oka ? rows[T.a + i] : 0, rb = okb ? rows[T.b + i] : 0;
+        cp_async16(&sA[i * Str + part * 8], U + (int64_t)ra * kCh + part * 8, oka);
+        cp_async16(&sB[i * Str + part * 8], U + (int64_t)rb * kCh + part * 8, okb);
+    }
+    cp_commit();
+    cp_wait0();
+    __syncthreads();
+    const int wm0 = (warp % 4) * 32, wn0 = (warp / 4) * 64;
+    float acc[2][8][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < kCh; ks += 16) {
+        uint32_t af[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+            ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
+                    &sA[(wm0 + mt * 16 + (lane & 15)) * Str + ks + (lane >> 4) * 8]);
+#pragma unroll
+        for (int np = 0; np < 4; ++np) {
+            uint32_t b0, b1, b2, b3;
+            ldsm_x4(b0, b1, b2, b3,
+                    &sB[(wn0 + np * 16 + (lane & 7) + (lane >> 4) * 8) * Str + ks +
+                        ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                mma_bf16(acc[mt][2 * np], af[mt], b0, b1);
+                mma_bf16(acc[mt][2 * np + 1], af[mt], b2, b3);
+            }
+        }
+    }
+    const float alpha = ab[0], beta = ab[1];
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int i = wm0 + mt * 16 + g + (q >> 1) * 8;
+                const int j = wn0 + nt * 8 + 2 * t + (q & 1);
+                const float z = alpha * acc[mt][nt][q] + beta;
+                if (i < T.na && j < T.nb && z >= thr) {
+                    const int32_t k = atomicAdd(count, 1);
+                    if (k < cap) {
+                        SelPair sp;
+                        sp.block = T.block;
+                        sp.i = T.i0 + i;
+                        sp.j = T.j0 + j;
+                        sp.logit = z;
+                        out[k] = sp;
+                    }
+                }
+            }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Host side
+struct Ranker {
+    float* params = nullptr;      // fp32 master (kNumParams)
+    float* grad = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    bf16* E = nullptr;
+    bf16* W1 = nullptr; bf16* W1T = nullptr;
+    bf16* W2 = nullptr; bf16* W2T = nullptr;
+    bf16* W3 = nullptr; bf16* W3T = nullptr;
+    int64_t step = 0;
+    bool ready = false;
+    // activation buffers (grown on demand)
+    DevBuf act[16];
+};
+
+enum ActId { A_CODES, A_ROWSEQ, A_X0, A_Z1, A_Z2, A_Z3, A_DZ, A_DY2, A_DX0, A_PART, A_V, A_DV,
+             A_SEQ, A_PIDX, A_Y, A_LOGIT };
+
+namespace {
+
+int act_ensure(cm_ctx* c, Ranker* K, int id, size_t bytes, void** out)
+{
+    DevBuf& b = K->act[id];
+    if (bytes < 256) bytes = 256;
+    if (bytes > b.cap) {
+        if (b.p) { cudaStreamSynchronize(c->stream); cudaFree(b.p); }
+        const size_t want = std::max(bytes, b.cap + b.cap / 2);
+        b.p = nullptr;
+        b.cap = 0;
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CM_ERR_OOM, "ranker activation allocation failed");
+        }
+        b.cap = want;
+    }
+    *out = b.p;
+    return CM_OK;
+}
+
+#define AENSURE(id, bytes, ptr)                                                             \
+    do {                                                                                    \
+        void* p_;                                                                           \
+        int r_ = act_ensure(c, K, id, (size_t)(bytes), &p_);                                \
+        if (r_) return r_;                                                                  \
+        ptr = reinterpret_cast<decltype(ptr)>(p_);                                          \
+    } while (0)
+
+void ranker_free(void* p)
+{
+    Ranker* K = static_cast<Ranker*>(p);
+    if (!K) return;
+    cudaFree(K->params); cudaFree(K->grad); cudaFree(K->m); cudaFree(K->v);
+    cudaFree(K->E); cudaFree(K->W1); cudaFree(K->W1T); cudaFree(K->W2); cudaFree(K->W2T);
+    cudaFree(K->W3); cudaFree(K->W3T);
+    for (auto& b : K->act) if (b.p) cudaFree(b.p);
+    delete K;
+}
+
+int get_ranker(cm_ctx* c, Ranker** out)
+{
+    if (!c->ranker) {
+        Ranker* K = new (std::nothrow) Ranker();
+        if (!K) return fail(c, CM_ERR_OOM, "host allocation failed");
+        c->ranker = K;
+        c->ranker_free = ranker_free;
+        const size_t nb = kNumParams * sizeof(float);
+        CUDA_TRY(cudaMalloc(&K->params, nb));
+        CUDA_TRY(cudaMalloc(&K->grad, nb));
+        CUDA_TRY(cudaMalloc(&K->m, nb));
+        CUDA_TRY(cudaMalloc(&K->v, nb));
+        CUDA_TRY(cudaMalloc(&K->E, 20 * kEmb * sizeof(bf16)));
+        const size_t w1 = (size_t)kTaps * kEmb * kCh * sizeof(bf16);
+        const size_t w2 = (size_t)kTaps * kCh * kCh * sizeof(bf16);
+        CUDA_TRY(cudaMalloc(&K->W1, w1)); CUDA_TRY(cudaMalloc(&K->W1T, w1));
+        CUDA_TRY(cudaMalloc(&K->W2, w2)); CUDA_TRY(cudaMalloc(&K->W2T, w2));
+        CUDA_TRY(cudaMalloc(&K->W3, w2)); CUDA_TRY(cudaMalloc(&K->W3T, w2));
+    }
+    *out = static_cast<Ranker*>(c->ranker);
+    return CM_OK;
+}
+
+int refresh_bf16(cm_ctx* c, Ranker* K)
+{
+    const cudaStream_t st = c->stream;
+    cast_kernel<<<blocks_for(20 * kEmb, 256), 256, 0, st>>>(K->params + kOffE, K->E, 20 * kEmb);
+    cast_weights_kernel<<<blocks_for((int64_t)kTaps * kEmb * kCh, 256), 256, 0, st>>>(
+        K->params + kOffW1, kEmb, K->W1, K->W1T);
+    cast_weights_kernel<<<blocks_for((int64_t)kTaps * kCh * kCh, 256), 256, 0, st>>>(
+        K->params + kOffW2, kCh, K->W2, K->W2T);
+    cast_weights_kernel<<<blocks_for((int64_t)kTaps * kCh * kCh, 256), 256, 0, st>>>(
+        K->params + kOffW3, kCh, K->W3, K->W3T);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 4;
+    return CM_OK;
+}
+
+// A batch of distinct sequences laid out as rows with kGap zero rows around each.
+struct Batch {
+    std::vector<int32_t> sid;     // sequence ids
+    std::vector<int64_t> srow;    // first row of each sequence
+    std::vector<int32_t> slen;
+    int64_t R = 0;
+};
+
+void layout(const Prepared& P, const int32_t* ids, int64_t n, Batch& B)
+{
+    B.sid.assign(ids, ids + n);
+    B.srow.resize((size_t)n);
+    B.slen.resize((size_t)n);
+    int64_t r = kGap;
+    for (int64_t i = 0; i < n; ++i) {
+        B.srow[i] = r;
+        B.slen[i] = (int32_t)P.len(ids[i]);
+        r += B.slen[i] + kGap;
+    }
+    B.R = r;
+}
+
+// forward over a batch; leaves X0, Z1, Z2, Z3 and the pooled vectors V on the device
+int forward(cm_ctx* c, const Prepared& P, Ranker* K, const Batch& B, float** V_out)
+{
+    const cudaStream_t st = c->stream;
+    const int64_t R = B.R, ns = (int64_t)B.sid.size();
+    uint8_t* codes; int32_t* rowseq; bf16 *X0, *Z1, *Z2, *Z3; float* V;
+    int32_t* seqinfo;
+    AENSURE(A_CODES, R, codes);
+    AENSURE(A_ROWSEQ, R * 4, rowseq);
+    AENSURE(A_X0, R * kEmb * 2, X0);
+    AENSURE(A_Z1, R * kCh * 2, Z1);
+    AENSURE(A_Z2, R * kCh * 2, Z2);
+    AENSURE(A_Z3, R * kCh * 2, Z3);
+    AENSURE(A_V, ns * kCh * 4, V);
+    AENSURE(A_SEQ, ns * 16 + 64, seqinfo);
+    int32_t* d_sid = seqinfo;
+    int64_t* d_srow = reinterpret_cast<int64_t*>(seqinfo + ((ns + 1) & ~1LL));
+    int32_t* d_slen = reinterpret_cast<int32_t*>(d_srow + ns);
+    int r;
+    if ((r = copy_in(c, d_sid, B.sid.data(), ns * 4, false))) return r;
+    if ((r = copy_in(c, d_srow, B.srow.data(), ns * 8, false))) return r;
+    if ((r = copy_in(c, d_slen, B.slen.data(), ns * 4, false))) return r;
+    CUDA_TRY(cudaMemsetAsync(codes, 0xff, R, st));
+    CUDA_TRY(cudaMemsetAsync(rowseq, 0xff, R * 4, st));
+    gather_rows_kernel<<<(unsigned)ns, 128, 0, st>>>(P.db, P.off, d_sid, d_srow, d_slen, (int32_t)ns,
+                                                     codes, rowseq);
+    embed_fwd_kernel<<<blocks_for(R * kEmb, 256), 256, 0, st>>>(codes, R, K->E, X0);
+    const unsigned g = blocks_for(R, kBM);
+    conv_rows_kernel<kEmb, kCh, kEpiRelu><<<g, 256, 0, st>>>(X0, R, K->W1, K->params + kOffB1,
+                                                             rowseq, nullptr, Z1, nullptr);
+    conv_rows_kernel<kCh, kCh, kEpiRelu><<<g, 256, 0, st>>>(Z1, R, K->W2, K->params + kOffB2,
+                                                            rowseq, nullptr, Z2, nullptr);
+    conv_rows_kernel<kCh, kCh, kEpiLinear><<<g, 256, 0, st>>>(Z2, R, K->W3, K->params + kOffB3,
+                                                              rowseq, nullptr, Z3, nullptr);
+    pool_fwd_kernel<<<(unsigned)ns, kCh, 0, st>>>(Z3, d_srow, d_slen, V);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 6;
+    *V_out = V;
+    return CM_OK;
+}
+
+template <int CIN>
+int wgrad(cm_ctx* c, Ranker* K, const bf16* X, const bf16* dY, int64_t R, float* dW)
+{
+    const int M = kTaps * CIN;
+    const int mtiles = (M + 127) / 128, MPAD = mtiles * 128;
+    const int64_t rpc = 4096;
+    const int64_t nch = std::max<int64_t>(1, (R + rpc - 1) / rpc);
+    float* part;
+    AENSURE(A_PART, nch * MPAD * kCh * 4, part);
+    dim3 grid(mtiles, (unsigned)nch);
+    conv_wgrad_kernel<CIN><<<grid, 256, 0, c->stream>>>(X, dY, R, rpc, part, MPAD);
+    reduce_parts_kernel<<<blocks_for((int64_t)M * kCh, 256), 256, 0, c->stream>>>(part, nch, MPAD, M, dW);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 2;
+    return CM_OK;
+}
+
+// loss and gradient (accumulated into K->grad, which the caller zeroes) of a batch of pairs
+int loss_grad(cm_ctx* c, const Prepared& P, Ranker* K, const int32_t* pairs, const float* labels,
+              int64_t npairs, float* loss_out)
+{
+    const cudaStream_t st = c->stream;
+    // distinct sequences of the batch
+    std::vector<int32_t> ids(pairs, pairs + 2 * npairs);
+    std::vector<int32_t> uniq = ids;
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    std::vector<int32_t> pidx((size_t)npairs * 2);
+    for (int64_t i = 0; i < 2 * npairs; ++i)
+        pidx[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), ids[i]) - uniq.begin());
+    Batch B;
+    layout(P, uniq.data(), (int64_t)uniq.size(), B);
+    float* V;
+    int r = forward(c, P, K, B, &V);
+    if (r) return r;
+    const int64_t R = B.R, ns = (int64_t)uniq.size();
+    int32_t* d_pidx; float *d_y, *dv, *d_loss;
+    AENSURE(A_PIDX, npairs * 8, d_pidx);
+    AENSURE(A_Y, npairs * 4 + 64, d_y);
+    AENSURE(A_DV, ns * kCh * 4, dv);
+    d_loss = d_y + ((npairs + 15) & ~15LL);
+    if ((r = copy_in(c, d_pidx, pidx.data(), npairs * 8, false))) return r;
+    if ((r = copy_in(c, d_y, labels, npairs * 4, false))) return r;
+    CUDA_TRY(cudaMemsetAsync(dv, 0, ns * kCh * 4, st));
+    CUDA_TRY(cudaMemsetAsync(d_loss, 0, 4, st));
+    head_kernel<<<blocks_for(npairs * 32, 256), 256, 0, st>>>(V, d_pidx, d_y, (int32_t)npairs,
+                                                              K->params + kOffAlpha, nullptr, dv,
+                                                              K->grad + kOffAlpha, d_loss, 1);
+    uint8_t* codes = (uint8_t*)K->act[A_CODES].p;
+    int32_t* rowseq = (int32_t*)K->act[A_ROWSEQ].p;
+    bf16* X0 = (bf16*)K->act[A_X0].p;
+    bf16* Z1 = (bf16*)K->act[A_Z1].p;
+    bf16* Z2 = (bf16*)K->act[A_Z2].p;
+    bf16 *dZ, *dY2; float* dX0;
+    AENSURE(A_DZ, R * kCh * 2, dZ);
+    AENSURE(A_DY2, R * kCh * 2, dY2);
+    AENSURE(A_DX0, R * kEmb * 4, dX0);
+    int32_t* d_slen = reinterpret_cast<int32_t*>(
+        reinterpret_cast<int64_t*>((int32_t*)K->act[A_SEQ].p + ((ns + 1) & ~1LL)) + ns);
+    pool_bwd_kernel<<<blocks_for(R * kCh, 256), 256, 0, st>>>(dv, rowseq, d_slen, R, dZ);   // dY3
+    const unsigned g = blocks_for(R, kBM);
+    const unsigned gb = (unsigned)std::min<int64_t>(R, 1024);
+    // layer 3 (linear)
+    bias_grad_kernel<<<gb, kCh, 0, st>>>(dZ, R, K->grad + kOffB3);
+    if ((r = wgrad<kCh>(c, K, Z2, dZ, R, K->grad + kOffW3))) return r;
+    conv_rows_kernel<kCh, kCh, kEpiGate><<<g, 256, 0, st>>>(dZ, R, K->W3T, nullptr, rowseq, Z2,
+                                                            dY2, nullptr);           // dY2
+    // layer 2
+    bias_grad_kernel<<<gb, kCh, 0, st>>>(dY2, R, K->grad + kOffB2);
+    if ((r = wgrad<kCh>(c, K, Z1, dY2, R, K->grad + kOffW2))) return r;
+    conv_rows_kernel<kCh, kCh, kEpiGate><<<g, 256, 0, st>>>(dY2, R, K->W2T, nullptr, rowseq, Z1,
+                                                            dZ, nullptr);            // dY1
+    // layer 1
+    bias_grad_kernel<<<gb, kCh, 0, st>>>(dZ, R, K->grad + kOffB1);
+    if ((r = wgrad<kEmb>(c, K, X0, dZ, R, K->grad + kOffW1))) return r;
+    conv_rows_kernel<kCh, kEmb, kEpiF32><<<g, 256, 0, st>>>(dZ, R, K->W1T, nullptr, rowseq,
+                                                            nullptr, nullptr, dX0);
+    embed_bwd_kernel<<<std::min<unsigned>(blocks_for(R * kEmb, 256), 1024), 256, 0, st>>>(
+        codes, R, dX0, K->grad + kOffE);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 12;
+    if (loss_out) {
+        CUDA_TRY(cudaMemcpyAsync(loss_out, d_loss, 4, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return CM_OK;
+}
+
+}  // namespace
+
+// pooled 128-d vectors of `n` sequences (host ids) into device memory V (n x 128, fp32)
+int ranker_embed_device(cm_ctx* c, const Prepared& P, const int32_t* ids, int64_t n, float* V)
+{
+    Ranker* K;
+    int r = get_ranker(c, &K);
+    if (r) return r;
+    if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters (init, train or load first)");
+    const int64_t max_rows = (int64_t)1 << 22;   // activation budget per chunk
+    int64_t i = 0;
+    while (i < n) {
+        int64_t j = i, rows = kGap;
+        while (j < n && (j == i || rows + P.len(ids[j]) + kGap <= max_rows)) {
+            rows += P.len(ids[j]) + kGap;
+            ++j;
+        }
+        Batch B;
+        layout(P, ids + i, j - i, B);
+        float* Vc;
+        if ((r = forward(c, P, K, B, &Vc))) return r;
+        CUDA_TRY(cudaMemcpyAsync(V + i * kCh, Vc, (j - i) * kCh * 4, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        i = j;
+    }
+    return CM_OK;
+}
+
+int ranker_alpha_beta(cm_ctx* c, float* ab)
+{
+    Ranker* K;
+    int r = get_ranker(c, &K);
+    if (r) return r;
+    CUDA_TRY(cudaMemcpy(ab, K->params + kOffAlpha, 8, cudaMemcpyDeviceToHost));
+    return CM_OK;
+}
+
+// Logits of every (A row, B row) pair of the tiles at or above thr; returns them unsorted.
+int ranker_select(cm_ctx* c, const void* Uv, const std::vector<int32_t>& rows,
+                  const std::vector<SelTile>& tiles, float thr, std::vector<SelPair>& out)
+{
+    const bf16* U = static_cast<const bf16*>(Uv);
+    out.clear();
+    if (tiles.empty()) return CM_OK;
+    Ranker* K;
+    int r = get_ranker(c, &K);
+    if (r) return r;
+    int32_t* d_rows;
+    SelTile* d_tiles;
+    SelPair* d_out;
+    int32_t* d_cnt;
+    AENSURE(A_PIDX, rows.size() * 4, d_rows);
+    AENSURE(A_Y, tiles.size() * sizeof(SelTile), d_tiles);
+    AENSURE(A_DV, 64, d_cnt);
+    int32_t cap = 1 << 20;
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        AENSURE(A_LOGIT, (size_t)cap * sizeof(SelPair), d_out);
+        if ((r = copy_in(c, d_rows, rows.data(), rows.size() * 4, false))) return r;
+        if ((r = copy_in(c, d_tiles, tiles.data(), tiles.size() * sizeof(SelTile), false))) return r;
+        CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 4, c->stream));
+        for (size_t t0 = 0; t0 < tiles.size(); t0 += 65535) {
+            const unsigned nt = (unsigned)std::min<size_t>(65535, tiles.size() - t0);
+            pairsel_kernel<<<nt, 256, 0, c->stream>>>(U, d_rows, d_tiles + t0, K->params + kOffAlpha,
+                                                      thr, d_out, cap, d_cnt);
+            c->stats.launches += 1;
+        }
+        CUDA_TRY(cudaGetLastError());
+        int32_t n = 0;
+        CUDA_TRY(cudaMemcpyAsync(&n, d_cnt, 4, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (n <= cap) {
+            out.resize((size_t)n);
+            CUDA_TRY(cudaMemcpy(out.data(), d_out, (size_t)n * sizeof(SelPair), cudaMemcpyDeviceToHost));
+            return CM_OK;
+        }
+        cap = n;
+    }
+    return fail(c, CM_ERR_INTERNAL, "pair selection did not fit");
+}
+
+// unit rows U (bf16, n x 128) of the ranker vectors of all n sequences, in device memory
+int ranker_unit_vectors(cm_ctx* c, const Prepared& P, int64_t n, void** U_out)
+{
+    Ranker* K;
+    int r = get_ranker(c, &K);
+    if (r) return r;
+    float* V;
+    bf16* U;
+    void* pv;
+    if ((r = ensure_bytes(c, B_RES, (size_t)n * kCh * 4, &pv))) return r;
+    V = static_cast<float*>(pv);
+    std::vector<int32_t> ids((size_t)n);
+    std::iota(ids.begin(), ids.end(), 0);
+    if ((r = ranker_embed_device(c, P, ids.data(), n, V))) return r;
+    if ((r = ensure_bytes(c, B_SCRATCH, (size_t)n * kCh * 2, &pv))) return r;
+    U = static_cast<bf16*>(pv);
+    unit_rows_kernel<<<blocks_for(n * 32, 256), 256, 0, c->stream>>>(V, n, U);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 1;
+    *U_out = U;
+    return CM_OK;
+}
+
+
+}  // namespace cm
+
+using namespace cm;
+
+namespace {
+
+int set_params_host(cm_ctx* c, Ranker* K, const float* h)
+{
+    CUDA_TRY(cudaMemcpyAsync(K->params, h, kNumParams * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(K->m, 0, kNumParams * 4, c->stream));
+    CUDA_TRY(cudaMemsetAsync(K->v, 0, kNumParams * 4, c->stream));
+    K->step = 0;
+    int r = refresh_bf16(c, K);
+    if (r) return r;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    K->ready = true;
+    return CM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t cm_ranker_num_params(void) { return kNumParams; }
+
+int cm_ranker_init(cm_ctx* c, uint64_t seed)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    Ranker* K;
+    int r = get_ranker(c, &K);
+    if (r) return r;
+    std::vector<float> h((size_t)kNumParams, 0.f);
+    std::mt19937_64 g(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    auto fill = [&](int64_t off, int64_t n, float sd) {
+        for (int64_t i = 0; i < n; ++i) h[off + i] = nd(g) * sd;
+    };
+    fill(kOffE, 20 * kEmb, 1.0f);
+    fill(kOffW1, (int64_t)kTaps * kEmb * kCh, std::sqrt(2.f / (kTaps * kEmb)));
+    fill(kOffW2, (int64_t)kTaps * kCh * kCh, std::sqrt(2.f / (kTaps * kCh)));
+    fill(kOffW3, (int64_t)kTaps * kCh * kCh, std::sqrt(1.f / (kTaps * kCh)));
+    h[kOffAlpha] = 10.f;
+    h[kOffBeta] = -2.f;
+    return set_params_host(c, K, h.data());
+}
+
+int cm_ranker_set_params(cm_ctx* c, const float* params, int64_t n)
+{
+    if (!c || !params || n != kNumParams) return c ? fail(c, CM_ERR_ARG, "expected cm_ranker_num_params() floats") : CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    Ranker* K;
+    int r = get_ranker(c, &K);
+    if (r) return r;
+    return set_params_host(c, K, params);
+}
+
+int cm_ranker_get_params(cm_ctx* c, float* params, int64_t n)
+{
+    if (!c || !params || n != kNumParams) return c ? fail(c, CM_ERR_ARG, "expected cm_ranker_num_params() floats") : CM_ERR_ARG;
+    Ranker* K;
+    int r = get_ranker(c, &K);
+    if (r) return r;
+    if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters");
+    CUDA_TRY(cudaMemcpy(params, K->params, kNumParams * 4, cudaMemcpyDeviceToHost));
+    return CM_OK;
+}
+
+int cm_ranker_loss_grad(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                        const int32_t* pairs, const float* labels, int64_t n_pairs,
+                        float* loss, float* grad, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (flags & CM_DEVICE_PTRS) return fail(c, CM_ERR_ARG, "host pointers only");
+    if (n_pairs < 1 || !pairs || !labels || !loss) return fail(c, CM_ERR_ARG, "bad pairs");
+    Prepared P;
+    int r = prepare_seqs(c, seqs, offsets, n_seqs, flags, P);
+    if (r) return r;
+    for (int64_t k = 0; k < 2 * n_pairs; ++k)
+        if (pairs[k] < 0 || pairs[k] >= n_seqs) return fail(c, CM_ERR_ARG, "pair index out of range");
+    Ranker* K;
+    if ((r = get_ranker(c, &K))) return r;
+    if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters");
+    CUDA_TRY(cudaMemsetAsync(K->grad, 0, kNumParams * 4, c->stream));
+    if ((r = loss_grad(c, P, K, pairs, labels, n_pairs, loss))) return r;
+    if (grad) CUDA_TRY(cudaMemcpy(grad, K->grad, kNumParams * 4, cudaMemcpyDeviceToHost));
+    return CM_OK;
+}
+
+int cm_ranker_train(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                    const int32_t* pairs, const float* labels, int64_t n_pairs, int32_t epochs,
+                    int32_t batch_pairs, float lr, uint64_t seed, float* last_loss, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (flags & CM_DEVICE_PTRS) return fail(c, CM_ERR_ARG, "host pointers only");
+    if (n_pairs < 1 || !pairs || !labels || epochs < 1 || batch_pairs < 1 || !(lr > 0.f))
+        return fail(c, CM_ERR_ARG, "bad training arguments");
+    Prepared P;
+    int r = prepare_seqs(c, seqs, offsets, n_seqs, flags, P);
+    if (r) return r;
+    for (int64_t k = 0; k < 2 * n_pairs; ++k)
+        if (pairs[k] < 0 || pairs[k] >= n_seqs) return fail(c, CM_ERR_ARG, "pair index out of range");
+    Ranker* K;
+    if ((r = get_ranker(c, &K))) return r;
+    if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters (call cm_ranker_init)");
+    std::vector<int64_t> order((size_t)n_pairs);
+    std::iota(order.begin(), order.end(), 0);
+    std::mt19937_64 g(seed);
+    std::vector<int32_t> bp;
+    std::vector<float> by;
+    float loss = 0.f;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(order.begin(), order.end(), g);
+        for (int64_t s = 0; s < n_pairs; s += batch_pairs) {
+            const int64_t e = std::min<int64_t>(n_pairs, s + batch_pairs);
+            bp.resize((size_t)(e - s) * 2);
+            by.resize((size_t)(e - s));
+            for (int64_t i = s; i < e; ++i) {
+                bp[2 * (i - s)] = pairs[2 * order[i]];
+                bp[2 * (i - s) + 1] = pairs[2 * order[i] + 1];
+                by[i - s] = labels[order[i]];
+            }
+            CUDA_TRY(cudaMemsetAsync(K->grad, 0, kNumParams * 4, c->stream));
+            const bool last = (ep == epochs - 1) && (e == n_pairs);
+            if ((r = loss_grad(c, P, K, bp.data(), by.data(), e - s, last ? &loss : nullptr))) return r;
+            ++K->step;
+            const float bc1 = 1.f - std::pow(b1, (float)K->step), bc2 = 1.f - std::pow(b2, (float)K->step);
+            adam_kernel<<<blocks_for(kNumParams, 256), 256, 0, c->stream>>>(
+                K->params, K->grad, K->m, K->v, kNumParams, lr, b1, b2, eps, bc1, bc2);
+            CUDA_TRY(cudaGetLastError());
+            c->stats.launches += 1;
+            if ((r = refresh_bf16(c, K))) return r;
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (last_loss) *last_loss = loss;
+    return CM_OK;
+}
+
+int cm_ranker_standardize(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets,
+                          int32_t n_seqs, int32_t max_sample, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (flags & CM_DEVICE_PTRS) return fail(c, CM_ERR_ARG, "host pointers only");
+    if (n_seqs < 2 || max_sample < 2) return fail(c, CM_ERR_ARG, "need at least 2 sequences");
+    Prepared P;
+    int r = prepare_seqs(c, seqs, offsets, n_seqs, flags, P);
+    if (r) return r;
+    Ranker* K;
+    if ((r = get_ranker(c, &K))) return r;
+    if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters");
+    // evenly spaced sample of the set
+    const int64_t ns = std::min<int64_t>(n_seqs, max_sample);
+    std::vector<int32_t> ids((size_t)ns);
+    for (int64_t i = 0; i < ns; ++i) ids[i] = (int32_t)(i * (int64_t)n_seqs / ns);
+    void* pv;
+    if ((r = ensure_bytes(c, B_RES, (size_t)ns * kCh * 4, &pv))) return r;
+    if ((r = ranker_embed_device(c, P, ids.data(), ns, static_cast<float*>(pv)))) return r;
+    std::vector<float> V((size_t)ns * kCh);
+    CUDA_TRY(cudaMemcpyAsync(V.data(), pv, V.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<float> h((size_t)kNumParams);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), K->params, kNumParams * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int n = 0; n < kCh; ++n) {
+        double mu = 0, sq = 0;
+        for (int64_t i = 0; i < ns; ++i) mu += V[i * kCh + n];
+        mu /= (double)ns;
+        for (int64_t i = 0; i < ns; ++i) sq += (V[i * kCh + n] - mu) * (V[i * kCh + n] - mu);
+        const double sd = std::sqrt(sq / (double)(ns - 1)) + 1e-6;
+        for (int64_t q = 0; q < (int64_t)kTaps * kCh; ++q) h[kOffW3 + q * kCh + n] /= (float)sd;
+        h[kOffB3 + n] = (float)((h[kOffB3 + n] - mu) / sd);
+    }
+    return set_params_host(c, K, h.data());
+}
+
+int cm_ranker_logits(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                     const int32_t* pairs, int64_t n_pairs, float* out, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (flags & CM_DEVICE_PTRS) return fail(c, CM_ERR_ARG, "host pointers only");
+    if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !out))) return fail(c, CM_ERR_ARG, "bad pairs");
+    Prepared P;
+    int r = prepare_seqs(c, seqs, offsets, n_seqs, flags, P);
+    if (r) return r;
+    if (n_pairs == 0) return CM_OK;
+    for (int64_t k = 0; k < 2 * n_pairs; ++k)
+        if (pairs[k] < 0 || pairs[k] >= n_seqs) return fail(c, CM_ERR_ARG, "pair index out of range");
+    Ranker* K;
+    if ((r = get_ranker(c, &K))) return r;
+    if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters");
+    std::vector<int32_t> uniq(pairs, pairs + 2 * n_pairs);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    std::vector<int32_t> pidx((size_t)n_pairs * 2);
+    for (int64_t i = 0; i < 2 * n_pairs; ++i)
+        pidx[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), pairs[i]) - uniq.begin());
+    const int64_t ns = (int64_t)uniq.size();
+    void* pv;
+    if ((r = ensure_bytes(c, B_RES, (size_t)ns * kCh * 4, &pv))) return r;
+    float* V = static_cast<float*>(pv);
+    if ((r = ranker_embed_device(c, P, uniq.data(), ns, V))) return r;
+    int32_t* d_pidx;
+    float* d_logit;
+    AENSURE(A_PIDX, n_pairs * 8, d_pidx);
+    AENSURE(A_LOGIT, n_pairs * 4, d_logit);
+    if ((r = copy_in(c, d_pidx, pidx.data(), n_pairs * 8, false))) return r;
+    head_kernel<<<blocks_for(n_pairs * 32, 256), 256, 0, c->stream>>>(
+        V, d_pidx, nullptr, (int32_t)n_pairs, K->params + kOffAlpha, d_logit, nullptr, nullptr,
+        nullptr, 0);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 1;
+    CUDA_TRY(cudaMemcpyAsync(out, d_logit, n_pairs * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+int cm_ranker_embed(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                    float* out, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (!out && n_seqs > 0) return fail(c, CM_ERR_ARG, "null out");
+    Prepared P;
+    int r = prepare_seqs(c, seqs, offsets, n_seqs, flags, P);
+    if (r) return r;
+    if (n_seqs == 0) return CM_OK;
+    std::vector<int32_t> ids((size_t)n_seqs);
+    std::iota(ids.begin(), ids.end(), 0);
+    float* V = out;
+    const bool dev = (flags & CM_DEVICE_PTRS) != 0;
+    if (!dev) {
+        void* p;
+        if ((r = ensure_bytes(c, B_RES, (size_t)n_seqs * kCh * 4, &p))) return r;
+        V = static_cast<float*>(p);
+    }
+    if ((r = ranker_embed_device(c, P, ids.data(), n_seqs, V))) return r;
+    if (!dev) CUDA_TRY(cudaMemcpyAsync(out, V, (size_t)n_seqs * kCh * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+}  // extern "C"

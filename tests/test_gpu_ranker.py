@@ -1,0 +1,146 @@
+"""GPU ranker kernels (BF16 tensor-core implicit GEMMs, FP32 accumulate) against the float64
+oracle.  Tolerances follow from BF16 rounding: unit roundoff 2^-9 on every weight and stored
+activation, three layers deep, gives ~1e-2 relative error; vectors and logits are checked at
+3e-2 of their scale, gradients by per-tensor cosine >= 0.99 and relative norm error <= 6e-2."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ranker as R
+import paper_1908_10574_gb300 as cm
+from paper_1908_10574_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return cm.Context(0)
+
+
+def _set(rng_seed=7, n=10, lens=(1, 3, 8, 40, 129, 300, 511, 700, 1300, 60)):
+    rng = np.random.default_rng(rng_seed)
+    base = [synth.random_seq(rng, L) for L in lens[:n]]
+    return synth.SeqSet.from_list(base)
+
+
+def test_embeddings_match_oracle(ctx):
+    ss = _set()
+    p = R.init_params(11).astype(np.float32)
+    ctx.ranker_set_params(p)
+    got = ctx.ranker_embed(ss.seqs, ss.offsets)
+    want = R.embed(ss.seqs, ss.offsets, p.astype(np.float64))
+    for i in range(len(ss)):
+        err = np.linalg.norm(got[i] - want[i]) / max(np.linalg.norm(want[i]), 1e-6)
+        assert err < 3e-2, (i, err)
+
+
+def test_empty_sequence_embeds_to_zero_and_logits(ctx):
+    ss = synth.SeqSet.from_list([np.zeros(0, np.uint8), synth.random_seq(np.random.default_rng(1), 50)])
+    p = R.init_params(12).astype(np.float32)
+    ctx.ranker_set_params(p)
+    got = ctx.ranker_embed(ss.seqs, ss.offsets)
+    assert np.allclose(got[0], 0)
+    z = ctx.ranker_logits(ss.seqs, ss.offsets, np.array([[0, 1], [1, 1], [1, 0]], np.int32))
+    want = R.logits(ss.seqs, ss.offsets, p.astype(np.float64), [[0, 1], [1, 1], [1, 0]])
+    assert np.allclose(z, want, rtol=3e-2, atol=3e-2 * np.abs(want).max())
+    assert z[0] == z[2]
+
+
+def test_loss_and_gradient_match_oracle(ctx):
+    ss = _set(8, 10, (20, 35, 64, 90, 120, 150, 200, 260, 300, 33))
+    rng = np.random.default_rng(3)
+    pairs = rng.integers(0, len(ss), size=(24, 2)).astype(np.int32)
+    labels = (rng.random(24) < 0.5).astype(np.float32)
+    p = R.init_params(13).astype(np.float32)
+    ctx.ranker_set_params(p)
+    loss, grad = ctx.ranker_loss_grad(ss.seqs, ss.offsets, pairs, labels)
+    wl, wg = R.loss_grad(ss.seqs, ss.offsets, p.astype(np.float64), pairs, labels)
+    assert abs(loss - wl) <= 2e-2 * abs(wl)
+    o = 0
+    for name, shp in R.SHAPES:
+        k = int(np.prod(shp))
+        g, w = grad[o:o + k].astype(np.float64), wg[o:o + k]
+        o += k
+        nw = np.linalg.norm(w)
+        if nw < 1e-9:
+            continue
+        cos = g @ w / (np.linalg.norm(g) * nw)
+        rel = np.linalg.norm(g - w) / nw
+        assert cos >= 0.99 and rel <= 6e-2, (name, cos, rel)
+
+
+def test_training_learns_family_similarity(ctx):
+    ss = synth.small_families()
+    n = len(ss)
+    pairs = oracle.triangle_pairs(n)
+    scores = oracle.sw_batch(ss.seqs, ss.offsets, pairs, synth.BLOSUM62, 11, 1)
+    y = (scores > 100).astype(np.float32)
+    rng = np.random.default_rng(0)
+    pos = np.nonzero(y == 1)[0]
+    neg = rng.choice(np.nonzero(y == 0)[0], size=len(pos) * 3, replace=False)
+    sel = rng.permutation(np.concatenate([pos, neg]))
+    cut = int(0.8 * len(sel))
+    tr, te = sel[:cut], sel[cut:]
+    ctx.ranker_init(5)
+    ctx.ranker_standardize(ss.seqs, ss.offsets, max_sample=200)
+    V = ctx.ranker_embed(ss.seqs, ss.offsets)
+    # zero mean / unit variance per channel up to BF16 cancellation (Z3 rows are stored in
+    # BF16 while the channel mean being removed is large against its spread)
+    assert np.abs(V.mean(0)).max() < 0.2 and np.abs(V.std(0, ddof=1) - 1).max() < 0.1
+    z0 = ctx.ranker_logits(ss.seqs, ss.offsets, pairs[te])
+    loss = ctx.ranker_train(ss.seqs, ss.offsets, pairs[tr], y[tr], epochs=6, batch_pairs=64,
+                            lr=3e-4)
+    z1 = ctx.ranker_logits(ss.seqs, ss.offsets, pairs[te])
+
+    def auc(z, t):
+        order = np.argsort(z)
+        ranks = np.empty(len(z))
+        ranks[order] = np.arange(1, len(z) + 1)
+        npos = t.sum()
+        return (ranks[t == 1].sum() - npos * (npos + 1) / 2) / (npos * (len(t) - npos))
+
+    assert np.isfinite(loss)
+    assert auc(z0, y[te]) > 0.75                 # standardised random features already rank
+    assert auc(z1, y[te]) > 0.9 and auc(z1, y[te]) > auc(z0, y[te])
+
+
+def test_ranked_merge_without_pruning_keeps_full_recall(ctx):
+    ss = synth.small_families()
+    ctx.ranker_init(9)
+    ctx.ranker_standardize(ss.seqs, ss.offsets, max_sample=200)
+    truth, _ = oracle.all_pairs(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, T=100)
+    res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, 100, 10 ** 6, 15,
+                            use_ranker=True, prune_logit=-1e30)
+    n = len(ss)
+    assert res["stats"]["rep_comparisons"] == n * (n - 1) // 2
+    assert res["stats"]["ranker_selected"] == n * (n - 1) // 2
+    assert oracle.recall(res["pairs"], truth) == 1.0
+    plain = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, 100, 10 ** 6, 15)
+    assert res["pairs"].tolist() == plain["pairs"].tolist()
+
+
+def test_trained_ranker_prunes_with_high_recall(ctx):
+    train = synth.proteome(3000, family_size=8, singleton_frac=0.2, stream=11)
+    test = synth.proteome(800, family_size=8, singleton_frac=0.2, stream=12)
+    rng = np.random.default_rng(4)
+    fam = train.family
+    same = [np.nonzero(fam == f)[0] for f in np.unique(fam)]
+    pos = [rng.choice(g, 2, replace=False) for g in same if len(g) > 1 for _ in range(6)]
+    neg = rng.integers(0, len(train), size=(len(pos), 2))
+    pairs = np.concatenate([np.array(pos), neg]).astype(np.int32)
+    sc = ctx.sw_score_batch(train.seqs, train.offsets, pairs, synth.BLOSUM62, 11, 1)
+    y = (sc > 100).astype(np.float32)
+    ctx.ranker_init(3)
+    ctx.ranker_standardize(train.seqs, train.offsets, max_sample=512)
+    ctx.ranker_train(train.seqs, train.offsets, pairs, y, epochs=3, batch_pairs=128, lr=3e-4)
+    z = ctx.ranker_logits(train.seqs, train.offsets, pairs)
+    thr = float(np.quantile(z[y == 1], 0.002))      # keep 99.8 % of the training positives
+    truth, _ = oracle.all_pairs(test.seqs, test.offsets, synth.BLOSUM62, 11, 1, T=100)
+    plain = ctx.cluster_merge(test.seqs, test.offsets, synth.BLOSUM62, 11, 1, 100, 138, 15)
+    ranked = ctx.cluster_merge(test.seqs, test.offsets, synth.BLOSUM62, 11, 1, 100, 138, 15,
+                               use_ranker=True, prune_logit=thr)
+    rp, rr = oracle.recall(plain["pairs"], truth), oracle.recall(ranked["pairs"], truth)
+    assert rr >= 0.98 * rp
+    assert ranked["stats"]["rep_comparisons"] < 0.9 * plain["stats"]["rep_comparisons"]
+    assert ranked["stats"]["comparisons_scored"] < plain["stats"]["comparisons_scored"]
