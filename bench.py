@@ -225,16 +225,31 @@ def run_cluster_merge(args):
     ss = synth.proteome(n, family_size=8, singleton_frac=0.2, stream=3)
     ctx = cm.Context(0)
     T, mT, mU = T_SIG, M_T, M_U
+    ranker = None
+    if args.ranker:
+        ranker = train_ranker(ctx, args.train_seqs, args.train_pairs, args.epochs, args.keep,
+                              lr=args.lr, train_set=ss if args.transductive else None)
     t0 = time.perf_counter()
     res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT, mU)
     dt = time.perf_counter() - t0
+    ranked = None
+    if args.ranker:
+        t1 = time.perf_counter()
+        ranked = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT,
+                                   mU, use_ranker=True, prune_logit=ranker["prune_logit"],
+                                   ranker_min_pairs=args.min_pairs)
+        ranker["ranker_min_pairs"] = args.min_pairs
+        ranker["cluster_merge_seconds"] = time.perf_counter() - t1
+        ranker["stats"] = ranked["stats"]
+        ranker["clusters"] = len(ranked["clusters"])
+        ranker["similar_pairs"] = len(ranked["pairs"])
     out = {"metric": "ClusterMerge seconds", "value": dt, "unit": "s", "n_gpus": 1,
            "higher_is_better": False, "data": "synthetic", "dtype": "int16",
            "config": {"workload": "ClusterMerge of %d synthetic proteins (lognormal lengths, "
                                   "families of 8 + 20%% singletons), BLOSUM62 11/1, T=%d, mT=%d, "
                                   "mU=%d" % (n, T, mT, mU)},
            "clusters": len(res["clusters"]), "similar_pairs": len(res["pairs"]),
-           "stats": res["stats"]}
+           "stats": res["stats"], "ranker": ranker}
     if args.recall:
         t1 = time.perf_counter()
         truth = set()
@@ -247,10 +262,56 @@ def run_cluster_merge(args):
         out["all_pairs_seconds"] = time.perf_counter() - t1
         out["truth_pairs"] = len(truth)
         out["recall"] = len(found & truth) / max(len(truth), 1)
+        if ranked is not None:
+            fr = set(zip(ranked["pairs"][:, 0].tolist(), ranked["pairs"][:, 1].tolist()))
+            ranker["recall"] = len(fr & truth) / max(len(truth), 1)
         out["comparisons_fraction"] = (res["stats"]["rep_comparisons"] +
                                        res["stats"]["exchange_comparisons"] +
                                        res["stats"]["intra_comparisons"]) / (n * (n - 1) / 2)
     print(json.dumps(out), flush=True)
+
+
+def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, train_set=None):
+    """Train the ranker on a synthetic proteome (an independent one, or `train_set` itself):
+    half within-family pairs, half random pairs, labelled [SW score > T] by the GPU path; 10 %
+    held out to calibrate the pruning threshold so that a fraction `keep` of held-out
+    positives survives."""
+    tr = train_set if train_set is not None else \
+        synth.proteome(n_train_seqs, family_size=8, singleton_frac=0.2, stream=seed)
+    rng = np.random.default_rng(seed)
+    fam = tr.family
+    order = np.argsort(fam, kind="stable")
+    bounds = np.flatnonzero(np.diff(fam[order])) + 1
+    groups = [g for g in np.split(order, bounds) if len(g) > 1]
+    gi = rng.integers(0, len(groups), size=n_pairs // 2)
+    pos = np.array([rng.choice(groups[g], 2, replace=False) for g in gi])
+    neg = rng.integers(0, len(tr), size=(n_pairs - len(pos), 2))
+    pairs = np.concatenate([pos, neg]).astype(np.int32)
+    pairs = pairs[rng.permutation(len(pairs))]
+    t0 = time.perf_counter()
+    sc = ctx.sw_score_batch(tr.seqs, tr.offsets, pairs, synth.BLOSUM62, GAP_OPEN, GAP_EXT)
+    t_label = time.perf_counter() - t0
+    y = (sc > T_SIG).astype(np.float32)
+    cut = int(0.9 * len(pairs))
+    t0 = time.perf_counter()
+    ctx.ranker_init(seed)
+    ctx.ranker_standardize(tr.seqs, tr.offsets, max_sample=2048)
+    loss = ctx.ranker_train(tr.seqs, tr.offsets, pairs[:cut], y[:cut], epochs=epochs,
+                            batch_pairs=256, lr=lr, seed=seed)
+    t_train = time.perf_counter() - t0
+    z = ctx.ranker_logits(tr.seqs, tr.offsets, pairs[cut:])
+    yh = y[cut:]
+    thr = float(np.quantile(z[yh == 1], 1.0 - keep))
+    zo = np.argsort(z)
+    ranks = np.empty(len(z))
+    ranks[zo] = np.arange(1, len(z) + 1)
+    npos = yh.sum()
+    auc = float((ranks[yh == 1].sum() - npos * (npos + 1) / 2) / (npos * (len(yh) - npos)))
+    return {"train_seqs": len(tr), "transductive": train_set is not None, "train_pairs": int(cut), "heldout_pairs": int(len(pairs) - cut),
+            "positives": float(y.mean()), "epochs": epochs, "last_batch_loss": loss,
+            "label_seconds": t_label, "train_seconds": t_train, "heldout_auc": auc,
+            "prune_logit": thr, "keep_heldout_positives": keep,
+            "heldout_negatives_kept": float((z[yh == 0] >= thr).mean())}
 
 
 def main():
@@ -264,6 +325,16 @@ def main():
                     help="allpairs: SW GCUPS (default); cm: ClusterMerge seconds")
     ap.add_argument("--cm-seqs", type=int, default=100000)
     ap.add_argument("--recall", action="store_true")
+    ap.add_argument("--ranker", action="store_true", help="cm: also run the learned-ranker merge")
+    ap.add_argument("--train-seqs", type=int, default=100000)
+    ap.add_argument("--train-pairs", type=int, default=1000000)
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--keep", type=float, default=0.999)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--transductive", action="store_true",
+                    help="cm: train the ranker on the set being clustered (as the 100k setup)")
+    ap.add_argument("--min-pairs", type=int, default=100000,
+                    help="cm: merges with fewer rep x rep pairs stay unpruned")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--parts-per-gpu", type=int, default=PARTS_PER_GPU,
                     help="split of the triangle; a larger value gives shorter steps (profiling)")

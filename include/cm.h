@@ -135,9 +135,10 @@ typedef struct {
     int32_t mU;     /* full merge needs fewer than mU uncovered residues in the absorbed rep */
     int32_t use_ranker;    /* 1: the learned ranker orders and prunes rep x rep comparisons */
     float prune_logit;     /* with the ranker: rep pairs whose logit is below this are not
-                              aligned (treated as dissimilar); the rest are visited in
-                              descending logit order inside Algorithm 1's inner loop */
-    int32_t reserved[3];   /* must be 0 */
+                              aligned (treated as dissimilar); Algorithm 1 still visits the
+                              kept pairs in set order */
+    int32_t ranker_min_pairs;  /* only merges with |cs1|*|cs2| >= this use the ranker */
+    int32_t reserved[2];   /* must be 0 */
 } cm_params;
 
 typedef struct {

@@ -71,13 +71,18 @@ def exchange_similar(c1, c2, s, score, T, stats):
             c1.add(m)
 
 
-def merge(cs1, cs2, score, transitive, T, stats):
+def merge(cs1, cs2, score, transitive, T, stats, keep=None, min_pairs=0):
     """Algorithm 1.  `score(x, y)` is f on the pair (x, y); `transitive(r1, r2, s)` returns
-    (cluster2.IsTransitive(cluster1), cluster1.IsTransitive(cluster2)) for reps r1, r2."""
+    (cluster2.IsTransitive(cluster1), cluster1.IsTransitive(cluster2)) for reps r1, r2.
+    Optional pruning (the learned ranker's role): when len(cs1)*len(cs2) >= min_pairs, a
+    representative pair with keep(r1, r2) false is not compared at all."""
+    prune = keep is not None and len(cs1) * len(cs2) >= min_pairs
     new_set = []
     for c1 in cs1:
         for c2 in cs2:
             if c2.merged:
+                continue
+            if prune and not keep(c1.rep, c2.rep):
                 continue
             s = score(c1.rep, c2.rep)
             stats["rep"] += 1
@@ -104,7 +109,7 @@ def merge(cs1, cs2, score, transitive, T, stats):
     return new_set
 
 
-def bottom_up_merge(n, score, transitive, T, stats=None):
+def bottom_up_merge(n, score, transitive, T, stats=None, keep=None, min_pairs=0):
     """Algorithm 2: FIFO of singleton cluster sets, pop two, merge, push, until one is left."""
     if stats is None:
         stats = new_stats()
@@ -114,7 +119,7 @@ def bottom_up_merge(n, score, transitive, T, stats=None):
     while len(q) > 1:
         cs1 = q.popleft()
         cs2 = q.popleft()
-        q.append(merge(cs1, cs2, score, transitive, T, stats))
+        q.append(merge(cs1, cs2, score, transitive, T, stats, keep, min_pairs))
         stats["merges"] += 1
     return q.popleft(), stats
 
@@ -142,7 +147,7 @@ def intra_cluster_pairs(clusters, score, T, stats):
 
 
 def cluster_merge(seqs, offsets, S, gap_open, gap_extend, T, mT, mU, gap_mode=0,
-                  score_matrix=None):
+                  score_matrix=None, keep=None, min_pairs=0):
     """Full ClusterMerge over a sequence set: Algorithm 2 with protein transitivity (Sec. 4),
     then the intra-cluster all-against-all.  `score_matrix` (optional, n x n, from the oracle's
     own all_pairs) replaces direct SW calls by lookups; it is only used for symmetric S.
@@ -176,7 +181,7 @@ def cluster_merge(seqs, offsets, S, gap_open, gap_extend, T, mT, mU, gap_mode=0,
         uA, uB = uncovered(len(a), len(b), cells)
         return uA < mU, uB < mU
 
-    final, stats = bottom_up_merge(n, score, transitive, T)
+    final, stats = bottom_up_merge(n, score, transitive, T, keep=keep, min_pairs=min_pairs)
     pairs = intra_cluster_pairs(final, score, T, stats)
     clusters = [(c.rep, list(c.objs)) for c in final]
     return {"clusters": clusters, "pairs": pairs, "stats": stats}

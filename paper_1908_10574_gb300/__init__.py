@@ -177,14 +177,15 @@ class Context:
 
 
     def cluster_merge(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
-                      use_ranker=False, prune_logit=0.0):
+                      use_ranker=False, prune_logit=0.0, ranker_min_pairs=0):
         """ClusterMerge (Algorithms 1 and 2 with the Sec. 4 transitivity test) plus the
         intra-cluster all-against-all.  Returns a dict: clusters [(rep, [members])], pairs
         (k, 3) int64 (i, j, score) sorted, and the comparison counters."""
         seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
         flags |= self._prep([seqs, offsets, matrix])
         n = int(offsets.shape[0]) - 1
-        prm = _L.cm_params(int(T), int(mT), int(mU), int(bool(use_ranker)), float(prune_logit))
+        prm = _L.cm_params(int(T), int(mT), int(mU), int(bool(use_ranker)), float(prune_logit),
+                           int(ranker_min_pairs))
         res = ctypes.POINTER(_L.cm_result)()
         _L.check(self._h, _L.lib().cluster_merge(self._h, _ptr(seqs), _ptr(offsets), n,
                                                  _ptr(matrix), int(gap_open), int(gap_extend),
@@ -320,6 +321,6 @@ def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, c
 
 
 def cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
-                  use_ranker=False, prune_logit=0.0):
+                  use_ranker=False, prune_logit=0.0, ranker_min_pairs=0):
     return default_context().cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT,
-                                           mU, flags, use_ranker, prune_logit)
+                                           mU, flags, use_ranker, prune_logit, ranker_min_pairs)

@@ -36,7 +36,7 @@ class cm_stats(ctypes.Structure):
 class cm_params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("mT", ctypes.c_int32), ("mU", ctypes.c_int32),
                 ("use_ranker", ctypes.c_int32), ("prune_logit", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("ranker_min_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class cm_result(ctypes.Structure):

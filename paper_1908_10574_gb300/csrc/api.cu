@@ -170,29 +170,34 @@ void choose_R(int64_t m, int* R, int* npass)
     *npass = np;
 }
 
-// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows.
+// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows.  A query
+// without a partner runs in the single-query two-stream mode (twice the rows per task, split
+// over twice as many warp streams).
 void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
                const int64_t* srow, int64_t target)
 {
     int R, np;
     choose_R(m_hi, &R, &np);
+    const int two = hi_valid ? 0 : 1;
+    if (two) target *= 2;
     int32_t s = 0;
     while (s < ns) {
         const int64_t want = srow[s] + target;
         int32_t e = (int32_t)(std::lower_bound(srow + s + 1, srow + ns + 1, want) - srow);
         if (e > ns) e = ns;
-        SwTask t;
+        SwTask t{};
         t.block = block;
         t.k = k;
         t.s0 = s;
         t.s1 = e;
         t.npass = np;
         t.hi_valid = hi_valid ? 1 : 0;
+        t.two_streams = two;
         const int64_t rows = srow[e] - srow[s];
-        P.cells_padded += rows * 32 * R * np * 2;
+        P.cells_padded += rows * 32 * R * np * (two ? 1 : 2);
         P.tasks.push_back(t);
-        P.task_R.push_back(R);
-        P.keys.push_back({rows * R * np, R});
+        P.task_R.push_back(R * 2 + two);          // launch bin: register tile and mode
+        P.keys.push_back({rows * R * np / (two ? 2 : 1), R * 2 + two});
         s = e;
     }
 }
@@ -276,15 +281,17 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     size_t i0 = 0;
     int bin = 0;
     while (i0 < plan.tasks.size()) {
-        const int R = plan.task_R[i0];
+        const int key = plan.task_R[i0];
+        const int R = key / 2;
+        const bool two = (key & 1) != 0;
         size_t i1 = i0;
-        while (i1 < plan.tasks.size() && plan.task_R[i1] == R) ++i1;
+        while (i1 < plan.tasks.size() && plan.task_R[i1] == key) ++i1;
         a.tasks = d_tasks + i0;
         a.ntasks = (int32_t)(i1 - i0);
         a.task_counter = d_flags + 8 + bin;
         const int occ = std::max(1, sw16_ctas_per_sm(R, W));
         const int grid = (int)std::min<int64_t>(a.ntasks, (int64_t)c->num_sms * occ);
-        CUDA_TRY(launch_sw16(R, W, grid, a, st));
+        CUDA_TRY(launch_sw16(R, W, two, grid, a, st));
         c->stats.launches += 1;
         c->stats.sw16_launches += 1;
         i0 = i1;
@@ -400,7 +407,7 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
     int64_t maxlen_rows = 1;
     for (size_t s = 0; s + 1 < plan.srow.size(); ++s)
         maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
-    plan.max_warp_rows = c->rows_per_warp + 2 * maxlen_rows + target / c->W;
+    plan.max_warp_rows = 2 * c->rows_per_warp + 2 * maxlen_rows + 2 * target / c->W;
     int32_t* out;
     ENSURE(B_OUT, slots, out);
     int r = run_plan(c, P, plan, out, nullptr, flags);
@@ -630,7 +637,7 @@ int sw_score_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
     int64_t maxlen_rows = 0;
     for (size_t s = 0; s + 1 < plan.srow.size(); ++s)
         maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
-    plan.max_warp_rows = c->rows_per_warp + 2 * maxlen_rows + target / c->W;
+    plan.max_warp_rows = 2 * c->rows_per_warp + 2 * maxlen_rows + 2 * target / c->W;
 
     int64_t* d_omap;
     ENSURE(B_OMAP, n_pairs, d_omap);
@@ -761,7 +768,7 @@ int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t 
     int64_t maxlen_rows = 1;
     for (int32_t s = 0; s < n_seqs; ++s)
         maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
-    plan.max_warp_rows = c->rows_per_warp + 2 * maxlen_rows + target / c->W;
+    plan.max_warp_rows = 2 * c->rows_per_warp + 2 * maxlen_rows + 2 * target / c->W;
 
     int32_t* out;
     ENSURE(B_OUT, plan.nslots, out);

@@ -87,49 +87,33 @@ struct Driver {
 int Driver::run_round(const std::vector<Merge>& ms)
 {
     const size_t nm = ms.size();
-    // ---- wave 1: rep x rep scores.  Plain: every merge's full cross product (one CROSS block
-    // per merge, queries = cs1 reps by length).  Ranker: only the pairs whose ranker logit
-    // reaches prune_logit, each cs1 rep's candidates in descending logit order. ----
+    // ---- wave 1: rep x rep scores.  Every merge's full cross product is one CROSS block
+    // (queries = cs1 reps by length).  With the ranker, merges whose cross product has at
+    // least ranker_min_pairs pairs align only the pairs whose ranker logit reaches
+    // prune_logit (one single-query block per cs1 rep); Algorithm 1 still visits cs2 in set
+    // order, so the ranker changes which pairs are aligned, never the order of the loop. ----
     std::vector<int32_t> S;
     std::vector<int64_t> base;
     std::vector<std::vector<int32_t>> rowpos(nm);    // cs1 index -> row k in the block
-    // ranker mode: per merge, per cs1 index, the ranked candidates (i2, score)
+    std::vector<char> ranked(nm, 0);
+    // ranked merges: per cs1 index, the kept (i2, score) in ascending i2
     std::vector<std::vector<std::vector<std::pair<int32_t, int32_t>>>> cand(nm);
     double t0 = now_s();
     int r;
-    if (!U) {
-        std::vector<int32_t> ids;
-        std::vector<BlockReq> req(nm);
-        for (size_t m = 0; m < nm; ++m) {
-            const auto& cs1 = sets[ms[m].left];
-            const auto& cs2 = sets[ms[m].right];
-            std::vector<int32_t> order(cs1.size());
-            std::iota(order.begin(), order.end(), 0);
-            std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-                return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
-            });
-            rowpos[m].assign(cs1.size(), 0);
-            req[m].kind = kCross;
-            req[m].swap = 0;                              // pair (rep1, rep2)
-            req[m].a_begin = (int64_t)ids.size();
-            req[m].a_count = (int64_t)cs1.size();
-            for (size_t k = 0; k < order.size(); ++k) {
-                rowpos[m][order[k]] = (int32_t)k;
-                ids.push_back(arena[cs1[order[k]]].rep);
-            }
-            req[m].b_begin = (int64_t)ids.size();
-            req[m].b_count = (int64_t)cs2.size();
-            for (int32_t ci : cs2) ids.push_back(arena[ci].rep);
-        }
-        r = score_blocks(c, P, ids, req, S, base, flags);
-        if (r) return r;
-        scored += (int64_t)S.size();
-    } else {
+    std::vector<uint32_t> bitmap;
+    std::vector<int64_t> bitbase(nm, 0), words(nm, 0);
+    if (U) {
         std::vector<int32_t> rows;
         std::vector<SelTile> tiles;
+        int64_t nwords = 0;
         for (size_t m = 0; m < nm; ++m) {
             const auto& cs1 = sets[ms[m].left];
             const auto& cs2 = sets[ms[m].right];
+            if ((int64_t)cs1.size() * (int64_t)cs2.size() < (int64_t)prm.ranker_min_pairs) continue;
+            ranked[m] = 1;
+            words[m] = ((int64_t)cs2.size() + 31) / 32;
+            bitbase[m] = nwords;
+            nwords += words[m] * (int64_t)cs1.size();
             const int32_t a0 = (int32_t)rows.size();
             for (int32_t ci : cs1) rows.push_back(arena[ci].rep);
             const int32_t b0 = (int32_t)rows.size();
@@ -144,58 +128,89 @@ int Driver::run_round(const std::vector<Merge>& ms)
                     t.nb = std::min<int32_t>(128, (int32_t)cs2.size() - j0);
                     t.a = a0 + i0;
                     t.b = b0 + j0;
+                    t.words = (int32_t)words[m];
+                    t.bits = bitbase[m];
                     tiles.push_back(t);
                 }
         }
-        std::vector<SelPair> sel;
-        const double tr = now_s();
-        r = ranker_select(c, U, rows, tiles, prm.prune_logit, sel);
-        if (r) return r;
-        t_rank += now_s() - tr;
-        ++batches;
-        selected += (int64_t)sel.size();
-        std::sort(sel.begin(), sel.end(), [](const SelPair& x, const SelPair& y) {
-            if (x.block != y.block) return x.block < y.block;
-            if (x.i != y.i) return x.i < y.i;
-            if (x.logit != y.logit) return x.logit > y.logit;
-            return x.j < y.j;
-        });
-        // score the selected pairs: one CROSS block {rep1} x {its candidates}
-        std::vector<int32_t> ids;
-        std::vector<BlockReq> req;
-        std::vector<std::pair<int32_t, int32_t>> owner;     // (merge, i1) of each block
-        for (size_t q0 = 0; q0 < sel.size();) {
-            size_t q1 = q0;
-            while (q1 < sel.size() && sel[q1].block == sel[q0].block && sel[q1].i == sel[q0].i) ++q1;
-            const size_t m = (size_t)sel[q0].block;
+        if (!tiles.empty()) {
+            const double tr = now_s();
+            r = ranker_select(c, U, rows, tiles, prm.prune_logit, nwords, bitmap);
+            if (r) return r;
+            t_rank += now_s() - tr;
+            ++batches;
+        }
+    }
+    std::vector<int32_t> ids;
+    std::vector<BlockReq> req;
+    std::vector<int64_t> block_of(nm, -1);                 // plain merges: their block
+    std::vector<std::pair<int32_t, int32_t>> owner;        // ranked blocks: (merge, i1)
+    for (size_t m = 0; m < nm; ++m) {
+        const auto& cs1 = sets[ms[m].left];
+        const auto& cs2 = sets[ms[m].right];
+        if (!ranked[m]) {
+            std::vector<int32_t> order(cs1.size());
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+                return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
+            });
+            rowpos[m].assign(cs1.size(), 0);
             BlockReq b{};
             b.kind = kCross;
-            b.swap = 0;
+            b.swap = 0;                                      // pair (rep1, rep2)
             b.a_begin = (int64_t)ids.size();
-            b.a_count = 1;
-            ids.push_back(arena[sets[ms[m].left][sel[q0].i]].rep);
+            b.a_count = (int64_t)cs1.size();
+            for (size_t k = 0; k < order.size(); ++k) {
+                rowpos[m][order[k]] = (int32_t)k;
+                ids.push_back(arena[cs1[order[k]]].rep);
+            }
             b.b_begin = (int64_t)ids.size();
-            b.b_count = (int64_t)(q1 - q0);
-            for (size_t q = q0; q < q1; ++q) ids.push_back(arena[sets[ms[m].right][sel[q].j]].rep);
+            b.b_count = (int64_t)cs2.size();
+            for (int32_t ci : cs2) ids.push_back(arena[ci].rep);
+            block_of[m] = (int64_t)req.size();
             req.push_back(b);
-            owner.push_back({sel[q0].block, sel[q0].i});
-            q0 = q1;
+            owner.push_back({-1, -1});
+        } else {
+            for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
+                const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
+                BlockReq b{};
+                b.kind = kCross;
+                b.swap = 0;
+                b.a_begin = (int64_t)ids.size();
+                b.a_count = 1;
+                ids.push_back(arena[cs1[i1]].rep);
+                b.b_begin = (int64_t)ids.size();
+                for (int64_t w = 0; w < words[m]; ++w)
+                    for (uint32_t x = row[w]; x; x &= x - 1)
+                        ids.push_back(arena[cs2[w * 32 + __builtin_ctz(x)]].rep);
+                b.b_count = (int64_t)ids.size() - b.b_begin;
+                if (b.b_count == 0) { ids.resize(b.a_begin); continue; }
+                req.push_back(b);
+                owner.push_back({(int32_t)m, i1});
+            }
         }
-        r = score_blocks(c, P, ids, req, S, base, flags);
-        if (r) return r;
-        scored += (int64_t)S.size();
-        for (size_t m = 0; m < nm; ++m) cand[m].assign(sets[ms[m].left].size(), {});
-        size_t q = 0;
-        for (size_t bi = 0; bi < req.size(); ++bi) {
-            auto& lst = cand[owner[bi].first][owner[bi].second];
-            for (int64_t s2 = 0; s2 < req[bi].b_count; ++s2, ++q)
-                lst.push_back({sel[q].j, S[base[bi] + s2]});
-        }
+    }
+    r = score_blocks(c, P, ids, req, S, base, flags);
+    if (r) return r;
+    scored += (int64_t)S.size();
+    for (size_t m = 0; m < nm; ++m)
+        if (ranked[m]) cand[m].assign(sets[ms[m].left].size(), {});
+    for (size_t bi = 0; bi < req.size(); ++bi) {
+        if (owner[bi].first < 0) continue;
+        const size_t m = (size_t)owner[bi].first;
+        const int32_t i1 = owner[bi].second;
+        const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
+        auto& lst = cand[m][i1];
+        int64_t q = 0;
+        for (int64_t w = 0; w < words[m]; ++w)
+            for (uint32_t x = row[w]; x; x &= x - 1, ++q)
+                lst.push_back({(int32_t)(w * 32 + __builtin_ctz(x)), S[base[bi] + q]});
+        selected += (int64_t)lst.size();
     }
     t_rep += now_s() - t0;
     ++batches;
     auto score_of = [&](size_t m, int32_t i1, int32_t i2) {
-        return S[base[m] + (int64_t)rowpos[m][i1] * (int64_t)sets[ms[m].right].size() + i2];
+        return S[base[block_of[m]] + (int64_t)rowpos[m][i1] * (int64_t)sets[ms[m].right].size() + i2];
     };
 
     // ---- wave 2: alignment cells of every candidate full merge (s > mT and s > T) ----
@@ -212,7 +227,7 @@ int Driver::run_round(const std::vector<Merge>& ms)
             }
         };
         for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
-            if (U) {
+            if (ranked[m]) {
                 for (const auto& js : cand[m][i1]) add(i1, js.first, js.second);
             } else {
                 for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2) add(i1, i2, score_of(m, i1, i2));
@@ -238,11 +253,12 @@ int Driver::run_round(const std::vector<Merge>& ms)
         std::unordered_map<uint64_t, int64_t> cmap(cidx[m].begin(), cidx[m].end());
         std::vector<char> merged1(cs1.size(), 0), merged2(cs2.size(), 0);
         for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
-            const int32_t nvisit = U ? (int32_t)cand[m][i1].size() : (int32_t)cs2.size();
+            const bool rk = ranked[m] != 0;
+            const int32_t nvisit = rk ? (int32_t)cand[m][i1].size() : (int32_t)cs2.size();
             for (int32_t q = 0; q < nvisit; ++q) {
-                const int32_t i2 = U ? cand[m][i1][q].first : q;
+                const int32_t i2 = rk ? cand[m][i1][q].first : q;
                 if (merged2[i2]) continue;
-                const int32_t s = U ? cand[m][i1][q].second : score_of(m, i1, i2);
+                const int32_t s = rk ? cand[m][i1][q].second : score_of(m, i1, i2);
                 ++rep_cmp;
                 if (s <= prm.T) continue;
                 bool t21 = false, t12 = false;

@@ -40,13 +40,18 @@ struct SwBlock {
     int32_t has_map;    // 1: slot -> user index through out_map[]
 };
 
-// One CTA task: the query pair (k, k+1) of a block against subjects [s0, s1).
+// One CTA task.  Pair mode: the query pair (k, k+1) of a block against subjects [s0, s1),
+// the two queries in the two 16-bit halves, one subject stream per warp.  Single mode
+// (two_streams = 1): query k alone against subjects [s0, s1), each warp running two subject
+// streams in the two halves.
 struct SwTask {
     int32_t block;
     int32_t k;          // lo query index; hi = k+1 (if hi_valid)
     int32_t s0, s1;     // subjects covered (rows split over the CTA's warps)
     int32_t npass;      // column passes of 32*R columns
-    int32_t hi_valid;   // 0 when the lo query has no partner
+    int32_t hi_valid;   // pair mode: 0 when the lo query has no partner
+    int32_t two_streams;
+    int32_t pad;
 };
 
 struct SwArgs {
@@ -92,7 +97,7 @@ struct CellJob {
 
 // ---- launchers (sw16.cu) ---------------------------------------------------------------
 int sw16_smem_bytes(int R);
-cudaError_t launch_sw16(int R, int W, int grid, const SwArgs& a, cudaStream_t st);
+cudaError_t launch_sw16(int R, int W, bool two, int grid, const SwArgs& a, cudaStream_t st);
 cudaError_t launch_sw32(int R, int grid, const SwArgs& a, const PairRef* pr, int32_t npairs,
                         int32_t* counter, cudaStream_t st);
 int sw32_smem_bytes(int R);

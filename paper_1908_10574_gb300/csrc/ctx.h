@@ -92,15 +92,15 @@ struct SelTile {
     int32_t i0, j0;        // offsets of the tile inside its block
     int32_t na, nb;        // valid rows / columns of the tile (<= 128)
     int32_t a, b;          // first A row / B row of the tile in the row list
-    int32_t pad;
-};
-struct SelPair {
-    int32_t block, i, j;
-    float logit;
+    int32_t words;         // 32-bit words per bitmap row of the block
+    int64_t bits;          // first bitmap word of the block
 };
 int ranker_unit_vectors(cm_ctx* c, const Prepared& P, int64_t n, void** U_out);
+// sets bit (i, j) of each block's bitmap (row-major, `words` words per row) where the
+// ranker logit of (A row i, B row j) reaches thr; `bitmap` holds nwords words on return
 int ranker_select(cm_ctx* c, const void* U, const std::vector<int32_t>& rows,
-                  const std::vector<SelTile>& tiles, float thr, std::vector<SelPair>& out);
+                  const std::vector<SelTile>& tiles, float thr, int64_t nwords,
+                  std::vector<uint32_t>& bitmap);
 int ranker_alpha_beta(cm_ctx* c, float* ab);
 
 struct Plan {

@@ -478,8 +478,7 @@ __global__ void __launch_bounds__(256) pairsel_kernel(const bf16* __restrict__ U
                                                       const int32_t* __restrict__ rows,
                                                       const SelTile* __restrict__ tiles,
                                                       const float* __restrict__ ab, float thr,
-                                                      SelPair* __restrict__ out, int32_t cap,
-                                                      int32_t* __restrict__ count)
+                                                      uint32_t* __restrict__ bitmap)
 {
     constexpr int Str = kCh + 8;
     __shared__ __align__(16) bf16 sA[128 * Str];
@@ -536,15 +535,8 @@ __global__ void __launch_bounds__(256) pairsel_kernel(const bf16* __restrict__ U
                 const int j = wn0 + nt * 8 + 2 * t + (q & 1);
                 const float z = alpha * acc[mt][nt][q] + beta;
                 if (i < T.na && j < T.nb && z >= thr) {
-                    const int32_t k = atomicAdd(count, 1);
-                    if (k < cap) {
-                        SelPair sp;
-                        sp.block = T.block;
-                        sp.i = T.i0 + i;
-                        sp.j = T.j0 + j;
-                        sp.logit = z;
-                        out[k] = sp;
-                    }
+                    const int32_t bi = T.i0 + i, bj = T.j0 + j;
+                    atomicOr(&bitmap[T.bits + (int64_t)bi * T.words + (bj >> 5)], 1u << (bj & 31));
                 }
             }
 }
@@ -838,47 +830,36 @@ int ranker_alpha_beta(cm_ctx* c, float* ab)
     return CM_OK;
 }
 
-// Logits of every (A row, B row) pair of the tiles at or above thr; returns them unsorted.
+// Bitmaps of the (A row, B row) pairs of every tile whose ranker logit reaches thr.
 int ranker_select(cm_ctx* c, const void* Uv, const std::vector<int32_t>& rows,
-                  const std::vector<SelTile>& tiles, float thr, std::vector<SelPair>& out)
+                  const std::vector<SelTile>& tiles, float thr, int64_t nwords,
+                  std::vector<uint32_t>& bitmap)
 {
     const bf16* U = static_cast<const bf16*>(Uv);
-    out.clear();
+    bitmap.assign((size_t)nwords, 0u);
     if (tiles.empty()) return CM_OK;
     Ranker* K;
     int r = get_ranker(c, &K);
     if (r) return r;
     int32_t* d_rows;
     SelTile* d_tiles;
-    SelPair* d_out;
-    int32_t* d_cnt;
+    uint32_t* d_bits;
     AENSURE(A_PIDX, rows.size() * 4, d_rows);
     AENSURE(A_Y, tiles.size() * sizeof(SelTile), d_tiles);
-    AENSURE(A_DV, 64, d_cnt);
-    int32_t cap = 1 << 20;
-    for (int attempt = 0; attempt < 6; ++attempt) {
-        AENSURE(A_LOGIT, (size_t)cap * sizeof(SelPair), d_out);
-        if ((r = copy_in(c, d_rows, rows.data(), rows.size() * 4, false))) return r;
-        if ((r = copy_in(c, d_tiles, tiles.data(), tiles.size() * sizeof(SelTile), false))) return r;
-        CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 4, c->stream));
-        for (size_t t0 = 0; t0 < tiles.size(); t0 += 65535) {
-            const unsigned nt = (unsigned)std::min<size_t>(65535, tiles.size() - t0);
-            pairsel_kernel<<<nt, 256, 0, c->stream>>>(U, d_rows, d_tiles + t0, K->params + kOffAlpha,
-                                                      thr, d_out, cap, d_cnt);
-            c->stats.launches += 1;
-        }
-        CUDA_TRY(cudaGetLastError());
-        int32_t n = 0;
-        CUDA_TRY(cudaMemcpyAsync(&n, d_cnt, 4, cudaMemcpyDeviceToHost, c->stream));
-        CUDA_TRY(cudaStreamSynchronize(c->stream));
-        if (n <= cap) {
-            out.resize((size_t)n);
-            CUDA_TRY(cudaMemcpy(out.data(), d_out, (size_t)n * sizeof(SelPair), cudaMemcpyDeviceToHost));
-            return CM_OK;
-        }
-        cap = n;
+    AENSURE(A_LOGIT, nwords * 4, d_bits);
+    if ((r = copy_in(c, d_rows, rows.data(), rows.size() * 4, false))) return r;
+    if ((r = copy_in(c, d_tiles, tiles.data(), tiles.size() * sizeof(SelTile), false))) return r;
+    CUDA_TRY(cudaMemsetAsync(d_bits, 0, nwords * 4, c->stream));
+    for (size_t t0 = 0; t0 < tiles.size(); t0 += 65535) {
+        const unsigned nt = (unsigned)std::min<size_t>(65535, tiles.size() - t0);
+        pairsel_kernel<<<nt, 256, 0, c->stream>>>(U, d_rows, d_tiles + t0, K->params + kOffAlpha,
+                                                  thr, d_bits);
+        c->stats.launches += 1;
     }
-    return fail(c, CM_ERR_INTERNAL, "pair selection did not fit");
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(bitmap.data(), d_bits, nwords * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CM_OK;
 }
 
 // unit rows U (bf16, n x 128) of the ranker vectors of all n sequences, in device memory

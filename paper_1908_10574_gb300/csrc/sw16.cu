@@ -21,6 +21,8 @@
 // the running maximum) and 2 IADDs.  If a stored best reaches 32767 - max(S), some cell may
 // have overflowed int16; that pair is marked and rescored on the int32 path, so every score
 // returned is exact.
+#include <algorithm>
+
 #include "cm_internal.h"
 
 namespace cm {
@@ -169,7 +171,116 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
     }
 }
 
-template <int R, int W>
+// Single-query mode: the lo and hi halves run two different subject streams (rows
+// [0, n_lo) of stream_lo and [0, n_hi) of stream_hi) against the same query.  The profile
+// holds (S, S) in both halves; per row the lo half is taken from the row of the lo residue
+// and the hi half from the row of the hi residue (one byte_perm per packed column).  First /
+// last flags, resets and score writes are per half.
+template <int R>
+__device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
+                                              const uint32_t* __restrict__ prof,
+                                              const uint8_t* __restrict__ st_lo, int64_t n_lo,
+                                              const uint8_t* __restrict__ st_hi, int64_t n_hi,
+                                              int pass, int npass, uint2* __restrict__ bnd,
+                                              int32_t s_lo0, int32_t s_hi0, int32_t k, int32_t ns)
+{
+    using G = Geo<R>;
+    const int lane = threadIdx.x & 31;
+    const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
+    const uint32_t BETA2 = (uint32_t)beta * 0x10001u;
+    const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;
+    const uint32_t NEGO = pack2(-o, -o);
+    const uint32_t E2 = (uint32_t)ge * 0x10001u;
+
+    uint32_t hp[R], fp[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) { hp[q] = BETA2; fp[q] = BMO2; }
+    uint32_t best = BETA2, out_h = BETA2, out_e = BMO2, out_acc = BETA2, diag0 = BETA2;
+    const uint32_t padpair = (uint32_t)kPadCode | ((uint32_t)kPadCode << 8);
+    uint32_t cur = padpair, prev = padpair, bh = BETA2, be = BMO2;
+    int32_t s_lo = s_lo0, s_hi = s_hi0;
+    const uint32_t* plane = prof + lane * G::LS;
+    const int64_t nrows = n_lo > n_hi ? n_lo : n_hi;
+    const int64_t nsteps = nrows + 31;
+
+    for (int64_t t = 0; t < nsteps; ++t) {
+        const int j = (int)(t & 31);
+        if (j == 0) {
+            prev = cur;
+            const int64_t r = t + lane;
+            const uint32_t lo = (r < n_lo) ? (uint32_t)st_lo[r] : (uint32_t)kPadCode;
+            const uint32_t hi = (r < n_hi) ? (uint32_t)st_hi[r] : (uint32_t)kPadCode;
+            cur = lo | (hi << 8);
+            if (pass > 0) {
+                if (r < nrows) { const uint2 v = bnd[r]; bh = v.x; be = v.y; }
+                else { bh = BETA2; be = BMO2; }
+            }
+        }
+        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
+        uint32_t hl = __shfl_up_sync(kFull, out_h, 1);
+        uint32_t el = __shfl_up_sync(kFull, out_e, 1);
+        uint32_t ai = __shfl_up_sync(kFull, out_acc, 1);
+        if (pass > 0) {
+            const uint32_t x = __shfl_sync(kFull, bh, j);
+            const uint32_t y = __shfl_sync(kFull, be, j);
+            if (lane == 0) { hl = x; el = y; }
+        } else if (lane == 0) {
+            hl = BETA2; el = BMO2;
+        }
+        if (lane == 0) ai = BETA2;
+        uint32_t dg = diag0;
+        diag0 = hl;
+        if (rv & ((uint32_t)kFirst | ((uint32_t)kFirst << 8))) {
+            const uint32_t keep = ((rv & kFirst) ? 0u : 0x0000ffffu) |
+                                  ((rv & ((uint32_t)kFirst << 8)) ? 0u : 0xffff0000u);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                hp[q] = (hp[q] & keep) | (BETA2 & ~keep);
+                fp[q] = (fp[q] & keep) | (BMO2 & ~keep);
+            }
+            best = (best & keep) | (BETA2 & ~keep);
+            dg = (dg & keep) | (BETA2 & ~keep);
+        }
+        const uint32_t* prow_lo = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
+        const uint32_t* prow_hi = plane + min((rv >> 8) & 31u, (uint32_t)kPadCode) * G::ROWW;
+        uint32_t h = hl, e = el, hprev = BETA2;
+#pragma unroll
+        for (int j4 = 0; j4 < R / 4; ++j4) {
+            const uint4 sl = *reinterpret_cast<const uint4*>(prow_lo + 4 * j4);
+            const uint4 sh = *reinterpret_cast<const uint4*>(prow_hi + 4 * j4);
+            const uint32_t s4[4] = {__byte_perm(sl.x, sh.x, 0x7610), __byte_perm(sl.y, sh.y, 0x7610),
+                                    __byte_perm(sl.z, sh.z, 0x7610), __byte_perm(sl.w, sh.w, 0x7610)};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = 4 * j4 + u;
+                e = __viaddmax_s16x2(h, NEGO, e - E2);
+                const uint32_t f = __viaddmax_s16x2(hp[q], NEGO, fp[q] - E2);
+                fp[q] = f;
+                const uint32_t d = __viaddmax_s16x2(dg, s4[u], BETA2);
+                dg = hp[q];
+                h = __vimax3_s16x2(d, e, f);
+                hp[q] = h;
+                if (u & 1) best = __vimax3_s16x2(best, h, hprev); else hprev = h;
+            }
+        }
+        out_h = h;
+        out_e = e;
+        out_acc = __vmaxs2(ai, best);
+        if (lane == 31 && (rv & ((uint32_t)kLast | ((uint32_t)kLast << 8)))) {
+            if (rv & kLast) {
+                const int32_t sidx = s_lo++;
+                if (sidx < ns) store_score(a, B, k, sidx, (int32_t)(int16_t)(out_acc & 0xffffu), pass);
+            }
+            if (rv & ((uint32_t)kLast << 8)) {
+                const int32_t sidx = s_hi++;
+                if (sidx < ns) store_score(a, B, k, sidx, (int32_t)(int16_t)(out_acc >> 16), pass);
+            }
+        }
+        if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_uint2(out_h, out_e);
+    }
+}
+
+template <int R, int W, bool TWO>
 __global__ void __launch_bounds__(W * 32, 16 / W)
 sw16_kernel(const __grid_constant__ SwArgs a)
 {
@@ -195,25 +306,30 @@ sw16_kernel(const __grid_constant__ SwArgs a)
         const SwBlock B = a.blocks[T.block];
         const int32_t* A_ids = a.ids + B.a_ids;
         const int32_t q_lo = A_ids[T.k];
-        const int32_t q_hi = T.hi_valid ? A_ids[T.k + 1] : q_lo;
+        const int32_t q_hi = (!TWO && T.hi_valid) ? A_ids[T.k + 1] : q_lo;
         const int64_t qoff_lo = a.off[q_lo], m_lo = a.off[q_lo + 1] - qoff_lo;
         const int64_t qoff_hi = a.off[q_hi];
-        const int64_t m_hi = T.hi_valid ? a.off[q_hi + 1] - qoff_hi : 0;
+        const int64_t m_hi = (TWO || T.hi_valid) ? a.off[q_hi + 1] - qoff_hi : 0;
         const int32_t ns_lo = (B.kind == kTri) ? T.k : B.nb;
         const int32_t ns_hi = (B.kind == kTri) ? T.k + 1 : B.nb;
         const int64_t* srow = a.srows + B.srow;
 
-        // rows of this task split over the CTA's warps at subject boundaries
+        // rows of this task split over the CTA's warp streams at subject boundaries
+        constexpr int NS = TWO ? 2 * W : W;
         const int64_t R0 = srow[T.s0], R1 = srow[T.s1];
-        const int32_t sw0 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * warp / W);
-        const int32_t sw1 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (warp + 1) / W);
+        const int u0 = TWO ? 2 * warp : warp;
+        const int32_t sw0 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * u0 / NS);
+        const int32_t sw1 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 1) / NS);
+        const int32_t sw2 = TWO ? lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 2) / NS) : sw1;
         const int64_t r_begin = srow[sw0];
         int64_t nrows = srow[sw1] - r_begin;
-        if (T.npass > 1 && nrows > a.bnd_stride) {      // boundary buffer too small: refuse
-            if (lane == 0) atomicExch(a.err, 1);
-            nrows = 0;
+        int64_t nrows_hi = srow[sw2] - srow[sw1];
+        if (T.npass > 1 && (nrows > a.bnd_stride || nrows_hi > a.bnd_stride)) {
+            if (lane == 0) atomicExch(a.err, 1);      // boundary buffer too small: refuse
+            nrows = nrows_hi = 0;
         }
         const uint8_t* stream = a.streams + B.stream + r_begin;
+        const uint8_t* stream_hi = a.streams + B.stream + srow[sw1];
 
         for (int pass = 0; pass < T.npass; ++pass) {
             const int64_t c0 = (int64_t)pass * G::COLS;
@@ -234,9 +350,14 @@ sw16_kernel(const __grid_constant__ SwArgs a)
                 prof[x * G::ROWW + ln * G::LS + k] = pack2(sl, sh);
             }
             __syncthreads();
-            if (nrows > 0)
+            if (TWO) {
+                if (nrows > 0 || nrows_hi > 0)
+                    warp_dp16_two<R>(a, B, prof, stream, nrows, stream_hi, nrows_hi, pass, T.npass,
+                                     bnd, sw0, sw1, T.k, ns_lo);
+            } else if (nrows > 0) {
                 warp_dp16<R>(a, B, prof, stream, nrows, pass, T.npass, bnd, sw0, T.k, ns_lo,
                              ns_hi, T.hi_valid != 0);
+            }
             __syncthreads();
         }
     }
@@ -484,29 +605,29 @@ __global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ Sw
     }
 }
 
-template <int R, int W>
+template <int R, int W, bool TWO>
 cudaError_t launch_one(int grid, const SwArgs& a, cudaStream_t st)
 {
     const int smem = Geo<R>::PROF_WORDS * 4 + 2 * Geo<R>::COLS;
-    cudaError_t e = cudaFuncSetAttribute(sw16_kernel<R, W>,
+    cudaError_t e = cudaFuncSetAttribute(sw16_kernel<R, W, TWO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    sw16_kernel<R, W><<<grid, W * 32, smem, st>>>(a);
+    sw16_kernel<R, W, TWO><<<grid, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int W>
+template <int W, bool TWO>
 cudaError_t launch_w(int R, int grid, const SwArgs& a, cudaStream_t st)
 {
     switch (R) {
-    case 4: return launch_one<4, W>(grid, a, st);
-    case 8: return launch_one<8, W>(grid, a, st);
-    case 12: return launch_one<12, W>(grid, a, st);
-    case 16: return launch_one<16, W>(grid, a, st);
-    case 20: return launch_one<20, W>(grid, a, st);
-    case 24: return launch_one<24, W>(grid, a, st);
-    case 28: return launch_one<28, W>(grid, a, st);
-    case 32: return launch_one<32, W>(grid, a, st);
+    case 4: return launch_one<4, W, TWO>(grid, a, st);
+    case 8: return launch_one<8, W, TWO>(grid, a, st);
+    case 12: return launch_one<12, W, TWO>(grid, a, st);
+    case 16: return launch_one<16, W, TWO>(grid, a, st);
+    case 20: return launch_one<20, W, TWO>(grid, a, st);
+    case 24: return launch_one<24, W, TWO>(grid, a, st);
+    case 28: return launch_one<28, W, TWO>(grid, a, st);
+    case 32: return launch_one<32, W, TWO>(grid, a, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -515,13 +636,17 @@ template <int R, int W>
 int occ_one()
 {
     const int smem = Geo<R>::PROF_WORDS * 4 + 2 * Geo<R>::COLS;
-    if (cudaFuncSetAttribute(sw16_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess)
-        return 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sw16_kernel<R, W>, W * 32, smem) !=
-        cudaSuccess)
-        return 1;
+    int n = 1 << 30;
+    for (int two = 0; two < 2; ++two) {
+        auto f = two ? sw16_kernel<R, W, true> : sw16_kernel<R, W, false>;
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess)
+            return 1;
+        int m = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, f, W * 32, smem) != cudaSuccess)
+            return 1;
+        n = std::min(n, m);
+    }
     return n;
 }
 
@@ -572,12 +697,15 @@ int sw16_smem_bytes(int R)
     return kProfRows * 32 * LS * 4 + 2 * 32 * R;
 }
 
-cudaError_t launch_sw16(int R, int W, int grid, const SwArgs& a, cudaStream_t st)
+cudaError_t launch_sw16(int R, int W, bool two, int grid, const SwArgs& a, cudaStream_t st)
 {
-    switch (W) {
-    case 4: return launch_w<4>(R, grid, a, st);
-    case 8: return launch_w<8>(R, grid, a, st);
-    case 16: return launch_w<16>(R, grid, a, st);
+    switch (W * 2 + (two ? 1 : 0)) {
+    case 8: return launch_w<4, false>(R, grid, a, st);
+    case 9: return launch_w<4, true>(R, grid, a, st);
+    case 16: return launch_w<8, false>(R, grid, a, st);
+    case 17: return launch_w<8, true>(R, grid, a, st);
+    case 32: return launch_w<16, false>(R, grid, a, st);
+    case 33: return launch_w<16, true>(R, grid, a, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -144,3 +144,50 @@ def test_trained_ranker_prunes_with_high_recall(ctx):
     assert rr >= 0.98 * rp
     assert ranked["stats"]["rep_comparisons"] < 0.9 * plain["stats"]["rep_comparisons"]
     assert ranked["stats"]["comparisons_scored"] < plain["stats"]["comparisons_scored"]
+
+
+def test_ranked_merge_prune_everything_large_matches_oracle(ctx):
+    """A threshold above every logit prunes all pairs of merges at or above min_pairs; merges
+    below it stay exact.  The oracle with keep = False reproduces this exactly."""
+    ss = synth.small_families()
+    n = len(ss)
+    ctx.ranker_set_params(R.init_params(21).astype(np.float32))
+    truth, scores = oracle.all_pairs(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, T=100)
+    M = np.zeros((n, n), np.int64)
+    M[np.triu_indices(n, 1)] = scores
+    M = M + M.T
+    for min_pairs in (4, 64, 1000):
+        want = oracle.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, T=100, mT=138,
+                                    mU=15, score_matrix=M, keep=lambda a, b: False,
+                                    min_pairs=min_pairs)
+        got = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, 100, 138, 15,
+                                use_ranker=True, prune_logit=1e30, ranker_min_pairs=min_pairs)
+        assert got["clusters"] == want["clusters"]
+        assert got["pairs"].tolist() == want["pairs"].tolist()
+        st, ws = got["stats"], want["stats"]
+        assert (st["rep_comparisons"], st["exchange_comparisons"], st["intra_comparisons"]) == \
+            (ws["rep"], ws["exchange"], ws["intra"])
+        assert st["ranker_selected"] == 0
+
+
+def test_selection_kernel_keeps_the_pairs_above_threshold(ctx):
+    """With full merges disabled every pair of sequences meets exactly once as a rep pair, so
+    the tensor-core selection must keep exactly the pairs whose logit (computed by the separate
+    head kernel) reaches the threshold -- up to pairs within BF16 error of it."""
+    ss = synth.small_families()
+    n = len(ss)
+    ctx.ranker_init(4)
+    ctx.ranker_standardize(ss.seqs, ss.offsets, max_sample=200)
+    pairs = oracle.triangle_pairs(n)
+    z = ctx.ranker_logits(ss.seqs, ss.offsets, pairs)
+    thr = float(np.quantile(z, 0.7))
+    res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, 100, 10 ** 6, 15,
+                            use_ranker=True, prune_logit=thr, ranker_min_pairs=0)
+    st = res["stats"]
+    want = int((z >= thr).sum())
+    ambiguous = int((np.abs(z - thr) < 0.05).sum())
+    assert abs(st["ranker_selected"] - want) <= ambiguous
+    assert st["rep_comparisons"] == st["ranker_selected"]
+    truth, _ = oracle.all_pairs(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, T=100)
+    tset = {(int(i), int(j)) for i, j, _ in truth}
+    assert all((int(i), int(j)) in tset for i, j, _ in res["pairs"])

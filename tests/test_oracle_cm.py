@@ -145,3 +145,21 @@ def test_lookup_and_direct_scoring_agree(small):
     b = oracle.cluster_merge(sub.seqs, sub.offsets, S, 11, 1, T=60, mT=83, mU=15)
     assert a["clusters"] == b["clusters"]
     assert a["pairs"].tolist() == b["pairs"].tolist()
+
+
+def test_pruning_hook_keep_all_is_plain_and_keep_none_skips_large_merges():
+    F = {(0, 1): 50, (0, 2): 40, (1, 2): 5, (0, 3): 12, (1, 3): 30, (2, 3): 3}
+    plain, st = run(4, F, {})
+
+    def score(x, y):
+        return F[(min(x, y), max(x, y))]
+
+    final, st2 = bottom_up_merge(4, score, lambda a, b, s: (False, False), T,
+                                 keep=lambda a, b: True, min_pairs=0)
+    assert [(c.rep, list(c.objs)) for c in final] == plain and st2["rep"] == st["rep"]
+    # merges of two singletons (1 pair) stay exact below min_pairs=2; the final 2x2 merge is
+    # pruned entirely, so no rep comparison happens there
+    final, st3 = bottom_up_merge(4, score, lambda a, b, s: (False, False), T,
+                                 keep=lambda a, b: False, min_pairs=2)
+    assert st3["rep"] == 2
+    assert [(c.rep, list(c.objs)) for c in final] == [(0, [0, 1]), (1, [1, 0]), (2, [2]), (3, [3])]
