@@ -160,12 +160,12 @@ int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t
 // ---- planning ---------------------------------------------------------------------------
 void choose_R(int64_t m, int* R, int* npass)
 {
-    if (m <= 0) { *R = 4; *npass = 1; return; }
+    if (m <= 0) { *R = 2; *npass = 1; return; }
     const int np = (int)((m + 1023) / 1024);
     const int64_t per = (m + np - 1) / np;
     int r = (int)((per + 31) / 32);
-    r = (r + 3) / 4 * 4;
-    r = std::max(4, std::min(32, r));
+    r = (r + 1) / 2 * 2;                         // register tiles of 2..32 columns per lane
+    r = std::max(2, std::min(32, r));
     *R = r;
     *npass = np;
 }
@@ -267,7 +267,7 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     // boundary buffer for multi-pass queries and for the int32 rerun
     const int64_t stride = std::max<int64_t>(plan.max_warp_rows, P.maxlen) + 64;
     int max_ctas = 0;
-    for (int R = 4; R <= 32; R += 4)
+    for (int R = 2; R <= 32; R += 2)
         max_ctas = std::max(max_ctas, c->num_sms * std::max(1, sw16_ctas_per_sm(R, W)));
     const int64_t nwarps = std::max<int64_t>((int64_t)max_ctas * W,
                                              (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));

@@ -1,679 +1,22 @@
-// Batched Smith-Waterman (Gotoh affine gaps) on sm_103a: the similarity f of the paper's
-// protein clustering (Sec. 4), scored for many pairs at once.
-//
-// Recurrences (a gap of k residues costs o + (k-1)e; H >= 0 makes the alignment local):
-//   E(r,c) = max(E(r,c-1) - e, H(r,c-1) - o)
-//   F(r,c) = max(F(r-1,c) - e, H(r-1,c) - o)
-//   H(r,c) = max(0, H(r-1,c-1) + S(q_c, x_r), E(r,c), F(r,c)),   score = max H
-//
-// Mapping.  A warp owns 32*R query columns (lane l holds columns l*R .. l*R+R-1 in
-// registers) and streams subject rows through an anti-diagonal wavefront: at step t lane l
-// computes row t-l of its columns, receiving H and E of its left neighbour's last column for
-// the same row by one warp shuffle.  Many subjects are concatenated in one row stream (first
-// and last rows flagged), so the fill/drain of the wavefront is paid once per stream, not once
-// per pair.  The two 16-bit halves of every register carry two different queries that share
-// the subject stream, so each packed DPX instruction advances two cells.
-//
-// Packed-int16 formulation.  Every stored value carries a bias beta >= o+e (stored = true +
-// beta), which keeps each half within [beta-o, 32767]: integer adds of packed constants then
-// never borrow across halves (they run on the IADD path, off the DPX pipe), and only the
-// maxima use DPX.  Per packed column: 4.5 ALU-pipe ops (3 viaddmax, 1 vimax3, 1/2 vimax3 for
-// the running maximum) and 2 IADDs.  If a stored best reaches 32767 - max(S), some cell may
-// have overflowed int16; that pair is marked and rescored on the int32 path, so every score
-// returned is exact.
-#include <algorithm>
-
-#include "cm_internal.h"
+// Launchers of the Smith-Waterman kernels (templates in sw16_kernel.cuh): the int16x2 kernel
+// dispatch by CTA width, the int32 rescoring kernel and the alignment-cells kernel.
+#include "sw16_kernel.cuh"
 
 namespace cm {
 
-namespace {
-
-constexpr uint32_t kFull = 0xffffffffu;
-constexpr int kSpad = -1024;   // profile entry of pad rows / pad columns (any value <= 0 works)
-
-__host__ __device__ constexpr int lane_stride(int R) { return ((R / 4) & 1) ? R : R + 4; }
-
-template <int R>
-struct Geo {
-    static constexpr int LS = lane_stride(R);       // 32-bit words per lane in a profile row
-    static constexpr int ROWW = 32 * LS;            // words per profile row (multiple of 128 B)
-    static constexpr int PROF_WORDS = kProfRows * ROWW;
-    static constexpr int COLS = 32 * R;             // query columns per pass
-};
-
-__device__ __forceinline__ uint32_t pack2(int lo, int hi)
-{
-    return (uint32_t)(uint16_t)(int16_t)lo | ((uint32_t)(uint16_t)(int16_t)hi << 16);
-}
-
-__device__ __forceinline__ int64_t tri(int64_t k) { return k * (k - 1) / 2; }
-
-__device__ __forceinline__ int32_t lower_bound64(const int64_t* v, int32_t lo, int32_t hi,
-                                                 int64_t key)
-{
-    // first index s in [lo, hi] with v[s] >= key (v strictly increasing)
-    while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (v[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int64_t slot_of(const SwBlock& B, int32_t k, int32_t s)
-{
-    const int64_t base = (B.kind == kTri) ? (tri(k) - tri(B.k0)) : (int64_t)(k - B.k0) * B.nb;
-    return B.out_base + base + s;
-}
-
-__device__ __forceinline__ void store_score(const SwArgs& a, const SwBlock& B, int32_t k,
-                                            int32_t s, int32_t stored, int pass)
-{
-    int64_t slot = slot_of(B, k, s);
-    if (B.has_map) slot = a.out_map[slot];
-    const int32_t val = (stored >= a.sat_thr) ? kSat : stored - a.beta;
-    if (pass == 0) {
-        a.out[slot] = val;
-    } else {
-        const int32_t old = a.out[slot];
-        if (old != kSat) a.out[slot] = (val == kSat) ? kSat : max(old, val);
-    }
-}
-
-// One warp: rows [r_begin, r_begin + nrows) of the block stream against the profile tile of
-// this pass.  Lane 31 writes one score per subject per query half at the subject's last row.
-template <int R>
-__device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
-                                          const uint32_t* __restrict__ prof,
-                                          const uint8_t* __restrict__ stream, int64_t nrows,
-                                          int pass, int npass, uint2* __restrict__ bnd,
-                                          int32_t s_first, int32_t k_lo, int32_t ns_lo,
-                                          int32_t ns_hi, bool hi_valid)
-{
-    using G = Geo<R>;
-    const int lane = threadIdx.x & 31;
-    const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
-    const uint32_t BETA2 = (uint32_t)beta * 0x10001u;
-    const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;
-    const uint32_t NEGO = pack2(-o, -o);
-    const uint32_t E2 = (uint32_t)ge * 0x10001u;
-
-    uint32_t hp[R], fp[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) { hp[k] = BETA2; fp[k] = BMO2; }
-    uint32_t best = BETA2, out_h = BETA2, out_e = BMO2, out_acc = BETA2, diag0 = BETA2;
-    uint32_t cur = kPadCode, prev = kPadCode, bh = BETA2, be = BMO2;
-    int32_t s_cur = s_first;
-    const uint32_t* plane = prof + lane * G::LS;
-    const int64_t nsteps = nrows + 31;
-
-    for (int64_t t = 0; t < nsteps; ++t) {
-        const int j = (int)(t & 31);
-        if (j == 0) {
-            prev = cur;
-            const int64_t r = t + lane;
-            cur = (r < nrows) ? (uint32_t)stream[r] : (uint32_t)kPadCode;
-            if (pass > 0) {
-                if (r < nrows) { const uint2 v = bnd[r]; bh = v.x; be = v.y; }
-                else { bh = BETA2; be = BMO2; }
-            }
-        }
-        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-        uint32_t hl = __shfl_up_sync(kFull, out_h, 1);
-        uint32_t el = __shfl_up_sync(kFull, out_e, 1);
-        uint32_t ai = __shfl_up_sync(kFull, out_acc, 1);
-        if (pass > 0) {
-            const uint32_t x = __shfl_sync(kFull, bh, j);
-            const uint32_t y = __shfl_sync(kFull, be, j);
-            if (lane == 0) { hl = x; el = y; }
-        } else if (lane == 0) {
-            hl = BETA2; el = BMO2;
-        }
-        if (lane == 0) ai = BETA2;
-        uint32_t dg = diag0;
-        diag0 = hl;
-        if (rv & kFirst) {
-#pragma unroll
-            for (int k = 0; k < R; ++k) { hp[k] = BETA2; fp[k] = BMO2; }
-            best = BETA2;
-            dg = BETA2;
-        }
-        const uint32_t* prow = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-        uint32_t h = hl, e = el, hprev = BETA2;
-#pragma unroll
-        for (int j4 = 0; j4 < R / 4; ++j4) {
-            const uint4 sv = *reinterpret_cast<const uint4*>(prow + 4 * j4);
-            const uint32_t s4[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = 4 * j4 + u;
-                e = __viaddmax_s16x2(h, NEGO, e - E2);                 // E(r,c)
-                const uint32_t f = __viaddmax_s16x2(hp[k], NEGO, fp[k] - E2);  // F(r,c)
-                fp[k] = f;
-                const uint32_t d = __viaddmax_s16x2(dg, s4[u], BETA2);  // max(diag+S, 0)
-                dg = hp[k];
-                h = __vimax3_s16x2(d, e, f);                            // H(r,c)
-                hp[k] = h;
-                if (u & 1) best = __vimax3_s16x2(best, h, hprev); else hprev = h;
-            }
-        }
-        out_h = h;
-        out_e = e;
-        out_acc = __vmaxs2(ai, best);
-        if ((rv & kLast) && lane == 31) {
-            const int32_t s = s_cur++;
-            const int32_t lo = (int32_t)(int16_t)(out_acc & 0xffffu);
-            const int32_t hi = (int32_t)(int16_t)(out_acc >> 16);
-            if (s < ns_lo) store_score(a, B, k_lo, s, lo, pass);
-            if (hi_valid && s < ns_hi) store_score(a, B, k_lo + 1, s, hi, pass);
-        }
-        if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_uint2(out_h, out_e);
-    }
-}
-
-// Single-query mode: the lo and hi halves run two different subject streams (rows
-// [0, n_lo) of stream_lo and [0, n_hi) of stream_hi) against the same query.  The profile
-// holds (S, S) in both halves; per row the lo half is taken from the row of the lo residue
-// and the hi half from the row of the hi residue (one byte_perm per packed column).  First /
-// last flags, resets and score writes are per half.
-template <int R>
-__device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
-                                              const uint32_t* __restrict__ prof,
-                                              const uint8_t* __restrict__ st_lo, int64_t n_lo,
-                                              const uint8_t* __restrict__ st_hi, int64_t n_hi,
-                                              int pass, int npass, uint2* __restrict__ bnd,
-                                              int32_t s_lo0, int32_t s_hi0, int32_t k, int32_t ns)
-{
-    using G = Geo<R>;
-    const int lane = threadIdx.x & 31;
-    const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
-    const uint32_t BETA2 = (uint32_t)beta * 0x10001u;
-    const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;
-    const uint32_t NEGO = pack2(-o, -o);
-    const uint32_t E2 = (uint32_t)ge * 0x10001u;
-
-    uint32_t hp[R], fp[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) { hp[q] = BETA2; fp[q] = BMO2; }
-    uint32_t best = BETA2, out_h = BETA2, out_e = BMO2, out_acc = BETA2, diag0 = BETA2;
-    const uint32_t padpair = (uint32_t)kPadCode | ((uint32_t)kPadCode << 8);
-    uint32_t cur = padpair, prev = padpair, bh = BETA2, be = BMO2;
-    int32_t s_lo = s_lo0, s_hi = s_hi0;
-    const uint32_t* plane = prof + lane * G::LS;
-    const int64_t nrows = n_lo > n_hi ? n_lo : n_hi;
-    const int64_t nsteps = nrows + 31;
-
-    for (int64_t t = 0; t < nsteps; ++t) {
-        const int j = (int)(t & 31);
-        if (j == 0) {
-            prev = cur;
-            const int64_t r = t + lane;
-            const uint32_t lo = (r < n_lo) ? (uint32_t)st_lo[r] : (uint32_t)kPadCode;
-            const uint32_t hi = (r < n_hi) ? (uint32_t)st_hi[r] : (uint32_t)kPadCode;
-            cur = lo | (hi << 8);
-            if (pass > 0) {
-                if (r < nrows) { const uint2 v = bnd[r]; bh = v.x; be = v.y; }
-                else { bh = BETA2; be = BMO2; }
-            }
-        }
-        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-        uint32_t hl = __shfl_up_sync(kFull, out_h, 1);
-        uint32_t el = __shfl_up_sync(kFull, out_e, 1);
-        uint32_t ai = __shfl_up_sync(kFull, out_acc, 1);
-        if (pass > 0) {
-            const uint32_t x = __shfl_sync(kFull, bh, j);
-            const uint32_t y = __shfl_sync(kFull, be, j);
-            if (lane == 0) { hl = x; el = y; }
-        } else if (lane == 0) {
-            hl = BETA2; el = BMO2;
-        }
-        if (lane == 0) ai = BETA2;
-        uint32_t dg = diag0;
-        diag0 = hl;
-        if (rv & ((uint32_t)kFirst | ((uint32_t)kFirst << 8))) {
-            const uint32_t keep = ((rv & kFirst) ? 0u : 0x0000ffffu) |
-                                  ((rv & ((uint32_t)kFirst << 8)) ? 0u : 0xffff0000u);
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                hp[q] = (hp[q] & keep) | (BETA2 & ~keep);
-                fp[q] = (fp[q] & keep) | (BMO2 & ~keep);
-            }
-            best = (best & keep) | (BETA2 & ~keep);
-            dg = (dg & keep) | (BETA2 & ~keep);
-        }
-        const uint32_t* prow_lo = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-        const uint32_t* prow_hi = plane + min((rv >> 8) & 31u, (uint32_t)kPadCode) * G::ROWW;
-        uint32_t h = hl, e = el, hprev = BETA2;
-#pragma unroll
-        for (int j4 = 0; j4 < R / 4; ++j4) {
-            const uint4 sl = *reinterpret_cast<const uint4*>(prow_lo + 4 * j4);
-            const uint4 sh = *reinterpret_cast<const uint4*>(prow_hi + 4 * j4);
-            const uint32_t s4[4] = {__byte_perm(sl.x, sh.x, 0x7610), __byte_perm(sl.y, sh.y, 0x7610),
-                                    __byte_perm(sl.z, sh.z, 0x7610), __byte_perm(sl.w, sh.w, 0x7610)};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = 4 * j4 + u;
-                e = __viaddmax_s16x2(h, NEGO, e - E2);
-                const uint32_t f = __viaddmax_s16x2(hp[q], NEGO, fp[q] - E2);
-                fp[q] = f;
-                const uint32_t d = __viaddmax_s16x2(dg, s4[u], BETA2);
-                dg = hp[q];
-                h = __vimax3_s16x2(d, e, f);
-                hp[q] = h;
-                if (u & 1) best = __vimax3_s16x2(best, h, hprev); else hprev = h;
-            }
-        }
-        out_h = h;
-        out_e = e;
-        out_acc = __vmaxs2(ai, best);
-        if (lane == 31 && (rv & ((uint32_t)kLast | ((uint32_t)kLast << 8)))) {
-            if (rv & kLast) {
-                const int32_t sidx = s_lo++;
-                if (sidx < ns) store_score(a, B, k, sidx, (int32_t)(int16_t)(out_acc & 0xffffu), pass);
-            }
-            if (rv & ((uint32_t)kLast << 8)) {
-                const int32_t sidx = s_hi++;
-                if (sidx < ns) store_score(a, B, k, sidx, (int32_t)(int16_t)(out_acc >> 16), pass);
-            }
-        }
-        if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_uint2(out_h, out_e);
-    }
-}
-
-template <int R, int W, bool TWO>
-__global__ void __launch_bounds__(W * 32, 16 / W)
-sw16_kernel(const __grid_constant__ SwArgs a)
-{
-    using G = Geo<R>;
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t* prof = reinterpret_cast<uint32_t*>(smem);
-    uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;          // [2][COLS]
-    __shared__ int16_t s_mat[400];
-    __shared__ int s_task[2];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < 400; i += W * 32) s_mat[i] = a.mat[i];
-    if (tid == 0) s_task[0] = atomicAdd(a.task_counter, 1);
-    __syncthreads();
-
-    uint2* bnd = a.bnd + ((int64_t)blockIdx.x * W + warp) * a.bnd_stride;
-    for (int it = 0;; ++it) {
-        const int ti = s_task[it & 1];
-        if (ti >= a.ntasks) break;
-        if (tid == 0) s_task[(it + 1) & 1] = atomicAdd(a.task_counter, 1);
-
-        const SwTask T = a.tasks[ti];
-        const SwBlock B = a.blocks[T.block];
-        const int32_t* A_ids = a.ids + B.a_ids;
-        const int32_t q_lo = A_ids[T.k];
-        const int32_t q_hi = (!TWO && T.hi_valid) ? A_ids[T.k + 1] : q_lo;
-        const int64_t qoff_lo = a.off[q_lo], m_lo = a.off[q_lo + 1] - qoff_lo;
-        const int64_t qoff_hi = a.off[q_hi];
-        const int64_t m_hi = (TWO || T.hi_valid) ? a.off[q_hi + 1] - qoff_hi : 0;
-        const int32_t ns_lo = (B.kind == kTri) ? T.k : B.nb;
-        const int32_t ns_hi = (B.kind == kTri) ? T.k + 1 : B.nb;
-        const int64_t* srow = a.srows + B.srow;
-
-        // rows of this task split over the CTA's warp streams at subject boundaries
-        constexpr int NS = TWO ? 2 * W : W;
-        const int64_t R0 = srow[T.s0], R1 = srow[T.s1];
-        const int u0 = TWO ? 2 * warp : warp;
-        const int32_t sw0 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * u0 / NS);
-        const int32_t sw1 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 1) / NS);
-        const int32_t sw2 = TWO ? lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 2) / NS) : sw1;
-        const int64_t r_begin = srow[sw0];
-        int64_t nrows = srow[sw1] - r_begin;
-        int64_t nrows_hi = srow[sw2] - srow[sw1];
-        if (T.npass > 1 && (nrows > a.bnd_stride || nrows_hi > a.bnd_stride)) {
-            if (lane == 0) atomicExch(a.err, 1);      // boundary buffer too small: refuse
-            nrows = nrows_hi = 0;
-        }
-        const uint8_t* stream = a.streams + B.stream + r_begin;
-        const uint8_t* stream_hi = a.streams + B.stream + srow[sw1];
-
-        for (int pass = 0; pass < T.npass; ++pass) {
-            const int64_t c0 = (int64_t)pass * G::COLS;
-            for (int c = tid; c < G::COLS; c += W * 32) {
-                qres[c] = (c0 + c < m_lo) ? a.db[qoff_lo + c0 + c] : kPadCode;
-                qres[G::COLS + c] = (c0 + c < m_hi) ? a.db[qoff_hi + c0 + c] : kPadCode;
-            }
-            __syncthreads();
-            for (int i = tid; i < kProfRows * G::COLS; i += W * 32) {
-                const int x = i / G::COLS, c = i - x * G::COLS;
-                const int ln = c / R, k = c - ln * R;
-                const int ql = qres[c], qh = qres[G::COLS + c];
-                int sl = kSpad, sh = kSpad;
-                if (x != kPadCode) {
-                    if (ql != kPadCode) sl = B.swap ? s_mat[x * 20 + ql] : s_mat[ql * 20 + x];
-                    if (qh != kPadCode) sh = B.swap ? s_mat[x * 20 + qh] : s_mat[qh * 20 + x];
-                }
-                prof[x * G::ROWW + ln * G::LS + k] = pack2(sl, sh);
-            }
-            __syncthreads();
-            if (TWO) {
-                if (nrows > 0 || nrows_hi > 0)
-                    warp_dp16_two<R>(a, B, prof, stream, nrows, stream_hi, nrows_hi, pass, T.npass,
-                                     bnd, sw0, sw1, T.k, ns_lo);
-            } else if (nrows > 0) {
-                warp_dp16<R>(a, B, prof, stream, nrows, pass, T.npass, bnd, sw0, T.k, ns_lo,
-                             ns_hi, T.hi_valid != 0);
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// ---- int32 rescoring of pairs flagged by the int16 pass: one warp per pair -----------------
-template <int R>
-__global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs a,
-                                                 const PairRef* __restrict__ pr,
-                                                 int32_t npairs, int32_t* counter)
-{
-    using G = Geo<R>;
-    extern __shared__ __align__(16) uint8_t smem[];
-    int32_t* prof = reinterpret_cast<int32_t*>(smem);
-    uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;
-    __shared__ int16_t s_mat[400];
-    const int lane = threadIdx.x;
-    for (int i = lane; i < 400; i += 32) s_mat[i] = a.mat[i];
-    __syncwarp();
-    const int o = a.gap_open, ge = a.gap_extend;
-    int2* bnd = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * a.bnd_stride);
-
-    for (;;) {
-        int p = 0;
-        if (lane == 0) p = atomicAdd(counter, 1);
-        p = __shfl_sync(kFull, p, 0);
-        if (p >= npairs) break;
-        const PairRef P = pr[p];
-        const int64_t qoff = a.off[P.q], m = a.off[P.q + 1] - qoff;
-        const int64_t xoff = a.off[P.x];
-        int64_t n = a.off[P.x + 1] - xoff;
-        const int npass = (m <= G::COLS) ? 1 : (int)((m + G::COLS - 1) / G::COLS);
-        if (npass > 1 && n > a.bnd_stride) {
-            if (lane == 0) atomicExch(a.err, 1);
-            n = 0;
-        }
-        int32_t result = 0;
-        for (int pass = 0; pass < npass; ++pass) {
-            const int64_t c0 = (int64_t)pass * G::COLS;
-            __syncwarp();
-            for (int c = lane; c < G::COLS; c += 32)
-                qres[c] = (c0 + c < m) ? a.db[qoff + c0 + c] : kPadCode;
-            __syncwarp();
-            for (int i = lane; i < kProfRows * G::COLS; i += 32) {
-                const int x = i / G::COLS, c = i - x * G::COLS;
-                const int ln = c / R, k = c - ln * R;
-                const int q = qres[c];
-                int s = kSpad;
-                if (x != kPadCode && q != kPadCode) s = P.swap ? s_mat[x * 20 + q] : s_mat[q * 20 + x];
-                prof[x * G::ROWW + ln * G::LS + k] = s;
-            }
-            __syncwarp();
-            int32_t hp[R], fp[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) { hp[k] = 0; fp[k] = -o; }
-            int32_t best = 0, out_h = 0, out_e = -o, out_acc = 0, diag0 = 0;
-            uint32_t cur = kPadCode, prev = kPadCode;
-            int32_t bh = 0, be = -o;
-            const int32_t* plane = prof + lane * G::LS;
-            for (int64_t t = 0; t < n + 31; ++t) {
-                const int j = (int)(t & 31);
-                if (j == 0) {
-                    prev = cur;
-                    const int64_t r = t + lane;
-                    cur = (r < n) ? (uint32_t)a.db[xoff + r] : (uint32_t)kPadCode;
-                    if (pass > 0) {
-                        if (r < n) { const int2 v = bnd[r]; bh = v.x; be = v.y; }
-                        else { bh = 0; be = -o; }
-                    }
-                }
-                const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-                int32_t hl = __shfl_up_sync(kFull, out_h, 1);
-                int32_t el = __shfl_up_sync(kFull, out_e, 1);
-                int32_t ai = __shfl_up_sync(kFull, out_acc, 1);
-                if (pass > 0) {
-                    const int32_t x = __shfl_sync(kFull, bh, j), y = __shfl_sync(kFull, be, j);
-                    if (lane == 0) { hl = x; el = y; }
-                } else if (lane == 0) {
-                    hl = 0; el = -o;
-                }
-                if (lane == 0) ai = 0;
-                int32_t dg = diag0;
-                diag0 = hl;
-                const int32_t* prow = plane + (int)min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-                int32_t h = hl, e = el;
-#pragma unroll
-                for (int j4 = 0; j4 < R / 4; ++j4) {
-                    const int4 sv = *reinterpret_cast<const int4*>(prow + 4 * j4);
-                    const int32_t s4[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int k = 4 * j4 + u;
-                        e = __viaddmax_s32(h, -o, e - ge);
-                        const int32_t f = __viaddmax_s32(hp[k], -o, fp[k] - ge);
-                        fp[k] = f;
-                        const int32_t d = __viaddmax_s32(dg, s4[u], 0);
-                        dg = hp[k];
-                        h = __vimax3_s32(d, e, f);
-                        hp[k] = h;
-                        best = max(best, h);
-                    }
-                }
-                out_h = h;
-                out_e = e;
-                out_acc = max(ai, best);
-                const int64_t r = t - lane;
-                if (lane == 31 && n > 0 && r == n - 1) result = max(result, out_acc);
-                if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_int2(out_h, out_e);
-            }
-        }
-        if (lane == 31) a.out[P.slot] = result;
-    }
-}
-
-// ---- alignment cells: score plus the first row-major cell reaching it, one warp per job ----
-// Rows stream the job's first sequence a[0..m) (reversed when J.reverse), columns hold its
-// second sequence b[0..n) (reversed likewise); cell scores are matrix[a residue][b residue].
-// Every lane keeps the first (row, column) of its own best in row-major order (strict >); the
-// warp and the column passes then keep the largest score, then the smallest row, then the
-// smallest column.
-template <int R>
-__global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ SwArgs a,
-                                                     const CellJob* __restrict__ jobs,
-                                                     int32_t njobs, int32_t* counter,
-                                                     int32_t* __restrict__ res)
-{
-    using G = Geo<R>;
-    extern __shared__ __align__(16) uint8_t smem[];
-    int32_t* prof = reinterpret_cast<int32_t*>(smem);
-    uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;
-    __shared__ int16_t s_mat[400];
-    const int lane = threadIdx.x;
-    for (int i = lane; i < 400; i += 32) s_mat[i] = a.mat[i];
-    __syncwarp();
-    const int o = a.gap_open, ge = a.gap_extend;
-    int2* bnd = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * a.bnd_stride);
-
-    for (;;) {
-        int p = 0;
-        if (lane == 0) p = atomicAdd(counter, 1);
-        p = __shfl_sync(kFull, p, 0);
-        if (p >= njobs) break;
-        const CellJob J = jobs[p];
-        const uint8_t* ra = a.db + a.off[J.a];
-        const uint8_t* cb = a.db + a.off[J.b];
-        int64_t m = J.m;
-        const int64_t n = J.n;
-        const int npass = (n <= G::COLS) ? 1 : (int)((n + G::COLS - 1) / G::COLS);
-        if (npass > 1 && m > a.bnd_stride) {
-            if (lane == 0) atomicExch(a.err, 1);
-            m = 0;
-        }
-        int32_t gbest = 0, grow = -1, gcol = -1;
-        for (int pass = 0; pass < npass && m > 0 && n > 0; ++pass) {
-            const int64_t c0 = (int64_t)pass * G::COLS;
-            __syncwarp();
-            for (int c = lane; c < G::COLS; c += 32) {
-                const int64_t cc = c0 + c;
-                qres[c] = (cc < n) ? (J.reverse ? cb[n - 1 - cc] : cb[cc]) : kPadCode;
-            }
-            __syncwarp();
-            for (int i = lane; i < kProfRows * G::COLS; i += 32) {
-                const int x = i / G::COLS, c = i - x * G::COLS;
-                const int ln = c / R, k = c - ln * R;
-                const int q = qres[c];
-                prof[x * G::ROWW + ln * G::LS + k] =
-                    (x != kPadCode && q != kPadCode) ? s_mat[x * 20 + q] : kSpad;
-            }
-            __syncwarp();
-            int32_t hp[R], fp[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) { hp[k] = 0; fp[k] = -o; }
-            int32_t out_h = 0, out_e = -o, diag0 = 0;
-            int32_t lbest = 0, lrow = -1, lcol = -1;
-            uint32_t cur = kPadCode, prev = kPadCode;
-            int32_t bh = 0, be = -o;
-            const int32_t* plane = prof + lane * G::LS;
-            const int32_t col0 = (int32_t)c0 + lane * R;
-            for (int64_t t = 0; t < m + 31; ++t) {
-                const int j = (int)(t & 31);
-                if (j == 0) {
-                    prev = cur;
-                    const int64_t r = t + lane;
-                    cur = (r < m) ? (uint32_t)(J.reverse ? ra[m - 1 - r] : ra[r]) : (uint32_t)kPadCode;
-                    if (pass > 0) {
-                        if (r < m) { const int2 v = bnd[r]; bh = v.x; be = v.y; }
-                        else { bh = 0; be = -o; }
-                    }
-                }
-                const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-                int32_t hl = __shfl_up_sync(kFull, out_h, 1);
-                int32_t el = __shfl_up_sync(kFull, out_e, 1);
-                if (pass > 0) {
-                    const int32_t x = __shfl_sync(kFull, bh, j), y = __shfl_sync(kFull, be, j);
-                    if (lane == 0) { hl = x; el = y; }
-                } else if (lane == 0) {
-                    hl = 0; el = -o;
-                }
-                int32_t dg = diag0;
-                diag0 = hl;
-                const int32_t row = (int32_t)(t - lane);
-                const int32_t* prow = plane + (int)min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-                int32_t h = hl, e = el;
-#pragma unroll
-                for (int j4 = 0; j4 < R / 4; ++j4) {
-                    const int4 sv = *reinterpret_cast<const int4*>(prow + 4 * j4);
-                    const int32_t s4[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int k = 4 * j4 + u;
-                        e = __viaddmax_s32(h, -o, e - ge);
-                        const int32_t f = __viaddmax_s32(hp[k], -o, fp[k] - ge);
-                        fp[k] = f;
-                        const int32_t d = __viaddmax_s32(dg, s4[u], 0);
-                        dg = hp[k];
-                        h = __vimax3_s32(d, e, f);
-                        hp[k] = h;
-                        if (h > lbest) { lbest = h; lrow = row; lcol = col0 + k; }
-                    }
-                }
-                out_h = h;
-                out_e = e;
-                if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_int2(out_h, out_e);
-            }
-            // cells of pad rows / pad columns stay below the maximum over real cells, so the
-            // warp's maximum (and its first cell) lies in a real row and column
-            for (int d = 16; d >= 1; d >>= 1) {
-                const int32_t ob = __shfl_xor_sync(kFull, lbest, d);
-                const int32_t orw = __shfl_xor_sync(kFull, lrow, d);
-                const int32_t oc = __shfl_xor_sync(kFull, lcol, d);
-                const bool better = ob > lbest ||
-                                    (ob == lbest && (orw < lrow || (orw == lrow && oc < lcol)));
-                if (better) { lbest = ob; lrow = orw; lcol = oc; }
-            }
-            const bool better = lbest > gbest ||
-                                (lbest == gbest && lbest > 0 &&
-                                 (lrow < grow || (lrow == grow && lcol < gcol)));
-            if (better) { gbest = lbest; grow = lrow; gcol = lcol; }
-        }
-        if (lane == 0) {
-            res[3 * (int64_t)p] = gbest;
-            res[3 * (int64_t)p + 1] = gbest > 0 ? grow : -1;
-            res[3 * (int64_t)p + 2] = gbest > 0 ? gcol : -1;
-        }
-    }
-}
-
-template <int R, int W, bool TWO>
-cudaError_t launch_one(int grid, const SwArgs& a, cudaStream_t st)
-{
-    const int smem = Geo<R>::PROF_WORDS * 4 + 2 * Geo<R>::COLS;
-    cudaError_t e = cudaFuncSetAttribute(sw16_kernel<R, W, TWO>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    sw16_kernel<R, W, TWO><<<grid, W * 32, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int W, bool TWO>
-cudaError_t launch_w(int R, int grid, const SwArgs& a, cudaStream_t st)
-{
-    switch (R) {
-    case 4: return launch_one<4, W, TWO>(grid, a, st);
-    case 8: return launch_one<8, W, TWO>(grid, a, st);
-    case 12: return launch_one<12, W, TWO>(grid, a, st);
-    case 16: return launch_one<16, W, TWO>(grid, a, st);
-    case 20: return launch_one<20, W, TWO>(grid, a, st);
-    case 24: return launch_one<24, W, TWO>(grid, a, st);
-    case 28: return launch_one<28, W, TWO>(grid, a, st);
-    case 32: return launch_one<32, W, TWO>(grid, a, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int R, int W>
-int occ_one()
-{
-    const int smem = Geo<R>::PROF_WORDS * 4 + 2 * Geo<R>::COLS;
-    int n = 1 << 30;
-    for (int two = 0; two < 2; ++two) {
-        auto f = two ? sw16_kernel<R, W, true> : sw16_kernel<R, W, false>;
-        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess)
-            return 1;
-        int m = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, f, W * 32, smem) != cudaSuccess)
-            return 1;
-        n = std::min(n, m);
-    }
-    return n;
-}
-
-template <int W>
-int occ_w(int R)
-{
-    switch (R) {
-    case 4: return occ_one<4, W>();
-    case 8: return occ_one<8, W>();
-    case 12: return occ_one<12, W>();
-    case 16: return occ_one<16, W>();
-    case 20: return occ_one<20, W>();
-    case 24: return occ_one<24, W>();
-    case 28: return occ_one<28, W>();
-    case 32: return occ_one<32, W>();
-    default: return 1;
-    }
-}
-
-}  // namespace
+cudaError_t launch_sw16_w4(int R, bool two, int grid, const SwArgs& a, cudaStream_t st);
+cudaError_t launch_sw16_w8(int R, bool two, int grid, const SwArgs& a, cudaStream_t st);
+cudaError_t launch_sw16_w16(int R, bool two, int grid, const SwArgs& a, cudaStream_t st);
+int sw16_occ_w4(int R);
+int sw16_occ_w8(int R);
+int sw16_occ_w16(int R);
 
 int sw16_ctas_per_sm(int R, int W)
 {
     switch (W) {
-    case 4: return occ_w<4>(R);
-    case 8: return occ_w<8>(R);
-    case 16: return occ_w<16>(R);
+    case 4: return sw16_occ_w4(R);
+    case 8: return sw16_occ_w8(R);
+    case 16: return sw16_occ_w16(R);
     default: return 1;
     }
 }
@@ -699,13 +42,10 @@ int sw16_smem_bytes(int R)
 
 cudaError_t launch_sw16(int R, int W, bool two, int grid, const SwArgs& a, cudaStream_t st)
 {
-    switch (W * 2 + (two ? 1 : 0)) {
-    case 8: return launch_w<4, false>(R, grid, a, st);
-    case 9: return launch_w<4, true>(R, grid, a, st);
-    case 16: return launch_w<8, false>(R, grid, a, st);
-    case 17: return launch_w<8, true>(R, grid, a, st);
-    case 32: return launch_w<16, false>(R, grid, a, st);
-    case 33: return launch_w<16, true>(R, grid, a, st);
+    switch (W) {
+    case 4: return launch_sw16_w4(R, two, grid, a, st);
+    case 8: return launch_sw16_w8(R, two, grid, a, st);
+    case 16: return launch_sw16_w16(R, two, grid, a, st);
     default: return cudaErrorInvalidValue;
     }
 }
