@@ -265,7 +265,8 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     a.sat_thr = (flags & CM_FORCE_INT32) ? -1 : P.sat_thr;   // -1: every pair goes to int32
 
     // boundary buffer for multi-pass queries and for the int32 rerun
-    const int64_t stride = std::max<int64_t>(plan.max_warp_rows, P.maxlen) + 64;
+    // even, so the pair-mode records (16 bytes per two rows) stay 16-byte aligned
+    const int64_t stride = (std::max<int64_t>(plan.max_warp_rows, P.maxlen) + 64 + 1) & ~(int64_t)1;
     int max_ctas = 0;
     for (int R = 2; R <= 32; R += 2)
         max_ctas = std::max(max_ctas, c->num_sms * std::max(1, sw16_ctas_per_sm(R, W)));
@@ -360,7 +361,7 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
         for (int64_t s = 0; s < r.b_count; ++s) {
             const int32_t id = ids[r.b_begin + s];
             b_ids.push_back(id);
-            plan.srow.push_back(plan.srow.back() + std::max<int64_t>(P.len(id), 1));
+            plan.srow.push_back(plan.srow.back() + stream_rows(P.len(id)));
         }
         if (r.kind != kTri)
             for (int64_t k = 0; k < r.a_count; ++k) a_ids.push_back(ids[r.a_begin + k]);
@@ -618,7 +619,7 @@ int sw_score_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
             const int32_t b = hp[2 * ord[g] + 1];
             const int64_t mb = P.hoff[b + 1] - P.hoff[b];
             b_ids.push_back(b);
-            plan.srow.push_back(plan.srow.back() + std::max<int64_t>(mb, 1));
+            plan.srow.push_back(plan.srow.back() + stream_rows(mb));
             omap[(size_t)slot++] = ord[g];
             plan.cells += ma * mb;
         }
@@ -712,7 +713,7 @@ int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t 
     plan.srow.resize((size_t)n_seqs + 1);
     plan.srow[0] = 0;
     for (int32_t s = 0; s < n_seqs; ++s)
-        plan.srow[s + 1] = plan.srow[s] + std::max<int64_t>(P.hoff[L[s] + 1] - P.hoff[L[s]], 1);
+        plan.srow[s + 1] = plan.srow[s] + stream_rows(P.hoff[L[s] + 1] - P.hoff[L[s]]);
     // parts: equal shares of cells, boundaries on even k
     std::vector<double> cum((size_t)n_seqs + 1, 0.0);
     int64_t residues = 0;

@@ -56,14 +56,11 @@ __global__ void gather_kernel(const uint8_t* __restrict__ db, const int64_t* __r
         const int32_t id = ids[s];
         const int64_t b = off[id], len = off[id + 1] - b;
         uint8_t* dst = stream + srow[s];
-        if (len == 0) {
-            if (lane == 0) dst[0] = kPadCode | kFirst | kLast;
-            continue;
-        }
-        for (int64_t r = lane; r < len; r += 32) {
-            uint8_t v = db[b + r];
+        const int64_t rows = srow[s + 1] - srow[s];        // len rounded up to even, >= 2
+        for (int64_t r = lane; r < rows; r += 32) {
+            uint8_t v = (r < len) ? db[b + r] : kPadCode;
             if (r == 0) v |= kFirst;
-            if (r == len - 1) v |= kLast;
+            if (r == (len > 0 ? len - 1 : 0)) v |= kLast;
             dst[r] = v;
         }
     }

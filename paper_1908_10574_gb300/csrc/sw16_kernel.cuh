@@ -87,13 +87,16 @@ __device__ __forceinline__ void store_score(const SwArgs& a, const SwBlock& B, i
     }
 }
 
-// One warp: rows [r_begin, r_begin + nrows) of the block stream against the profile tile of
-// this pass.  Lane 31 writes one score per subject per query half at the subject's last row.
+// One warp: rows [0, nrows) of its stream (nrows even; every subject starts on an even row)
+// against the profile tile of this pass.  A step covers two rows, 2u and 2u+1: row 2u+1 trails
+// row 2u by one column inside the lane, so the two rows form independent dependency chains,
+// and the step's fixed costs (shuffles, residue and flag handling) are shared by both rows.
+// Lane 31 writes one score per subject per query half after the subject's last row.
 template <int R>
 __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
                                           const uint32_t* __restrict__ prof,
                                           const uint8_t* __restrict__ stream, int64_t nrows,
-                                          int pass, int npass, uint2* __restrict__ bnd,
+                                          int pass, int npass, uint4* __restrict__ bnd,
                                           int32_t s_first, int32_t k_lo, int32_t ns_lo,
                                           int32_t ns_hi, bool hi_valid)
 {
@@ -104,84 +107,120 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
     const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;
     const uint32_t NEGO = pack2(-o, -o);
     const uint32_t E2 = (uint32_t)ge * 0x10001u;
+    const uint32_t PADPAIR = (uint32_t)kPadCode | ((uint32_t)kPadCode << 8);
 
     uint32_t hp[R], fp[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) { hp[k] = BETA2; fp[k] = BMO2; }
-    uint32_t best = BETA2, out_h = BETA2, out_e = BMO2, out_acc = BETA2, diag0 = BETA2;
-    uint32_t cur = kPadCode, prev = kPadCode, bh = BETA2, be = BMO2;
+    uint32_t best = BETA2, out_acc = BETA2;
+    uint32_t oa_h = BETA2, oa_e = BMO2, ob_h = BETA2, ob_e = BMO2;   // last column, rows A, B
+    uint32_t diagA0 = BETA2;                     // H(2u-1, c0-1) for the next step's row A
+    uint32_t cur = PADPAIR, prev = PADPAIR;
+    uint4 bv = make_uint4(BETA2, BMO2, BETA2, BMO2);
     int32_t s_cur = s_first;
     const uint32_t* plane = prof + lane * G::LS;
-    const int64_t nsteps = nrows + 31;
+    const int64_t nsup = nrows >> 1;             // super-rows of two rows
+    const int64_t nsteps = nsup + 31;
+    const uint16_t* st16 = reinterpret_cast<const uint16_t*>(stream);
 
     for (int64_t t = 0; t < nsteps; ++t) {
         const int j = (int)(t & 31);
         if (j == 0) {
             prev = cur;
-            const int64_t r = t + lane;
-            cur = (r < nrows) ? (uint32_t)stream[r] : (uint32_t)kPadCode;
+            const int64_t u = t + lane;
+            cur = (u < nsup) ? (uint32_t)st16[u] : PADPAIR;
             if (pass > 0) {
-                if (r < nrows) { const uint2 v = bnd[r]; bh = v.x; be = v.y; }
-                else { bh = BETA2; be = BMO2; }
+                if (u < nsup) bv = bnd[u];
+                else bv = make_uint4(BETA2, BMO2, BETA2, BMO2);
             }
         }
         const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-        uint32_t hl = __shfl_up_sync(kFull, out_h, 1);
-        uint32_t el = __shfl_up_sync(kFull, out_e, 1);
+        uint32_t haL = __shfl_up_sync(kFull, oa_h, 1);
+        uint32_t eaL = __shfl_up_sync(kFull, oa_e, 1);
+        uint32_t hbL = __shfl_up_sync(kFull, ob_h, 1);
+        uint32_t ebL = __shfl_up_sync(kFull, ob_e, 1);
         uint32_t ai = __shfl_up_sync(kFull, out_acc, 1);
         if (pass > 0) {
-            const uint32_t x = __shfl_sync(kFull, bh, j);
-            const uint32_t y = __shfl_sync(kFull, be, j);
-            if (lane == 0) { hl = x; el = y; }
+            const uint32_t x0 = __shfl_sync(kFull, bv.x, j), x1 = __shfl_sync(kFull, bv.y, j);
+            const uint32_t x2 = __shfl_sync(kFull, bv.z, j), x3 = __shfl_sync(kFull, bv.w, j);
+            if (lane == 0) { haL = x0; eaL = x1; hbL = x2; ebL = x3; }
         } else if (lane == 0) {
-            hl = BETA2; el = BMO2;
+            haL = BETA2; eaL = BMO2; hbL = BETA2; ebL = BMO2;
         }
         if (lane == 0) ai = BETA2;
-        uint32_t dg = diag0;
-        diag0 = hl;
-        if (rv & kFirst) {
+        uint32_t dgA = diagA0;
+        diagA0 = hbL;
+        if (rv & kFirst) {                       // a subject starts at row 2u
 #pragma unroll
             for (int k = 0; k < R; ++k) { hp[k] = BETA2; fp[k] = BMO2; }
             best = BETA2;
-            dg = BETA2;
+            dgA = BETA2;
         }
-        const uint32_t* prow = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-        uint32_t h = hl, e = el, hprev = BETA2;
+        const uint32_t* prowA = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
+        const uint32_t* prowB = plane + min((rv >> 8) & 31u, (uint32_t)kPadCode) * G::ROWW;
+        uint32_t hA = haL, eA = eaL, hB = hbL, eB = ebL, dgB = haL;
+        uint32_t sBprev = 0;
 #pragma unroll
         for (int j4 = 0; j4 < (R + 3) / 4; ++j4) {
-            uint32_t s4[4];
+            uint32_t sa[4], sb[4];
             if (4 * j4 + 4 <= R) {
-                const uint4 sv = *reinterpret_cast<const uint4*>(prow + 4 * j4);
-                s4[0] = sv.x; s4[1] = sv.y; s4[2] = sv.z; s4[3] = sv.w;
+                const uint4 va = *reinterpret_cast<const uint4*>(prowA + 4 * j4);
+                const uint4 vb = *reinterpret_cast<const uint4*>(prowB + 4 * j4);
+                sa[0] = va.x; sa[1] = va.y; sa[2] = va.z; sa[3] = va.w;
+                sb[0] = vb.x; sb[1] = vb.y; sb[2] = vb.z; sb[3] = vb.w;
             } else {
-                const uint2 sv = *reinterpret_cast<const uint2*>(prow + 4 * j4);
-                s4[0] = sv.x; s4[1] = sv.y; s4[2] = s4[3] = 0;
+                const uint2 va = *reinterpret_cast<const uint2*>(prowA + 4 * j4);
+                const uint2 vb = *reinterpret_cast<const uint2*>(prowB + 4 * j4);
+                sa[0] = va.x; sa[1] = va.y; sa[2] = sa[3] = 0;
+                sb[0] = vb.x; sb[1] = vb.y; sb[2] = sb[3] = 0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = 4 * j4 + u;
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * j4 + q;
                 if (k >= R) break;
-                e = __viaddmax_s16x2(h, NEGO, e - E2);                 // E(r,c)
-                const uint32_t f = __viaddmax_s16x2(hp[k], NEGO, fp[k] - E2);  // F(r,c)
-                fp[k] = f;
-                const uint32_t d = __viaddmax_s16x2(dg, s4[u], BETA2);  // max(diag+S, 0)
-                dg = hp[k];
-                h = __vimax3_s16x2(d, e, f);                            // H(r,c)
-                hp[k] = h;
-                if (u & 1) best = __vimax3_s16x2(best, h, hprev); else hprev = h;
+                // row A = 2u, column k
+                eA = __viaddmax_s16x2(hA, NEGO, eA - E2);
+                const uint32_t fA = __viaddmax_s16x2(hp[k], NEGO, fp[k] - E2);
+                const uint32_t dA = __viaddmax_s16x2(dgA, sa[q], BETA2);
+                dgA = hp[k];
+                hA = __vimax3_s16x2(dA, eA, fA);
+                // row B = 2u+1, column k-1 (reads row A's column k-1, written last iteration)
+                if (k > 0) {
+                    eB = __viaddmax_s16x2(hB, NEGO, eB - E2);
+                    const uint32_t fB = __viaddmax_s16x2(hp[k - 1], NEGO, fp[k - 1] - E2);
+                    const uint32_t dB = __viaddmax_s16x2(dgB, sBprev, BETA2);
+                    dgB = hp[k - 1];
+                    hB = __vimax3_s16x2(dB, eB, fB);
+                    hp[k - 1] = hB;
+                    fp[k - 1] = fB;
+                    best = __vimax3_s16x2(best, hB, hA);
+                } else {
+                    best = __vmaxs2(best, hA);
+                }
+                hp[k] = hA;
+                fp[k] = fA;
+                sBprev = sb[q];
             }
         }
-        out_h = h;
-        out_e = e;
+        {   // row B, last column
+            eB = __viaddmax_s16x2(hB, NEGO, eB - E2);
+            const uint32_t fB = __viaddmax_s16x2(hp[R - 1], NEGO, fp[R - 1] - E2);
+            const uint32_t dB = __viaddmax_s16x2(dgB, sBprev, BETA2);
+            hB = __vimax3_s16x2(dB, eB, fB);
+            hp[R - 1] = hB;
+            fp[R - 1] = fB;
+            best = __vmaxs2(best, hB);
+        }
+        oa_h = hA; oa_e = eA; ob_h = hB; ob_e = eB;
         out_acc = __vmaxs2(ai, best);
-        if ((rv & kLast) && lane == 31) {
+        if (lane == 31 && (rv & ((uint32_t)kLast | ((uint32_t)kLast << 8)))) {
             const int32_t s = s_cur++;
             const int32_t lo = (int32_t)(int16_t)(out_acc & 0xffffu);
             const int32_t hi = (int32_t)(int16_t)(out_acc >> 16);
             if (s < ns_lo) store_score(a, B, k_lo, s, lo, pass);
             if (hi_valid && s < ns_hi) store_score(a, B, k_lo + 1, s, hi, pass);
         }
-        if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_uint2(out_h, out_e);
+        if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_uint4(oa_h, oa_e, ob_h, ob_e);
     }
 }
 
@@ -320,6 +359,7 @@ sw16_kernel(const __grid_constant__ SwArgs a)
     __syncthreads();
 
     uint2* bnd = a.bnd + ((int64_t)blockIdx.x * W + warp) * a.bnd_stride;
+    uint4* bnd4 = reinterpret_cast<uint4*>(bnd);          // pair mode: one uint4 per two rows
     for (int it = 0;; ++it) {
         const int ti = s_task[it & 1];
         if (ti >= a.ntasks) break;
@@ -378,7 +418,7 @@ sw16_kernel(const __grid_constant__ SwArgs a)
                     warp_dp16_two<R>(a, B, prof, stream, nrows, stream_hi, nrows_hi, pass, T.npass,
                                      bnd, sw0, sw1, T.k, ns_lo);
             } else if (nrows > 0) {
-                warp_dp16<R>(a, B, prof, stream, nrows, pass, T.npass, bnd, sw0, T.k, ns_lo,
+                warp_dp16<R>(a, B, prof, stream, nrows, pass, T.npass, bnd4, sw0, T.k, ns_lo,
                              ns_hi, T.hi_valid != 0);
             }
             __syncthreads();
