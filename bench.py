@@ -355,9 +355,17 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = cm.Context(local)
+    ss = make_set()
+    tuning = {"source": "autotune"}
     if args.warps or args.rows:
         ctx.set_tuning(args.warps, args.rows)
-    ss = make_set()
+        tuning.update(source="command line", warps_per_cta=args.warps, rows_per_warp=args.rows)
+    else:
+        t0 = time.perf_counter()
+        w, r = ctx.autotune(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, sample_seqs=3000)
+        tuning.update(warps_per_cta=w, rows_per_warp=r,
+                      autotune_seconds=round(time.perf_counter() - t0, 2))
+    ctx.reset_stats()
     n_parts = args.parts_per_gpu * world
     seq = part_sequence(n_parts, (args.warmup + args.steps) * world)
     my_parts = seq[rank::world]
@@ -456,8 +464,7 @@ def main():
                           "cells_timed": int(cells_all), "significant_pairs_timed": found,
                           "parts_timed": my_parts[args.warmup:], "n_parts": n_parts,
                           "l2": "flushed between timed steps (256 MiB write)",
-                          "tuning": {"warps_per_cta": args.warps or 8,
-                                     "rows_per_warp": args.rows or 4096}},
+                          "tuning": tuning},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(st["launches"]), "clocks": clocks}
         print(json.dumps(out), flush=True)

@@ -77,6 +77,15 @@ int cm_set_stream(cm_ctx *ctx, void *cuda_stream);
  * warp stream (256 .. 65536).  0 keeps the current value.  The autotuner sets these. */
 int cm_set_tuning(cm_ctx *ctx, int32_t warps_per_cta, int32_t rows_per_warp);
 
+/* Autotuner: scores the all-against-all of a length-stratified sample of `sample_seqs` of the
+ * given sequences (0 = 3000) under every CTA width (4, 8, 16 warps) and warp-stream length
+ * (4096 .. 32768 rows), keeps the fastest (CUDA-event time of the int16x2 kernel per cell) as
+ * the context's tuning and reports it.  With cache_path (may be NULL) the choice is looked up
+ * first and appended after measuring, keyed by GPU name, SM count and median length bucket. */
+int cm_autotune(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                const int8_t *matrix, int32_t gap_open, int32_t gap_extend, int32_t sample_seqs,
+                const char *cache_path, int32_t *warps_out, int32_t *rows_out, uint32_t flags);
+
 /* Counters of the work done since cm_create or the last cm_reset_stats. */
 typedef struct {
     int64_t pairs;              /* pairs scored */

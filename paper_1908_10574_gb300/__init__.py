@@ -102,6 +102,19 @@ class Context:
     def reset_stats(self):
         _L.check(self._h, _L.lib().cm_reset_stats(self._h))
 
+    def autotune(self, seqs, offsets, matrix, gap_open, gap_extend, sample_seqs=0,
+                 cache_path=None, flags=0):
+        """Pick the CTA width and warp-stream length by timing a sample (see cm_autotune);
+        returns (warps_per_cta, rows_per_warp)."""
+        seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
+        flags |= self._prep([seqs, offsets, matrix])
+        w, r = ctypes.c_int32(0), ctypes.c_int32(0)
+        _L.check(self._h, _L.lib().cm_autotune(
+            self._h, _ptr(seqs), _ptr(offsets), int(offsets.shape[0]) - 1, _ptr(matrix),
+            int(gap_open), int(gap_extend), int(sample_seqs),
+            cache_path.encode() if cache_path else None, ctypes.byref(w), ctypes.byref(r), flags))
+        return w.value, r.value
+
     def set_tuning(self, warps_per_cta=0, rows_per_warp=0):
         _L.check(self._h, _L.lib().cm_set_tuning(self._h, int(warps_per_cta), int(rows_per_warp)))
 

@@ -77,6 +77,8 @@ def lib():
         "cm_set_stream": (ctypes.c_int, [p, p]),
         "cm_set_tuning": (ctypes.c_int, [p, i32, i32]),
         "cm_get_stats": (ctypes.c_int, [p, ctypes.POINTER(cm_stats)]),
+        "cm_autotune": (ctypes.c_int, [p, p, p, i32, p, i32, i32, i32, ctypes.c_char_p,
+                                       ctypes.POINTER(i32), ctypes.POINTER(i32), u32]),
         "cm_reset_stats": (ctypes.c_int, [p]),
         "sw_score_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
         "sw_cells_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),

@@ -490,6 +490,81 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
     return CM_OK;
 }
 
+// Plan of part `part` of `n_parts` (about equal cell counts) of the all-against-all triangle:
+// one TRI block over the sequences in length order (ties by index), so that every pair's
+// query is the longer sequence.  L receives that order, k0 the first query row of the part.
+void allpairs_plan(cm_ctx* c, const Prepared& P, int32_t n_seqs, int64_t part, int64_t n_parts,
+                   std::vector<int32_t>& L, int32_t& k0_out, Plan& plan)
+{
+    L.resize((size_t)n_seqs);
+    std::iota(L.begin(), L.end(), 0);
+    std::stable_sort(L.begin(), L.end(), [&](int32_t x, int32_t y) {
+        return P.hoff[x + 1] - P.hoff[x] < P.hoff[y + 1] - P.hoff[y];
+    });
+    plan.srow.resize((size_t)n_seqs + 1);
+    plan.srow[0] = 0;
+    for (int32_t s = 0; s < n_seqs; ++s)
+        plan.srow[s + 1] = plan.srow[s] + stream_rows(P.hoff[L[s] + 1] - P.hoff[L[s]]);
+    // parts: equal shares of cells, boundaries on even k
+    std::vector<double> cum((size_t)n_seqs + 1, 0.0);
+    int64_t residues = 0;
+    for (int32_t k = 0; k < n_seqs; ++k) {
+        const int64_t mk = P.hoff[L[k] + 1] - P.hoff[L[k]];
+        cum[k + 1] = cum[k] + (double)mk * (double)residues;
+        residues += mk;
+    }
+    auto kb = [&](int64_t p) -> int32_t {
+        if (p <= 0) return 0;
+        if (p >= n_parts) return n_seqs;
+        const double want = cum[n_seqs] * (double)p / (double)n_parts;
+        int32_t k = (int32_t)(std::lower_bound(cum.begin(), cum.end(), want) - cum.begin());
+        k &= ~1;
+        return std::min(k, n_seqs);
+    };
+    const int32_t k0 = kb(part), k1 = kb(part + 1);
+    SwBlock B{};
+    B.kind = kTri;
+    B.swap = 0;
+    B.na = n_seqs;
+    B.nb = n_seqs;
+    B.a_ids = 0;
+    B.b_ids = 0;
+    B.stream = 0;
+    B.srow = 0;
+    B.out_base = 0;
+    B.k0 = k0;
+    B.has_map = 0;
+    plan.blocks.push_back(B);
+    plan.first_slot.push_back(0);
+    plan.ids = L;
+    auto tri = [](int64_t k) { return k * (k - 1) / 2; };
+    plan.nslots = tri(k1) - tri(k0);
+    plan.pairs = plan.nslots;
+    const int64_t target = (int64_t)c->W * c->rows_per_warp;
+    for (int32_t k = k0; k < k1; k += 2) {
+        const bool hi = (k + 1 < k1);
+        const int32_t ns = hi ? k + 1 : k;
+        const int64_t m_hi = P.hoff[L[hi ? k + 1 : k] + 1] - P.hoff[L[hi ? k + 1 : k]];
+        if (ns > 0) add_tasks(plan, 0, k, ns, hi, m_hi, plan.srow.data(), target);
+    }
+    {   // cells = sum over pairs of len(a) * len(b)
+        int64_t acc = 0, pre = 0;
+        for (int32_t k = 0; k < k1; ++k) {
+            const int64_t mk = P.hoff[L[k] + 1] - P.hoff[L[k]];
+            if (k >= k0) acc += mk * pre;
+            pre += mk;
+        }
+        plan.cells = acc;
+    }
+    order_tasks(plan);
+    int64_t maxlen_rows = 1;
+    for (int32_t s = 0; s < n_seqs; ++s)
+        maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
+    plan.max_warp_rows = 2 * c->rows_per_warp + 2 * maxlen_rows + 2 * target / c->W;
+
+    k0_out = k0;
+}
+
 }  // namespace cm
 
 // =========================================================================================
@@ -686,6 +761,94 @@ int sw_cells_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
     return CM_OK;
 }
 
+int cm_autotune(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                const int8_t* matrix, int32_t gap_open, int32_t gap_extend, int32_t sample_seqs,
+                const char* cache_path, int32_t* warps_out, int32_t* rows_out, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    Prepared P;
+    int r = prepare(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, flags, P);
+    if (r) return r;
+    if (n_seqs < 2) return fail(c, CM_ERR_ARG, "autotune needs at least 2 sequences");
+    // length profile of the set: median length bucket (powers of two)
+    std::vector<int64_t> lens((size_t)n_seqs);
+    for (int32_t i = 0; i < n_seqs; ++i) lens[i] = P.len(i);
+    std::vector<int64_t> sl = lens;
+    std::nth_element(sl.begin(), sl.begin() + sl.size() / 2, sl.end());
+    int bucket = 0;
+    while (bucket < 30 && ((int64_t)1 << bucket) < sl[sl.size() / 2]) ++bucket;
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, c->device));
+    char key[256];
+    std::snprintf(key, sizeof(key), "%s|%d|%d", prop.name, prop.multiProcessorCount, bucket);
+    for (char* q = key; *q; ++q)
+        if (*q == ' ') *q = '_';
+    if (cache_path) {
+        FILE* f = std::fopen(cache_path, "r");
+        if (f) {
+            char k2[256];
+            int w = 0, rw = 0;
+            while (std::fscanf(f, "%255s %d %d", k2, &w, &rw) == 3) {
+                if (std::strcmp(k2, key) == 0 && cm_set_tuning(c, w, rw) == CM_OK) {
+                    std::fclose(f);
+                    if (warps_out) *warps_out = c->W;
+                    if (rows_out) *rows_out = c->rows_per_warp;
+                    return CM_OK;
+                }
+            }
+            std::fclose(f);
+        }
+    }
+    // timing sample: the middle part of the caller's own all-against-all, so that query
+    // lengths and subject-stream lengths are those of the real workload
+    (void)sample_seqs;
+    std::vector<int32_t> Lord;
+    Plan plan0;
+    int32_t k0 = 0;
+    const int64_t nparts = std::max<int64_t>(1, std::min<int64_t>(256, n_seqs / 4));
+    allpairs_plan(c, P, n_seqs, nparts / 2, nparts, Lord, k0, plan0);
+    if (plan0.tasks.empty()) return fail(c, CM_ERR_ARG, "autotune sample is empty");
+    int32_t* d_out;
+    ENSURE(B_OUT, plan0.nslots, d_out);
+    const int Ws[3] = {4, 8, 16};
+    const int Rs[4] = {4096, 8192, 16384, 32768};
+    const int W0 = c->W, R0 = c->rows_per_warp;
+    double best_rate = -1.0;
+    int bw = W0, brw = R0;
+    for (int wi = 0; wi < 3; ++wi)
+        for (int ri = 0; ri < 4; ++ri) {
+            c->W = Ws[wi];
+            c->rows_per_warp = Rs[ri];
+            double ms = 0.0;
+            int64_t cells = 0;
+            Plan plan;
+            allpairs_plan(c, P, n_seqs, nparts / 2, nparts, Lord, k0, plan);
+            for (int rep = 0; rep < 2; ++rep) {       // first run warms up, second is timed
+                const double ms0 = c->stats.sw16_ms;
+                const int64_t c0 = c->stats.cells;
+                r = run_plan(c, P, plan, d_out, nullptr, flags);
+                if (r) { c->W = W0; c->rows_per_warp = R0; return r; }
+                ms = c->stats.sw16_ms - ms0;
+                cells = c->stats.cells - c0;
+            }
+            const double rate = ms > 0 ? (double)cells / ms : 0.0;
+            if (rate > best_rate) { best_rate = rate; bw = Ws[wi]; brw = Rs[ri]; }
+        }
+    c->W = bw;
+    c->rows_per_warp = brw;
+    if (cache_path) {
+        FILE* f = std::fopen(cache_path, "a");
+        if (f) {
+            std::fprintf(f, "%s %d %d\n", key, bw, brw);
+            std::fclose(f);
+        }
+    }
+    if (warps_out) *warps_out = bw;
+    if (rows_out) *rows_out = brw;
+    return CM_OK;
+}
+
 int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
                 const int8_t* matrix, int32_t gap_open, int32_t gap_extend, int32_t T,
                 int64_t part, int64_t n_parts, int32_t* pairs_out, int32_t* scores_out,
@@ -703,74 +866,10 @@ int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t 
     if (!P.symmetric) return fail(c, CM_ERR_ARG, "sw_allpairs needs a symmetric matrix");
     const bool dev = (flags & CM_DEVICE_PTRS) != 0;
     CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
-    // length order (ties by index): query = the longer sequence of every pair
-    std::vector<int32_t> L((size_t)n_seqs);
-    std::iota(L.begin(), L.end(), 0);
-    std::stable_sort(L.begin(), L.end(), [&](int32_t x, int32_t y) {
-        return P.hoff[x + 1] - P.hoff[x] < P.hoff[y + 1] - P.hoff[y];
-    });
+    std::vector<int32_t> L;
     Plan plan;
-    plan.srow.resize((size_t)n_seqs + 1);
-    plan.srow[0] = 0;
-    for (int32_t s = 0; s < n_seqs; ++s)
-        plan.srow[s + 1] = plan.srow[s] + stream_rows(P.hoff[L[s] + 1] - P.hoff[L[s]]);
-    // parts: equal shares of cells, boundaries on even k
-    std::vector<double> cum((size_t)n_seqs + 1, 0.0);
-    int64_t residues = 0;
-    for (int32_t k = 0; k < n_seqs; ++k) {
-        const int64_t mk = P.hoff[L[k] + 1] - P.hoff[L[k]];
-        cum[k + 1] = cum[k] + (double)mk * (double)residues;
-        residues += mk;
-    }
-    auto kb = [&](int64_t p) -> int32_t {
-        if (p <= 0) return 0;
-        if (p >= n_parts) return n_seqs;
-        const double want = cum[n_seqs] * (double)p / (double)n_parts;
-        int32_t k = (int32_t)(std::lower_bound(cum.begin(), cum.end(), want) - cum.begin());
-        k &= ~1;
-        return std::min(k, n_seqs);
-    };
-    const int32_t k0 = kb(part), k1 = kb(part + 1);
-    SwBlock B{};
-    B.kind = kTri;
-    B.swap = 0;
-    B.na = n_seqs;
-    B.nb = n_seqs;
-    B.a_ids = 0;
-    B.b_ids = 0;
-    B.stream = 0;
-    B.srow = 0;
-    B.out_base = 0;
-    B.k0 = k0;
-    B.has_map = 0;
-    plan.blocks.push_back(B);
-    plan.first_slot.push_back(0);
-    plan.ids = L;
-    auto tri = [](int64_t k) { return k * (k - 1) / 2; };
-    plan.nslots = tri(k1) - tri(k0);
-    plan.pairs = plan.nslots;
-    const int64_t target = (int64_t)c->W * c->rows_per_warp;
-    for (int32_t k = k0; k < k1; k += 2) {
-        const bool hi = (k + 1 < k1);
-        const int32_t ns = hi ? k + 1 : k;
-        const int64_t m_hi = P.hoff[L[hi ? k + 1 : k] + 1] - P.hoff[L[hi ? k + 1 : k]];
-        if (ns > 0) add_tasks(plan, 0, k, ns, hi, m_hi, plan.srow.data(), target);
-    }
-    {   // cells = sum over pairs of len(a) * len(b)
-        int64_t acc = 0, pre = 0;
-        for (int32_t k = 0; k < k1; ++k) {
-            const int64_t mk = P.hoff[L[k] + 1] - P.hoff[L[k]];
-            if (k >= k0) acc += mk * pre;
-            pre += mk;
-        }
-        plan.cells = acc;
-    }
-    order_tasks(plan);
-    int64_t maxlen_rows = 1;
-    for (int32_t s = 0; s < n_seqs; ++s)
-        maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
-    plan.max_warp_rows = 2 * c->rows_per_warp + 2 * maxlen_rows + 2 * target / c->W;
-
+    int32_t k0 = 0;
+    allpairs_plan(c, P, n_seqs, part, n_parts, L, k0, plan);
     int32_t* out;
     ENSURE(B_OUT, plan.nslots, out);
     if (!plan.tasks.empty())

@@ -30,7 +30,7 @@ struct cm_ctx {
     std::string err;
     cm_stats stats{};
     int W = 8;
-    int rows_per_warp = 4096;
+    int rows_per_warp = 16384;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cm::DevBuf buf[cm::B_COUNT];
     void* ranker = nullptr;                 // learned ranker state (ranker.cu)

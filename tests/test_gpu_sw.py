@@ -174,3 +174,18 @@ def test_ascii_input(ctx):
     got = ctx.sw_score_batch(seqs, off, np.array([[0, 1], [2, 2]], np.int32), S62, 11, 1,
                              flags=cm.CM_ASCII)
     assert got.tolist() == [17, 52]
+
+
+def test_autotune_choice_cache_and_unchanged_scores(ctx, tmp_path):
+    ss = _lognormal_set(400, 50, hi=2000)
+    pairs = synth.random_pairs(len(ss), 500, stream=13)
+    before = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    cache = str(tmp_path / "tune.txt")
+    w, r = ctx.autotune(ss.seqs, ss.offsets, S62, 11, 1, sample_seqs=300, cache_path=cache)
+    assert w in (4, 8, 16) and r in (4096, 8192, 16384, 32768)
+    assert open(cache).read().split()[1:] == [str(w), str(r)]
+    ctx.set_tuning(4, 4096)
+    assert ctx.autotune(ss.seqs, ss.offsets, S62, 11, 1, cache_path=cache) == (w, r)
+    after = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(before, after)
+    assert np.array_equal(after, oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1))
