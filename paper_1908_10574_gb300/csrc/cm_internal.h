@@ -14,17 +14,22 @@ namespace cm {
 // ---- residue streams -------------------------------------------------------------------
 // A block's subjects are concatenated into one byte stream, one byte per DP row:
 // bits 0-4 residue code (0..19, 20 = pad row whose scores are all non-positive),
-// bit 7 = first row of a subject, bit 6 = last row of a subject.  Every subject occupies an
-// even number of rows (a pad row follows an odd-length subject), so subjects start on even
-// rows and a kernel step can cover two rows; an empty subject is two pad rows, the first
-// carrying both flags, so its score comes out 0.
+// bit 7 = first row of a subject, bit 6 = last row of a subject.  Every subject occupies a
+// multiple of kRowGroup rows (pad rows follow it), so subjects start on group boundaries and a
+// kernel step can cover up to kRowGroup rows; an empty subject is one group of pad rows, the
+// first carrying both flags, so its score comes out 0.
 constexpr uint8_t kFirst = 0x80;
 constexpr uint8_t kLast = 0x40;
 constexpr uint8_t kPadCode = 20;
 constexpr int kProfRows = 21;          // 20 residues + pad row
 
-// rows a subject of `len` residues occupies in a stream
-inline int64_t stream_rows(int64_t len) { return len <= 0 ? 2 : (len + 1) / 2 * 2; }
+// rows a subject of `len` residues occupies in a stream: a multiple of kRowGroup (at least
+// one group), so subjects start on group boundaries and a kernel step can cover a group
+constexpr int kRowGroup = 4;
+inline int64_t stream_rows(int64_t len)
+{
+    return len <= 0 ? kRowGroup : (len + kRowGroup - 1) / kRowGroup * kRowGroup;
+}
 
 // ---- pair blocks -----------------------------------------------------------------------
 // A block is a set of pairs between queries A (held in registers, one column per residue)

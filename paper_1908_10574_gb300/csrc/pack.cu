@@ -56,7 +56,7 @@ __global__ void gather_kernel(const uint8_t* __restrict__ db, const int64_t* __r
         const int32_t id = ids[s];
         const int64_t b = off[id], len = off[id + 1] - b;
         uint8_t* dst = stream + srow[s];
-        const int64_t rows = srow[s + 1] - srow[s];        // len rounded up to even, >= 2
+        const int64_t rows = srow[s + 1] - srow[s];        // len rounded up to the row group
         for (int64_t r = lane; r < rows; r += 32) {
             uint8_t v = (r < len) ? db[b + r] : kPadCode;
             if (r == 0) v |= kFirst;

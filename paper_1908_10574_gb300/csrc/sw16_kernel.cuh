@@ -87,11 +87,23 @@ __device__ __forceinline__ void store_score(const SwArgs& a, const SwBlock& B, i
     }
 }
 
-// One warp: rows [0, nrows) of its stream (nrows even; every subject starts on an even row)
-// against the profile tile of this pass.  A step covers two rows, 2u and 2u+1: row 2u+1 trails
-// row 2u by one column inside the lane, so the two rows form independent dependency chains,
-// and the step's fixed costs (shuffles, residue and flag handling) are shared by both rows.
-// Lane 31 writes one score per subject per query half after the subject's last row.
+// One warp: rows [0, nrows) of its stream (every subject starts on a row that is a multiple of
+// kRowGroup) against the profile tile of this pass.  A step covers NR consecutive rows; row q
+// of the step trails row q-1 by one column inside the lane, so the NR rows form independent
+// dependency chains and the step's fixed costs (shuffles, residue and flag handling) are
+// shared by NR rows.  Lane 31 writes one score per subject per query half after the
+// subject's last row.
+// Rows per step by tile width: four, except at R = 28, where the four-row step runs at the
+// 128-register cap and measured slower than two rows.
+template <int R>
+struct RowsPerStep {
+    static constexpr int value = (R == 28) ? 2 : 4;
+};
+
+template <int NR> struct RowWord;
+template <> struct RowWord<2> { typedef uint16_t type; };
+template <> struct RowWord<4> { typedef uint32_t type; };
+
 template <int R>
 __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
                                           const uint32_t* __restrict__ prof,
@@ -101,126 +113,139 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
                                           int32_t ns_hi, bool hi_valid)
 {
     using G = Geo<R>;
+    constexpr int NR = RowsPerStep<R>::value;
+    typedef typename RowWord<NR>::type word_t;
     const int lane = threadIdx.x & 31;
     const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
     const uint32_t BETA2 = (uint32_t)beta * 0x10001u;
-    const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;
-    const uint32_t NEGO = pack2(-o, -o);
-    const uint32_t E2 = (uint32_t)ge * 0x10001u;
-    const uint32_t PADPAIR = (uint32_t)kPadCode | ((uint32_t)kPadCode << 8);
+    const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;   // H - o of an empty prefix; E, F floor
+    const uint32_t O2 = (uint32_t)o * 0x10001u;
+    const uint32_t NEGE = pack2(-ge, -ge);
+    const uint32_t PADW = (NR == 4) ? 0x14141414u : 0x1414u;      // kPadCode in every byte
+    uint32_t FIRSTBIT = kFirst, LASTBITS = 0;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) LASTBITS |= (uint32_t)kLast << (8 * q);
 
+    // hp[c] holds H - o of the row above (the value both E and F start a gap from, and the
+    // diagonal of column c+1 against a profile that carries +o); fp[c] holds F.
     uint32_t hp[R], fp[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) { hp[k] = BETA2; fp[k] = BMO2; }
+    for (int k = 0; k < R; ++k) { hp[k] = BMO2; fp[k] = BMO2; }
     uint32_t best = BETA2, out_acc = BETA2;
-    uint32_t oa_h = BETA2, oa_e = BMO2, ob_h = BETA2, ob_e = BMO2;   // last column, rows A, B
-    uint32_t diagA0 = BETA2;                     // H(2u-1, c0-1) for the next step's row A
-    uint32_t cur = PADPAIR, prev = PADPAIR;
-    uint4 bv = make_uint4(BETA2, BMO2, BETA2, BMO2);
+    uint32_t oh[NR], oe[NR];                      // last column of each row: H - o and E
+#pragma unroll
+    for (int q = 0; q < NR; ++q) { oh[q] = BMO2; oe[q] = BMO2; }
+    uint32_t diag0 = BMO2;                        // left H - o of the previous step's last row
+    uint32_t cur = PADW, prev = PADW;
+    uint4 bv[NR / 2];
+#pragma unroll
+    for (int q = 0; q < NR / 2; ++q) bv[q] = make_uint4(BMO2, BMO2, BMO2, BMO2);
     int32_t s_cur = s_first;
     const uint32_t* plane = prof + lane * G::LS;
-    const int64_t nsup = nrows >> 1;             // super-rows of two rows
+    const int64_t nsup = nrows / NR;
     const int64_t nsteps = nsup + 31;
-    const uint16_t* st16 = reinterpret_cast<const uint16_t*>(stream);
+    const word_t* stw = reinterpret_cast<const word_t*>(stream);
 
     for (int64_t t = 0; t < nsteps; ++t) {
         const int j = (int)(t & 31);
         if (j == 0) {
             prev = cur;
             const int64_t u = t + lane;
-            cur = (u < nsup) ? (uint32_t)st16[u] : PADPAIR;
+            cur = (u < nsup) ? (uint32_t)stw[u] : PADW;
             if (pass > 0) {
-                if (u < nsup) bv = bnd[u];
-                else bv = make_uint4(BETA2, BMO2, BETA2, BMO2);
+#pragma unroll
+                for (int q = 0; q < NR / 2; ++q)
+                    bv[q] = (u < nsup) ? bnd[u * (NR / 2) + q] : make_uint4(BMO2, BMO2, BMO2, BMO2);
             }
         }
         const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-        uint32_t haL = __shfl_up_sync(kFull, oa_h, 1);
-        uint32_t eaL = __shfl_up_sync(kFull, oa_e, 1);
-        uint32_t hbL = __shfl_up_sync(kFull, ob_h, 1);
-        uint32_t ebL = __shfl_up_sync(kFull, ob_e, 1);
+        uint32_t hL[NR], eL[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            hL[q] = __shfl_up_sync(kFull, oh[q], 1);
+            eL[q] = __shfl_up_sync(kFull, oe[q], 1);
+        }
         uint32_t ai = __shfl_up_sync(kFull, out_acc, 1);
         if (pass > 0) {
-            const uint32_t x0 = __shfl_sync(kFull, bv.x, j), x1 = __shfl_sync(kFull, bv.y, j);
-            const uint32_t x2 = __shfl_sync(kFull, bv.z, j), x3 = __shfl_sync(kFull, bv.w, j);
-            if (lane == 0) { haL = x0; eaL = x1; hbL = x2; ebL = x3; }
+#pragma unroll
+            for (int q = 0; q < NR / 2; ++q) {
+                const uint32_t x0 = __shfl_sync(kFull, bv[q].x, j), x1 = __shfl_sync(kFull, bv[q].y, j);
+                const uint32_t x2 = __shfl_sync(kFull, bv[q].z, j), x3 = __shfl_sync(kFull, bv[q].w, j);
+                if (lane == 0) { hL[2 * q] = x0; eL[2 * q] = x1; hL[2 * q + 1] = x2; eL[2 * q + 1] = x3; }
+            }
         } else if (lane == 0) {
-            haL = BETA2; eaL = BMO2; hbL = BETA2; ebL = BMO2;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) { hL[q] = BMO2; eL[q] = BMO2; }
         }
         if (lane == 0) ai = BETA2;
-        uint32_t dgA = diagA0;
-        diagA0 = hbL;
-        if (rv & kFirst) {                       // a subject starts at row 2u
+        uint32_t dg[NR], h[NR], e[NR];
+        dg[0] = diag0;
 #pragma unroll
-            for (int k = 0; k < R; ++k) { hp[k] = BETA2; fp[k] = BMO2; }
+        for (int q = 1; q < NR; ++q) dg[q] = hL[q - 1];
+        diag0 = hL[NR - 1];
+        if (rv & FIRSTBIT) {                      // a subject starts at the step's first row
+#pragma unroll
+            for (int k = 0; k < R; ++k) { hp[k] = BMO2; fp[k] = BMO2; }
             best = BETA2;
-            dgA = BETA2;
+            dg[0] = BMO2;
         }
-        const uint32_t* prowA = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-        const uint32_t* prowB = plane + min((rv >> 8) & 31u, (uint32_t)kPadCode) * G::ROWW;
-        uint32_t hA = haL, eA = eaL, hB = hbL, eB = ebL, dgB = haL;
-        uint32_t sBprev = 0;
+        const uint32_t* prow[NR];
 #pragma unroll
-        for (int j4 = 0; j4 < (R + 3) / 4; ++j4) {
-            uint32_t sa[4], sb[4];
-            if (4 * j4 + 4 <= R) {
-                const uint4 va = *reinterpret_cast<const uint4*>(prowA + 4 * j4);
-                const uint4 vb = *reinterpret_cast<const uint4*>(prowB + 4 * j4);
-                sa[0] = va.x; sa[1] = va.y; sa[2] = va.z; sa[3] = va.w;
-                sb[0] = vb.x; sb[1] = vb.y; sb[2] = vb.z; sb[3] = vb.w;
-            } else {
-                const uint2 va = *reinterpret_cast<const uint2*>(prowA + 4 * j4);
-                const uint2 vb = *reinterpret_cast<const uint2*>(prowB + 4 * j4);
-                sa[0] = va.x; sa[1] = va.y; sa[2] = sa[3] = 0;
-                sb[0] = vb.x; sb[1] = vb.y; sb[2] = sb[3] = 0;
-            }
+        for (int q = 0; q < NR; ++q) {
+            prow[q] = plane + min((rv >> (8 * q)) & 31u, (uint32_t)kPadCode) * G::ROWW;
+            h[q] = hL[q];
+            e[q] = eL[q];
+        }
+        uint32_t sq[NR][4];
+        uint32_t pend = 0;
+        bool has_pend = false;
+        // Row q trails row q-1 by one column.  Per packed cell: E = max(E - e, (H - o)_left),
+        // F = max(F - e, (H - o)_up), D = max((H - o)_diag + (S + o), beta), H = max(D, E, F),
+        // then H - o once for the neighbours (plain 32-bit subtract: H >= beta >= o + e, so
+        // neither half borrows).
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k = 4 * j4 + q;
-                if (k >= R) break;
-                // row A = 2u, column k
-                eA = __viaddmax_s16x2(hA, NEGO, eA - E2);
-                const uint32_t fA = __viaddmax_s16x2(hp[k], NEGO, fp[k] - E2);
-                const uint32_t dA = __viaddmax_s16x2(dgA, sa[q], BETA2);
-                dgA = hp[k];
-                hA = __vimax3_s16x2(dA, eA, fA);
-                // row B = 2u+1, column k-1 (reads row A's column k-1, written last iteration)
-                if (k > 0) {
-                    eB = __viaddmax_s16x2(hB, NEGO, eB - E2);
-                    const uint32_t fB = __viaddmax_s16x2(hp[k - 1], NEGO, fp[k - 1] - E2);
-                    const uint32_t dB = __viaddmax_s16x2(dgB, sBprev, BETA2);
-                    dgB = hp[k - 1];
-                    hB = __vimax3_s16x2(dB, eB, fB);
-                    hp[k - 1] = hB;
-                    fp[k - 1] = fB;
-                    best = __vimax3_s16x2(best, hB, hA);
-                } else {
-                    best = __vmaxs2(best, hA);
+        for (int k = 0; k < R + NR - 1; ++k) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const int c = k - q;
+                if (c < 0 || c >= R) continue;
+                if ((c & 3) == 0) {               // next four profile columns of row q
+                    if (c + 4 <= R) {
+                        const uint4 v = *reinterpret_cast<const uint4*>(prow[q] + c);
+                        sq[q][0] = v.x; sq[q][1] = v.y; sq[q][2] = v.z; sq[q][3] = v.w;
+                    } else {
+                        const uint2 v = *reinterpret_cast<const uint2*>(prow[q] + c);
+                        sq[q][0] = v.x; sq[q][1] = v.y;
+                    }
                 }
-                hp[k] = hA;
-                fp[k] = fA;
-                sBprev = sb[q];
+                e[q] = __viaddmax_s16x2(e[q], NEGE, h[q]);
+                const uint32_t f = __viaddmax_s16x2(fp[c], NEGE, hp[c]);
+                const uint32_t d = __viaddmax_s16x2(dg[q], sq[q][c & 3], BETA2);
+                dg[q] = hp[c];
+                const uint32_t hh = __vimax3_s16x2(d, e[q], f);
+                if (has_pend) { best = __vimax3_s16x2(best, pend, hh); has_pend = false; }
+                else { pend = hh; has_pend = true; }
+                h[q] = hh - O2;
+                hp[c] = h[q];
+                fp[c] = f;
             }
         }
-        {   // row B, last column
-            eB = __viaddmax_s16x2(hB, NEGO, eB - E2);
-            const uint32_t fB = __viaddmax_s16x2(hp[R - 1], NEGO, fp[R - 1] - E2);
-            const uint32_t dB = __viaddmax_s16x2(dgB, sBprev, BETA2);
-            hB = __vimax3_s16x2(dB, eB, fB);
-            hp[R - 1] = hB;
-            fp[R - 1] = fB;
-            best = __vmaxs2(best, hB);
-        }
-        oa_h = hA; oa_e = eA; ob_h = hB; ob_e = eB;
+        if (has_pend) best = __vmaxs2(best, pend);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) { oh[q] = h[q]; oe[q] = e[q]; }
         out_acc = __vmaxs2(ai, best);
-        if (lane == 31 && (rv & ((uint32_t)kLast | ((uint32_t)kLast << 8)))) {
+        if (lane == 31 && (rv & LASTBITS)) {
             const int32_t s = s_cur++;
             const int32_t lo = (int32_t)(int16_t)(out_acc & 0xffffu);
             const int32_t hi = (int32_t)(int16_t)(out_acc >> 16);
             if (s < ns_lo) store_score(a, B, k_lo, s, lo, pass);
             if (hi_valid && s < ns_hi) store_score(a, B, k_lo + 1, s, hi, pass);
         }
-        if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_uint4(oa_h, oa_e, ob_h, ob_e);
+        if (lane == 31 && pass + 1 < npass && t >= 31) {
+#pragma unroll
+            for (int q = 0; q < NR / 2; ++q)
+                bnd[(t - 31) * (NR / 2) + q] = make_uint4(oh[2 * q], oe[2 * q], oh[2 * q + 1], oe[2 * q + 1]);
+        }
     }
 }
 
@@ -242,15 +267,15 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
     const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
     const uint32_t BETA2 = (uint32_t)beta * 0x10001u;
     const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;
-    const uint32_t NEGO = pack2(-o, -o);
-    const uint32_t E2 = (uint32_t)ge * 0x10001u;
+    const uint32_t O2 = (uint32_t)o * 0x10001u;
+    const uint32_t NEGE = pack2(-ge, -ge);
 
     uint32_t hp[R], fp[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) { hp[q] = BETA2; fp[q] = BMO2; }
-    uint32_t best = BETA2, out_h = BETA2, out_e = BMO2, out_acc = BETA2, diag0 = BETA2;
+    for (int q = 0; q < R; ++q) { hp[q] = BMO2; fp[q] = BMO2; }
+    uint32_t best = BETA2, out_h = BMO2, out_e = BMO2, out_acc = BETA2, diag0 = BMO2;
     const uint32_t padpair = (uint32_t)kPadCode | ((uint32_t)kPadCode << 8);
-    uint32_t cur = padpair, prev = padpair, bh = BETA2, be = BMO2;
+    uint32_t cur = padpair, prev = padpair, bh = BMO2, be = BMO2;
     int32_t s_lo = s_lo0, s_hi = s_hi0;
     const uint32_t* plane = prof + lane * G::LS;
     const int64_t nrows = n_lo > n_hi ? n_lo : n_hi;
@@ -266,7 +291,7 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
             cur = lo | (hi << 8);
             if (pass > 0) {
                 if (r < nrows) { const uint2 v = bnd[r]; bh = v.x; be = v.y; }
-                else { bh = BETA2; be = BMO2; }
+                else { bh = BMO2; be = BMO2; }
             }
         }
         const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
@@ -278,7 +303,7 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
             const uint32_t y = __shfl_sync(kFull, be, j);
             if (lane == 0) { hl = x; el = y; }
         } else if (lane == 0) {
-            hl = BETA2; el = BMO2;
+            hl = BMO2; el = BMO2;
         }
         if (lane == 0) ai = BETA2;
         uint32_t dg = diag0;
@@ -288,11 +313,11 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
                                   ((rv & ((uint32_t)kFirst << 8)) ? 0u : 0xffff0000u);
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                hp[q] = (hp[q] & keep) | (BETA2 & ~keep);
+                hp[q] = (hp[q] & keep) | (BMO2 & ~keep);
                 fp[q] = (fp[q] & keep) | (BMO2 & ~keep);
             }
             best = (best & keep) | (BETA2 & ~keep);
-            dg = (dg & keep) | (BETA2 & ~keep);
+            dg = (dg & keep) | (BMO2 & ~keep);
         }
         const uint32_t* prow_lo = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
         const uint32_t* prow_hi = plane + min((rv >> 8) & 31u, (uint32_t)kPadCode) * G::ROWW;
@@ -315,14 +340,15 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
             for (int u = 0; u < 4; ++u) {
                 const int q = 4 * j4 + u;
                 if (q >= R) break;
-                e = __viaddmax_s16x2(h, NEGO, e - E2);
-                const uint32_t f = __viaddmax_s16x2(hp[q], NEGO, fp[q] - E2);
+                e = __viaddmax_s16x2(e, NEGE, h);               // h, hp[]: H - o
+                const uint32_t f = __viaddmax_s16x2(fp[q], NEGE, hp[q]);
                 fp[q] = f;
                 const uint32_t d = __viaddmax_s16x2(dg, s4[u], BETA2);
                 dg = hp[q];
-                h = __vimax3_s16x2(d, e, f);
+                const uint32_t hh = __vimax3_s16x2(d, e, f);
+                if (u & 1) best = __vimax3_s16x2(best, hh, hprev); else hprev = hh;
+                h = hh - O2;
                 hp[q] = h;
-                if (u & 1) best = __vimax3_s16x2(best, h, hprev); else hprev = h;
             }
         }
         out_h = h;
@@ -406,9 +432,9 @@ sw16_kernel(const __grid_constant__ SwArgs a)
                 const int ln = c / R, k = c - ln * R;
                 const int ql = qres[c], qh = qres[G::COLS + c];
                 int sl = kSpad, sh = kSpad;
-                if (x != kPadCode) {
-                    if (ql != kPadCode) sl = B.swap ? s_mat[x * 20 + ql] : s_mat[ql * 20 + x];
-                    if (qh != kPadCode) sh = B.swap ? s_mat[x * 20 + qh] : s_mat[qh * 20 + x];
+                if (x != kPadCode) {          // +o: the DP keeps H - o as its diagonal input
+                    if (ql != kPadCode) sl = (B.swap ? s_mat[x * 20 + ql] : s_mat[ql * 20 + x]) + a.gap_open;
+                    if (qh != kPadCode) sh = (B.swap ? s_mat[x * 20 + qh] : s_mat[qh * 20 + x]) + a.gap_open;
                 }
                 prof[x * G::ROWW + ln * G::LS + k] = pack2(sl, sh);
             }
