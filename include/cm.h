@@ -18,7 +18,8 @@
  *   - Sequences: `seqs` is one concatenated array of residue codes 0..19 in the order
  *     ARNDCQEGHILKMFPSTWYV (or ASCII letters with CM_ASCII); sequence i is
  *     seqs[offsets[i] .. offsets[i+1]), offsets has n_seqs+1 non-decreasing int64 entries
- *     starting at 0.  Sequences may be empty (their scores are 0).
+ *     starting at 0.  Sequences may be empty (their scores are 0); one longer than 2^28
+ *     residues is rejected with CM_ERR_ARG.
  *   - Matrix: 400 int8 entries, row-major, matrix[x*20 + y] = score of residue x of the
  *     pair's FIRST sequence against residue y of its SECOND sequence.  Entries must lie in
  *     [-1000, 1000]; it need not be symmetric.

@@ -108,6 +108,8 @@ int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t
     for (int32_t i = 0; i < n_seqs; ++i) {
         const int64_t L = P.hoff[i + 1] - P.hoff[i];
         if (L < 0) return fail(c, CM_ERR_ARG, "offsets must be non-decreasing");
+        if (L > kMaxSeqLen)
+            return fail(c, CM_ERR_ARG, "a sequence is longer than 2^28 residues");
         P.maxlen = std::max(P.maxlen, L);
     }
     const int64_t total = P.hoff[n_seqs];
@@ -160,12 +162,11 @@ int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t
 // ---- planning ---------------------------------------------------------------------------
 void choose_R(int64_t m, int* R, int* npass)
 {
-    if (m <= 0) { *R = 2; *npass = 1; return; }
+    if (m <= 0) { *R = 1; *npass = 1; return; }
     const int np = (int)((m + 1023) / 1024);
     const int64_t per = (m + np - 1) / np;
-    int r = (int)((per + 31) / 32);
-    r = (r + 1) / 2 * 2;                         // register tiles of 2..32 columns per lane
-    r = std::max(2, std::min(32, r));
+    int r = (int)((per + 31) / 32);              // register tiles of 1..32 columns per lane
+    r = std::max(1, std::min(32, r));
     *R = r;
     *npass = np;
 }
@@ -268,7 +269,7 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     // even, so the pair-mode records (16 bytes per two rows) stay 16-byte aligned
     const int64_t stride = (std::max<int64_t>(plan.max_warp_rows, P.maxlen) + 64 + 1) & ~(int64_t)1;
     int max_ctas = 0;
-    for (int R = 2; R <= 32; R += 2)
+    for (int R = 1; R <= 32; ++R)
         max_ctas = std::max(max_ctas, c->num_sms * std::max(1, sw16_ctas_per_sm(R, W)));
     const int64_t nwarps = std::max<int64_t>((int64_t)max_ctas * W,
                                              (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));

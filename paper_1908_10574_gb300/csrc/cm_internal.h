@@ -31,6 +31,9 @@ inline int64_t stream_rows(int64_t len)
     return len <= 0 ? kRowGroup : (len + kRowGroup - 1) / kRowGroup * kRowGroup;
 }
 
+// longest sequence accepted: keeps every warp stream of the kernels below 2^31 rows
+constexpr int64_t kMaxSeqLen = int64_t(1) << 28;
+
 // ---- pair blocks -----------------------------------------------------------------------
 // A block is a set of pairs between queries A (held in registers, one column per residue)
 // and subjects B (streamed row by row).  CROSS: query k pairs with every subject s < nb.

@@ -142,15 +142,15 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
     for (int q = 0; q < NR / 2; ++q) bv[q] = make_uint4(BMO2, BMO2, BMO2, BMO2);
     int32_t s_cur = s_first;
     const uint32_t* plane = prof + lane * G::LS;
-    const int64_t nsup = nrows / NR;
-    const int64_t nsteps = nsup + 31;
+    const int nsup = (int)(nrows / NR);           // a warp stream holds < 2^31 rows
+    const int nsteps = nsup + 31;
     const word_t* stw = reinterpret_cast<const word_t*>(stream);
 
-    for (int64_t t = 0; t < nsteps; ++t) {
-        const int j = (int)(t & 31);
+    for (int t = 0; t < nsteps; ++t) {
+        const int j = t & 31;
         if (j == 0) {
             prev = cur;
-            const int64_t u = t + lane;
+            const int u = t + lane;
             cur = (u < nsup) ? (uint32_t)stw[u] : PADW;
             if (pass > 0) {
 #pragma unroll
@@ -209,13 +209,15 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
             for (int q = 0; q < NR; ++q) {
                 const int c = k - q;
                 if (c < 0 || c >= R) continue;
-                if ((c & 3) == 0) {               // next four profile columns of row q
-                    if (c + 4 <= R) {
+                if ((c & 3) == 0) {               // next (up to) four profile columns of row q
+                    if (c + 3 <= R) {             // the lane's row segment holds whole 16-byte units
                         const uint4 v = *reinterpret_cast<const uint4*>(prow[q] + c);
                         sq[q][0] = v.x; sq[q][1] = v.y; sq[q][2] = v.z; sq[q][3] = v.w;
-                    } else {
+                    } else if (c + 2 == R) {
                         const uint2 v = *reinterpret_cast<const uint2*>(prow[q] + c);
                         sq[q][0] = v.x; sq[q][1] = v.y;
+                    } else {
+                        sq[q][0] = prow[q][c];
                     }
                 }
                 e[q] = __viaddmax_s16x2(e[q], NEGE, h[q]);
@@ -324,17 +326,18 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
         uint32_t h = hl, e = el, hprev = BETA2;
 #pragma unroll
         for (int j4 = 0; j4 < (R + 3) / 4; ++j4) {
-            uint32_t s4[4];
-            if (4 * j4 + 4 <= R) {
+            uint32_t s4[4] = {0, 0, 0, 0};
+            if (4 * j4 + 3 <= R) {
                 const uint4 sl = *reinterpret_cast<const uint4*>(prow_lo + 4 * j4);
                 const uint4 sh = *reinterpret_cast<const uint4*>(prow_hi + 4 * j4);
                 s4[0] = __byte_perm(sl.x, sh.x, 0x7610); s4[1] = __byte_perm(sl.y, sh.y, 0x7610);
                 s4[2] = __byte_perm(sl.z, sh.z, 0x7610); s4[3] = __byte_perm(sl.w, sh.w, 0x7610);
-            } else {
+            } else if (4 * j4 + 2 == R) {
                 const uint2 sl = *reinterpret_cast<const uint2*>(prow_lo + 4 * j4);
                 const uint2 sh = *reinterpret_cast<const uint2*>(prow_hi + 4 * j4);
                 s4[0] = __byte_perm(sl.x, sh.x, 0x7610); s4[1] = __byte_perm(sl.y, sh.y, 0x7610);
-                s4[2] = s4[3] = 0;
+            } else {
+                s4[0] = __byte_perm(prow_lo[4 * j4], prow_hi[4 * j4], 0x7610);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -351,6 +354,7 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
                 hp[q] = h;
             }
         }
+        if (R & 1) best = __vmaxs2(best, hprev);     // odd R: the last column has no partner
         out_h = h;
         out_e = e;
         out_acc = __vmaxs2(ai, best);

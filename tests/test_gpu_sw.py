@@ -57,6 +57,48 @@ def test_long_queries_multipass_and_ragged(ctx):
     assert np.array_equal(got, want)
 
 
+def _every_tile_set(stream):
+    """Two queries per register-tile width R = 1..32 (32R-20 and 32R-3 residues, so the
+    length-sorted pairing puts both in tile R) plus short sequences of every length mod 4.
+    Every other sequence starts with a substituted copy of an earlier one, so scores are
+    large and optimal alignments cross lanes."""
+    rng = np.random.default_rng(stream)
+    lens = [1, 2, 3, 5, 6, 7] + [L for R in range(1, 33) for L in (max(32 * R - 20, 12), 32 * R - 3)]
+    seqs = []
+    for i, L in enumerate(lens):
+        s = synth.random_seq(rng, L)
+        if i % 2 and i > 6:
+            donor = synth.mutate(rng, seqs[int(rng.integers(6, i))], sub_rate=0.2, indel_rate=0.0)
+            k = min(L, len(donor))
+            s[:k] = donor[:k]
+        seqs.append(s)
+    return synth.SeqSet.from_list(seqs)
+
+
+def test_every_tile_width_pair_mode_exact(ctx):
+    """All pairs through the all-against-all path: query pairs share a tile (pair mode) at
+    every R = 1..32, odd and even."""
+    ss = _every_tile_set(21)
+    got_pairs, got_scores = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, -1)
+    tri = oracle.triangle_pairs(len(ss))
+    want = oracle.sw_batch(ss.seqs, ss.offsets, tri, S62, 11, 1)
+    got = {(min(int(i), int(j)), max(int(i), int(j))): int(v)
+           for (i, j), v in zip(np.asarray(got_pairs), np.asarray(got_scores))}
+    assert len(got) == len(tri)
+    assert all(got[(int(i), int(j))] == int(w) for (i, j), w in zip(tri, want))
+
+
+def test_every_tile_width_single_query_mode_exact(ctx):
+    """Every ordered pair through sw_score_batch: each sequence is a lone query (single-query,
+    two-stream mode) at every R = 1..32."""
+    ss = _every_tile_set(22)
+    n = len(ss)
+    pairs = np.array([(i, j) for i in range(n) for j in range(n) if i != j], dtype=np.int32)
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got, want)
+
+
 def test_empty_sequences(ctx):
     rng = np.random.default_rng(3)
     seqs = [np.zeros(0, np.uint8), synth.random_seq(rng, 50), np.zeros(0, np.uint8),
