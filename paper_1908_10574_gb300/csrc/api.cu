@@ -12,7 +12,6 @@
 
 namespace cm {
 int64_t compact_chunks(int64_t nslots);
-int sw16_ctas_per_sm(int R, int W);
 int sw32_ctas_per_sm();
 }  // namespace cm
 
@@ -116,8 +115,8 @@ int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t
     if (total > 0 && !seqs) return fail(c, CM_ERR_ARG, "seqs is null");
     // residues
     int32_t* flags_d;
-    ENSURE(B_FLAGS, 64, flags_d);
-    CUDA_TRY(cudaMemsetAsync(flags_d, 0, 64 * sizeof(int32_t), c->stream));
+    ENSURE(B_FLAGS, kFlagWords, flags_d);
+    CUDA_TRY(cudaMemsetAsync(flags_d, 0, kFlagWords * sizeof(int32_t), c->stream));
     uint8_t* db;
     if (flags & CM_ASCII) {
         ENSURE(B_DB, total, db);
@@ -171,16 +170,26 @@ void choose_R(int64_t m, int* R, int* npass)
     *npass = np;
 }
 
-// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows.  A query
-// without a partner runs in the single-query two-stream mode (twice the rows per task, split
-// over twice as many warp streams).
+// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows and pick the
+// kernel mode.  A query without a partner runs in the single-query two-stream mode; a pair
+// whose longer query fits 16 lanes x 32 columns runs in the 16-lane segment mode (R per lane
+// twice that of a 32-lane tile, 16-column granularity).  Both two-stream modes take twice the
+// rows per task, split over twice as many streams.
 void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
                const int64_t* srow, int64_t target)
 {
     int R, np;
     choose_R(m_hi, &R, &np);
-    const int two = hi_valid ? 0 : 1;
-    if (two) target *= 2;
+    int mode = hi_valid ? kModePair : kModeTwo;
+    int seg = 32;
+    if (hi_valid && m_hi <= kSeg16MaxCols) {      // (the 32-lane pair kernels exist for R > 16)
+        mode = kModeSeg16;
+        seg = 16;
+        R = (int)std::max<int64_t>(1, (m_hi + 15) / 16);
+        np = 1;
+    }
+    const bool two_streams = mode != kModePair;
+    if (two_streams) target *= 2;
     int32_t s = 0;
     while (s < ns) {
         const int64_t want = srow[s] + target;
@@ -193,12 +202,13 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
         t.s1 = e;
         t.npass = np;
         t.hi_valid = hi_valid ? 1 : 0;
-        t.two_streams = two;
+        t.two_streams = mode == kModeTwo;
+        t.mode = mode;
         const int64_t rows = srow[e] - srow[s];
-        P.cells_padded += rows * 32 * R * np * (two ? 1 : 2);
+        P.cells_padded += rows * seg * R * np * (mode == kModeTwo ? 1 : 2);
         P.tasks.push_back(t);
-        P.task_R.push_back(R * 2 + two);          // launch bin: register tile and mode
-        P.keys.push_back({rows * R * np / (two ? 2 : 1), R * 2 + two});
+        P.task_R.push_back(R * 4 + mode);         // launch bin: register tile and mode
+        P.keys.push_back({rows * R * np / (two_streams ? 2 : 1), R * 4 + mode});
         s = e;
     }
 }
@@ -233,7 +243,7 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     ENSURE(B_IDS, plan.ids.size(), d_ids);
     ENSURE(B_SROW, plan.srow.size(), d_srow);
     ENSURE(B_FIRST, plan.first_slot.size(), d_first);
-    ENSURE(B_FLAGS, 64, d_flags);
+    ENSURE(B_FLAGS, kFlagWords, d_flags);
     const int64_t nrows_total = plan.srow.back();
     ENSURE(B_STREAM, nrows_total + 64, d_stream);
     int r;
@@ -242,7 +252,7 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     if ((r = copy_in(c, d_ids, plan.ids.data(), plan.ids.size() * sizeof(int32_t), false))) return r;
     if ((r = copy_in(c, d_srow, plan.srow.data(), plan.srow.size() * sizeof(int64_t), false))) return r;
     if ((r = copy_in(c, d_first, plan.first_slot.data(), plan.first_slot.size() * sizeof(int64_t), false))) return r;
-    CUDA_TRY(cudaMemsetAsync(d_flags, 0, 64 * sizeof(int32_t), st));
+    CUDA_TRY(cudaMemsetAsync(d_flags, 0, kFlagWords * sizeof(int32_t), st));
     // the B subjects of all blocks form one list in the id pool after the A ids
     const int64_t nsub = (int64_t)plan.srow.size() - 1;
     const int64_t b_first = (int64_t)plan.ids.size() - nsub;
@@ -270,7 +280,8 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     const int64_t stride = (std::max<int64_t>(plan.max_warp_rows, P.maxlen) + 64 + 1) & ~(int64_t)1;
     int max_ctas = 0;
     for (int R = 1; R <= 32; ++R)
-        max_ctas = std::max(max_ctas, c->num_sms * std::max(1, sw16_ctas_per_sm(R, W)));
+        for (int mode = 0; mode < 3; ++mode)
+            max_ctas = std::max(max_ctas, c->num_sms * sw16_occupancy(c, R, W, mode));
     const int64_t nwarps = std::max<int64_t>((int64_t)max_ctas * W,
                                              (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
     uint2* d_bnd;
@@ -284,16 +295,16 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     int bin = 0;
     while (i0 < plan.tasks.size()) {
         const int key = plan.task_R[i0];
-        const int R = key / 2;
-        const bool two = (key & 1) != 0;
+        const int R = key / 4, mode = key % 4;
         size_t i1 = i0;
         while (i1 < plan.tasks.size() && plan.task_R[i1] == key) ++i1;
+        if (bin >= kTaskBins) return fail(c, CM_ERR_INTERNAL, "more launch bins than task tickets");
         a.tasks = d_tasks + i0;
         a.ntasks = (int32_t)(i1 - i0);
         a.task_counter = d_flags + 8 + bin;
-        const int occ = std::max(1, sw16_ctas_per_sm(R, W));
+        const int occ = sw16_occupancy(c, R, W, mode);
         const int grid = (int)std::min<int64_t>(a.ntasks, (int64_t)c->num_sms * occ);
-        CUDA_TRY(launch_sw16(R, W, two, grid, a, st));
+        CUDA_TRY(launch_sw16(R, W, mode, grid, a, st));
         c->stats.launches += 1;
         c->stats.sw16_launches += 1;
         i0 = i1;
@@ -435,7 +446,7 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
     uint2* d_bnd;
     ENSURE(B_JOBS, n_pairs, d_jobs);
     ENSURE(B_RES, 3 * n_pairs, d_res);
-    ENSURE(B_FLAGS, 64, d_flags);
+    ENSURE(B_FLAGS, kFlagWords, d_flags);
     const int occ = std::max(1, cells_wf_ctas_per_sm());
     const int grid = (int)std::min<int64_t>(n_pairs, (int64_t)c->num_sms * occ);
     const int64_t stride = P.maxlen + 64;
@@ -453,7 +464,7 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
     for (int dir = 0; dir < 2; ++dir) {
         int r = copy_in(c, d_jobs, jobs.data(), jobs.size() * sizeof(CellJob), false);
         if (r) return r;
-        CUDA_TRY(cudaMemsetAsync(d_flags, 0, 64 * sizeof(int32_t), st));
+        CUDA_TRY(cudaMemsetAsync(d_flags, 0, kFlagWords * sizeof(int32_t), st));
         CUDA_TRY(launch_cells_wf(grid, a, d_jobs, (int32_t)jobs.size(), d_flags + 4, d_res, st));
         c->stats.launches += 1;
         std::vector<int32_t> res(jobs.size() * 3);

@@ -53,10 +53,16 @@ struct SwBlock {
     int32_t has_map;    // 1: slot -> user index through out_map[]
 };
 
+// Launch modes of the int16x2 kernel (see sw16_kernel): query pair over 32 lanes; single
+// query with two subject streams in the word halves; query pair with two subject streams,
+// one per 16-lane half-warp segment (short queries).
+enum SwMode : int32_t { kModePair = 0, kModeTwo = 1, kModeSeg16 = 2 };
+constexpr int kSeg16MaxCols = 16 * 32;   // longest query tile of the 16-lane mode
+
 // One CTA task.  Pair mode: the query pair (k, k+1) of a block against subjects [s0, s1),
 // the two queries in the two 16-bit halves, one subject stream per warp.  Single mode
 // (two_streams = 1): query k alone against subjects [s0, s1), each warp running two subject
-// streams in the two halves.
+// streams in the two halves.  `mode` is the kernel's SwMode.
 struct SwTask {
     int32_t block;
     int32_t k;          // lo query index; hi = k+1 (if hi_valid)
@@ -64,7 +70,7 @@ struct SwTask {
     int32_t npass;      // column passes of 32*R columns
     int32_t hi_valid;   // pair mode: 0 when the lo query has no partner
     int32_t two_streams;
-    int32_t pad;
+    int32_t mode;
 };
 
 struct SwArgs {
@@ -109,8 +115,8 @@ struct CellJob {
 };
 
 // ---- launchers (sw16.cu) ---------------------------------------------------------------
-int sw16_smem_bytes(int R);
-cudaError_t launch_sw16(int R, int W, bool two, int grid, const SwArgs& a, cudaStream_t st);
+int sw16_ctas_per_sm(int R, int W, int mode);
+cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaStream_t st);
 cudaError_t launch_sw32(int R, int grid, const SwArgs& a, const PairRef* pr, int32_t npairs,
                         int32_t* counter, cudaStream_t st);
 int sw32_smem_bytes(int R);

@@ -2,6 +2,7 @@
 // preparation, the planner (pair blocks -> length-binned CTA tasks) and plan execution.
 #pragma once
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -35,11 +36,20 @@ struct cm_ctx {
     cm::DevBuf buf[cm::B_COUNT];
     void* ranker = nullptr;                 // learned ranker state (ranker.cu)
     void (*ranker_free)(void*) = nullptr;
+    int sw16_occ[3][33][3] = {};            // CTAs per SM by (W = 4/8/16, R, mode); 0 = unknown
 };
 
 namespace cm {
 
 int fail(cm_ctx* c, int code, const std::string& msg);
+
+// resident CTAs per SM of the int16x2 kernel (W, R, mode), queried once per context
+inline int sw16_occupancy(cm_ctx* c, int R, int W, int mode)
+{
+    int& v = c->sw16_occ[W == 4 ? 0 : W == 8 ? 1 : 2][R][mode];
+    if (v == 0) v = std::max(1, sw16_ctas_per_sm(R, W, mode));
+    return v;
+}
 
 #define CUDA_TRY(call)                                                                      \
     do {                                                                                    \
@@ -59,6 +69,12 @@ int ensure(cm_ctx* c, BufId id, size_t count, T** out)
     *out = reinterpret_cast<T*>(p);
     return r;
 }
+
+// B_FLAGS layout (int32 words): [1] kernel bounds-check flag, [2..3] int32-rerun list count and
+// ticket, [4..7] other kernels' tickets, [8 ..) one task ticket per (tile width, launch mode)
+// bin of the int16x2 kernel.
+constexpr int kTaskBins = 32 * 3;
+constexpr int kFlagWords = 8 + kTaskBins;
 
 #define ENSURE(id, n, ptr)                                                                  \
     do {                                                                                    \

@@ -4,21 +4,27 @@
 
 namespace cm {
 
-cudaError_t launch_sw16_w4(int R, bool two, int grid, const SwArgs& a, cudaStream_t st);
-cudaError_t launch_sw16_w8(int R, bool two, int grid, const SwArgs& a, cudaStream_t st);
-cudaError_t launch_sw16_w16(int R, bool two, int grid, const SwArgs& a, cudaStream_t st);
-int sw16_occ_w4(int R);
-int sw16_occ_w8(int R);
-int sw16_occ_w16(int R);
+#define CM_DECL(w, m)                                                                     \
+    cudaError_t launch_sw16_w##w##_m##m(int R, int grid, const SwArgs& a, cudaStream_t st); \
+    int sw16_occ_w##w##_m##m(int R);
+CM_DECL(4, 0) CM_DECL(4, 1) CM_DECL(4, 2)
+CM_DECL(8, 0) CM_DECL(8, 1) CM_DECL(8, 2)
+CM_DECL(16, 0) CM_DECL(16, 1) CM_DECL(16, 2)
+#undef CM_DECL
 
-int sw16_ctas_per_sm(int R, int W)
+int sw16_ctas_per_sm(int R, int W, int mode)
 {
+#define CM_OCC_CASE(w)                                                                   \
+    case w:                                                                              \
+        return mode == kModePair ? sw16_occ_w##w##_m0(R)                                 \
+                                 : mode == kModeTwo ? sw16_occ_w##w##_m1(R) : sw16_occ_w##w##_m2(R);
     switch (W) {
-    case 4: return sw16_occ_w4(R);
-    case 8: return sw16_occ_w8(R);
-    case 16: return sw16_occ_w16(R);
+    CM_OCC_CASE(4)
+    CM_OCC_CASE(8)
+    CM_OCC_CASE(16)
     default: return 1;
     }
+#undef CM_OCC_CASE
 }
 
 int sw32_ctas_per_sm()
@@ -34,20 +40,20 @@ int sw32_ctas_per_sm()
     return n;
 }
 
-int sw16_smem_bytes(int R)
+cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaStream_t st)
 {
-    const int LS = lane_stride(R);
-    return kProfRows * 32 * LS * 4 + 2 * 32 * R;
-}
-
-cudaError_t launch_sw16(int R, int W, bool two, int grid, const SwArgs& a, cudaStream_t st)
-{
+#define CM_LAUNCH_CASE(w)                                                                \
+    case w:                                                                              \
+        return mode == kModePair ? launch_sw16_w##w##_m0(R, grid, a, st)                 \
+               : mode == kModeTwo ? launch_sw16_w##w##_m1(R, grid, a, st)                \
+                                  : launch_sw16_w##w##_m2(R, grid, a, st);
     switch (W) {
-    case 4: return launch_sw16_w4(R, two, grid, a, st);
-    case 8: return launch_sw16_w8(R, two, grid, a, st);
-    case 16: return launch_sw16_w16(R, two, grid, a, st);
+    CM_LAUNCH_CASE(4)
+    CM_LAUNCH_CASE(8)
+    CM_LAUNCH_CASE(16)
     default: return cudaErrorInvalidValue;
     }
+#undef CM_LAUNCH_CASE
 }
 
 int sw32_smem_bytes(int R)

@@ -41,12 +41,13 @@ __host__ __device__ constexpr int lane_stride(int R)
     return (((R + 3) / 4) & 1) ? (R + 3) / 4 * 4 : (R + 3) / 4 * 4 + 4;
 }
 
-template <int R>
+// Tile geometry: SEG lanes (32, or 16 for a half-warp segment) of R columns each.
+template <int R, int SEG = 32>
 struct Geo {
     static constexpr int LS = lane_stride(R);       // 32-bit words per lane in a profile row
-    static constexpr int ROWW = 32 * LS;            // words per profile row (multiple of 128 B)
+    static constexpr int ROWW = SEG * LS;           // words per profile row (multiple of 64 B)
     static constexpr int PROF_WORDS = kProfRows * ROWW;
-    static constexpr int COLS = 32 * R;             // query columns per pass
+    static constexpr int COLS = SEG * R;            // query columns per pass
 };
 
 __device__ __forceinline__ uint32_t pack2(int lo, int hi)
@@ -87,35 +88,39 @@ __device__ __forceinline__ void store_score(const SwArgs& a, const SwBlock& B, i
     }
 }
 
-// One warp: rows [0, nrows) of its stream (every subject starts on a row that is a multiple of
-// kRowGroup) against the profile tile of this pass.  A step covers NR consecutive rows; row q
-// of the step trails row q-1 by one column inside the lane, so the NR rows form independent
-// dependency chains and the step's fixed costs (shuffles, residue and flag handling) are
-// shared by NR rows.  Lane 31 writes one score per subject per query half after the
-// subject's last row.
-// Rows per step by tile width: four, except at R = 28, where the four-row step runs at the
-// 128-register cap and measured slower than two rows.
+// One wavefront segment of SEG lanes (a whole warp, or a half-warp when SEG = 16): rows
+// [0, nrows) of its stream (every subject starts on a row that is a multiple of kRowGroup)
+// against the profile tile of this pass.  A step covers NR consecutive rows; row q of the step
+// trails row q-1 by one column inside the lane, so the NR rows form independent dependency
+// chains and the step's fixed costs (shuffles, residue and flag handling) are shared by NR
+// rows.  The segment's last lane writes one score per subject per query half after the
+// subject's last row.  All lanes of the warp run `nrows_max` (the longest segment's rows);
+// the other segment's lanes step through pad rows meanwhile.  Multi-pass tiles (boundary
+// columns in `bnd`) use SEG = 32 only.
+// Rows per step by tile width: four at every R (a row group; two-row steps are kept
+// available for tiles that would not fit the register budget).
 template <int R>
 struct RowsPerStep {
-    static constexpr int value = (R == 28) ? 2 : 4;
+    static constexpr int value = 4;
 };
 
 template <int NR> struct RowWord;
 template <> struct RowWord<2> { typedef uint16_t type; };
 template <> struct RowWord<4> { typedef uint32_t type; };
 
-template <int R>
+template <int R, int SEG>
 __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
                                           const uint32_t* __restrict__ prof,
                                           const uint8_t* __restrict__ stream, int64_t nrows,
-                                          int pass, int npass, uint4* __restrict__ bnd,
-                                          int32_t s_first, int32_t k_lo, int32_t ns_lo,
-                                          int32_t ns_hi, bool hi_valid)
+                                          int64_t nrows_max, int pass, int npass,
+                                          uint4* __restrict__ bnd, int32_t s_first,
+                                          int32_t k_lo, int32_t ns_lo, int32_t ns_hi,
+                                          bool hi_valid)
 {
-    using G = Geo<R>;
+    using G = Geo<R, SEG>;
     constexpr int NR = RowsPerStep<R>::value;
     typedef typename RowWord<NR>::type word_t;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (SEG - 1);    // lane within the segment
     const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
     const uint32_t BETA2 = (uint32_t)beta * 0x10001u;
     const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;   // H - o of an empty prefix; E, F floor
@@ -143,30 +148,30 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
     int32_t s_cur = s_first;
     const uint32_t* plane = prof + lane * G::LS;
     const int nsup = (int)(nrows / NR);           // a warp stream holds < 2^31 rows
-    const int nsteps = nsup + 31;
+    const int nsteps = (int)(nrows_max / NR) + SEG - 1;
     const word_t* stw = reinterpret_cast<const word_t*>(stream);
 
     for (int t = 0; t < nsteps; ++t) {
-        const int j = t & 31;
+        const int j = t & (SEG - 1);
         if (j == 0) {
             prev = cur;
             const int u = t + lane;
             cur = (u < nsup) ? (uint32_t)stw[u] : PADW;
-            if (pass > 0) {
+            if (SEG == 32 && pass > 0) {
 #pragma unroll
                 for (int q = 0; q < NR / 2; ++q)
                     bv[q] = (u < nsup) ? bnd[u * (NR / 2) + q] : make_uint4(BMO2, BMO2, BMO2, BMO2);
             }
         }
-        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
+        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & (SEG - 1), SEG);
         uint32_t hL[NR], eL[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
-            hL[q] = __shfl_up_sync(kFull, oh[q], 1);
-            eL[q] = __shfl_up_sync(kFull, oe[q], 1);
+            hL[q] = __shfl_up_sync(kFull, oh[q], 1, SEG);
+            eL[q] = __shfl_up_sync(kFull, oe[q], 1, SEG);
         }
-        uint32_t ai = __shfl_up_sync(kFull, out_acc, 1);
-        if (pass > 0) {
+        uint32_t ai = __shfl_up_sync(kFull, out_acc, 1, SEG);
+        if (SEG == 32 && pass > 0) {
 #pragma unroll
             for (int q = 0; q < NR / 2; ++q) {
                 const uint32_t x0 = __shfl_sync(kFull, bv[q].x, j), x1 = __shfl_sync(kFull, bv[q].y, j);
@@ -236,14 +241,14 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
 #pragma unroll
         for (int q = 0; q < NR; ++q) { oh[q] = h[q]; oe[q] = e[q]; }
         out_acc = __vmaxs2(ai, best);
-        if (lane == 31 && (rv & LASTBITS)) {
+        if (lane == SEG - 1 && (rv & LASTBITS)) {
             const int32_t s = s_cur++;
             const int32_t lo = (int32_t)(int16_t)(out_acc & 0xffffu);
             const int32_t hi = (int32_t)(int16_t)(out_acc >> 16);
             if (s < ns_lo) store_score(a, B, k_lo, s, lo, pass);
             if (hi_valid && s < ns_hi) store_score(a, B, k_lo + 1, s, hi, pass);
         }
-        if (lane == 31 && pass + 1 < npass && t >= 31) {
+        if (SEG == 32 && lane == 31 && pass + 1 < npass && t >= 31) {
 #pragma unroll
             for (int q = 0; q < NR / 2; ++q)
                 bnd[(t - 31) * (NR / 2) + q] = make_uint4(oh[2 * q], oe[2 * q], oh[2 * q + 1], oe[2 * q + 1]);
@@ -372,11 +377,17 @@ __device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
     }
 }
 
-template <int R, int W, bool TWO>
+// Persistent int16x2 kernel.  MODE kModePair: a query pair (two 16-bit halves) per task, one
+// subject stream per warp over 32 lanes.  kModeTwo: one query, two subject streams in the two
+// halves of each warp.  kModeSeg16: a query pair, two subject streams per warp, one per
+// half-warp segment of 16 lanes (short queries: 16 lanes x R columns).
+template <int R, int W, int MODE>
 __global__ void __launch_bounds__(W * 32, 16 / W)
 sw16_kernel(const __grid_constant__ SwArgs a)
 {
-    using G = Geo<R>;
+    constexpr bool TWO = (MODE == kModeTwo);
+    constexpr int SEG = (MODE == kModeSeg16) ? 16 : 32;
+    using G = Geo<R, SEG>;
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* prof = reinterpret_cast<uint32_t*>(smem);
     uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;          // [2][COLS]
@@ -407,17 +418,18 @@ sw16_kernel(const __grid_constant__ SwArgs a)
         const int32_t ns_hi = (B.kind == kTri) ? T.k + 1 : B.nb;
         const int64_t* srow = a.srows + B.srow;
 
-        // rows of this task split over the CTA's warp streams at subject boundaries
-        constexpr int NS = TWO ? 2 * W : W;
+        // rows of this task split over the CTA's streams at subject boundaries
+        constexpr int NS = (MODE == kModePair) ? W : 2 * W;
         const int64_t R0 = srow[T.s0], R1 = srow[T.s1];
-        const int u0 = TWO ? 2 * warp : warp;
+        const int u0 = (MODE == kModePair) ? warp : 2 * warp;
         const int32_t sw0 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * u0 / NS);
         const int32_t sw1 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 1) / NS);
-        const int32_t sw2 = TWO ? lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 2) / NS) : sw1;
+        const int32_t sw2 = (MODE == kModePair)
+                                ? sw1 : lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 2) / NS);
         const int64_t r_begin = srow[sw0];
         int64_t nrows = srow[sw1] - r_begin;
         int64_t nrows_hi = srow[sw2] - srow[sw1];
-        if (T.npass > 1 && (nrows > a.bnd_stride || nrows_hi > a.bnd_stride)) {
+        if (T.npass > 1 && (MODE == kModeSeg16 || nrows > a.bnd_stride || nrows_hi > a.bnd_stride)) {
             if (lane == 0) atomicExch(a.err, 1);      // boundary buffer too small: refuse
             nrows = nrows_hi = 0;
         }
@@ -443,13 +455,20 @@ sw16_kernel(const __grid_constant__ SwArgs a)
                 prof[x * G::ROWW + ln * G::LS + k] = pack2(sl, sh);
             }
             __syncthreads();
-            if (TWO) {
+            if (MODE == kModeTwo) {
                 if (nrows > 0 || nrows_hi > 0)
                     warp_dp16_two<R>(a, B, prof, stream, nrows, stream_hi, nrows_hi, pass, T.npass,
                                      bnd, sw0, sw1, T.k, ns_lo);
+            } else if (MODE == kModeSeg16) {
+                const bool upper = lane >= 16;
+                const int64_t nmax = nrows > nrows_hi ? nrows : nrows_hi;
+                if (nmax > 0)
+                    warp_dp16<R, 16>(a, B, prof, upper ? stream_hi : stream,
+                                     upper ? nrows_hi : nrows, nmax, pass, T.npass, bnd4,
+                                     upper ? sw1 : sw0, T.k, ns_lo, ns_hi, T.hi_valid != 0);
             } else if (nrows > 0) {
-                warp_dp16<R>(a, B, prof, stream, nrows, pass, T.npass, bnd4, sw0, T.k, ns_lo,
-                             ns_hi, T.hi_valid != 0);
+                warp_dp16<R, 32>(a, B, prof, stream, nrows, nrows, pass, T.npass, bnd4, sw0, T.k,
+                                 ns_lo, ns_hi, T.hi_valid != 0);
             }
             __syncthreads();
         }
