@@ -338,6 +338,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--parts-per-gpu", type=int, default=PARTS_PER_GPU,
                     help="split of the triangle; a larger value gives shorter steps (profiling)")
+    ap.add_argument("--part-offset", type=int, default=0,
+                    help="start the part sequence further along (profiling a given length range)")
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--rows", type=int, default=0)
     args = ap.parse_args()
@@ -367,7 +369,7 @@ def main():
                       autotune_seconds=round(time.perf_counter() - t0, 2))
     ctx.reset_stats()
     n_parts = args.parts_per_gpu * world
-    seq = part_sequence(n_parts, (args.warmup + args.steps) * world)
+    seq = part_sequence(n_parts, (args.warmup + args.steps) * world, args.part_offset)
     my_parts = seq[rank::world]
     d_seqs = torch.from_numpy(ss.seqs).to(dev)
     d_off = torch.from_numpy(ss.offsets).to(dev)
