@@ -285,32 +285,43 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     const int64_t nwarps = std::max<int64_t>((int64_t)max_ctas * W,
                                              (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
     uint2* d_bnd;
-    ENSURE(B_BND, nwarps * stride, d_bnd);
-    a.bnd = d_bnd;
+    ENSURE(B_BND, 2 * nwarps * stride, d_bnd);     // one half per stream
     a.bnd_stride = stride;
 
-    // one persistent launch per register-tile width R, longest tasks first within it
+    // One persistent launch per (register tile, mode) bin, longest tasks first within it.
+    // Consecutive bins alternate between the context stream and the auxiliary stream, so the
+    // next bin's CTAs take the SMs that the previous bin's CTAs leave as its queue drains
+    // (launch tails overlap); each stream has its own half of the boundary buffer.
     CUDA_TRY(cudaEventRecord(c->ev[0], st));
+    CUDA_TRY(cudaEventRecord(c->fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(c->aux, c->fork, 0));
     size_t i0 = 0;
     int bin = 0;
-    while (i0 < plan.tasks.size()) {
+    cudaError_t le = cudaSuccess;
+    while (i0 < plan.tasks.size() && le == cudaSuccess && bin < kTaskBins) {
         const int key = plan.task_R[i0];
         const int R = key / 4, mode = key % 4;
         size_t i1 = i0;
         while (i1 < plan.tasks.size() && plan.task_R[i1] == key) ++i1;
-        if (bin >= kTaskBins) return fail(c, CM_ERR_INTERNAL, "more launch bins than task tickets");
         a.tasks = d_tasks + i0;
         a.ntasks = (int32_t)(i1 - i0);
         a.task_counter = d_flags + 8 + bin;
         const int occ = sw16_occupancy(c, R, W, mode);
         const int grid = (int)std::min<int64_t>(a.ntasks, (int64_t)c->num_sms * occ);
-        CUDA_TRY(launch_sw16(R, W, mode, grid, a, st));
+        a.bnd = d_bnd + (bin & 1) * nwarps * stride;
+        le = launch_sw16(R, W, mode, grid, a, (bin & 1) ? c->aux : st);
         c->stats.launches += 1;
         c->stats.sw16_launches += 1;
         i0 = i1;
         ++bin;
     }
+    // join the auxiliary stream before any return, so no launch of this call outlives it
+    CUDA_TRY(cudaEventRecord(c->join, c->aux));
+    CUDA_TRY(cudaStreamWaitEvent(st, c->join, 0));
+    CUDA_TRY(le);
+    if (i0 < plan.tasks.size()) return fail(c, CM_ERR_INTERNAL, "more launch bins than task tickets");
     CUDA_TRY(cudaEventRecord(c->ev[1], st));
+    a.bnd = d_bnd;
 
     // int32 rescoring of every pair the int16 pass marked as possibly saturated
     PairRef* d_pref;
@@ -592,9 +603,14 @@ int cm_create(cm_ctx** out, int device)
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        delete c;
+        cudaGetLastError();
+        c->stream = nullptr;
+        cm_destroy(c);
         cudaGetLastError();
         return CM_ERR_CUDA;
     }
@@ -613,6 +629,9 @@ void cm_destroy(cm_ctx* c)
     if (c->ranker && c->ranker_free) c->ranker_free(c->ranker);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
+    if (c->aux) cudaStreamDestroy(c->aux);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
 }

@@ -33,6 +33,8 @@ struct cm_ctx {
     int W = 8;
     int rows_per_warp = 16384;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t aux = nullptr;             // second stream: alternate length bins overlap tails
+    cudaEvent_t fork = nullptr, join = nullptr;
     cm::DevBuf buf[cm::B_COUNT];
     void* ranker = nullptr;                 // learned ranker state (ranker.cu)
     void (*ranker_free)(void*) = nullptr;

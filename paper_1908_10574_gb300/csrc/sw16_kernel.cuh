@@ -68,6 +68,15 @@ __device__ __forceinline__ int32_t lower_bound64(const int64_t* v, int32_t lo, i
     return lo;
 }
 
+// subject boundary in [lo, hi] nearest to row `key` (ties to the later one): stream splits
+// land within half a subject of their target, so the warps of a task finish closer together
+__device__ __forceinline__ int32_t nearest_boundary(const int64_t* v, int32_t lo, int32_t hi,
+                                                    int64_t key)
+{
+    const int32_t s = lower_bound64(v, lo, hi, key);
+    return (s > lo && key - v[s - 1] < v[s] - key) ? s - 1 : s;
+}
+
 __device__ __forceinline__ int64_t slot_of(const SwBlock& B, int32_t k, int32_t s)
 {
     const int64_t base = (B.kind == kTri) ? (tri(k) - tri(B.k0)) : (int64_t)(k - B.k0) * B.nb;
@@ -422,10 +431,10 @@ sw16_kernel(const __grid_constant__ SwArgs a)
         constexpr int NS = (MODE == kModePair) ? W : 2 * W;
         const int64_t R0 = srow[T.s0], R1 = srow[T.s1];
         const int u0 = (MODE == kModePair) ? warp : 2 * warp;
-        const int32_t sw0 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * u0 / NS);
-        const int32_t sw1 = lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 1) / NS);
+        const int32_t sw0 = nearest_boundary(srow, T.s0, T.s1, R0 + (R1 - R0) * u0 / NS);
+        const int32_t sw1 = nearest_boundary(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 1) / NS);
         const int32_t sw2 = (MODE == kModePair)
-                                ? sw1 : lower_bound64(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 2) / NS);
+                                ? sw1 : nearest_boundary(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 2) / NS);
         const int64_t r_begin = srow[sw0];
         int64_t nrows = srow[sw1] - r_begin;
         int64_t nrows_hi = srow[sw2] - srow[sw1];
