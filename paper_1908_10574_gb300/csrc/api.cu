@@ -170,11 +170,12 @@ void choose_R(int64_t m, int* R, int* npass)
     *npass = np;
 }
 
-// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows and pick the
-// kernel mode.  A query without a partner runs in the single-query two-stream mode; a pair
-// whose longer query fits 16 lanes x 32 columns runs in the 16-lane segment mode (R per lane
-// twice that of a 32-lane tile, 16-column granularity).  Both two-stream modes take twice the
-// rows per task, split over twice as many streams.
+// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows per stream
+// and pick the kernel mode.  A query without a partner runs in a single-query mode (two
+// subject streams per 32-lane warp, or four over two 16-lane segments); a pair runs over 32
+// lanes or, when its longer query fits 16 lanes x 32 columns, in the 16-lane segment mode
+// (R per lane twice that of a 32-lane tile, 16-column granularity).  A task holds `target`
+// rows per stream of its warps.
 void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
                const int64_t* srow, int64_t target)
 {
@@ -182,14 +183,15 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
     choose_R(m_hi, &R, &np);
     int mode = hi_valid ? kModePair : kModeTwo;
     int seg = 32;
-    if (hi_valid && m_hi <= kSeg16MaxCols) {      // (the 32-lane pair kernels exist for R > 16)
-        mode = kModeSeg16;
+    if (m_hi <= (hi_valid ? kSeg16MaxCols : kTwo16MaxCols)) {   // (32-lane kernels: wider R only)
+        mode = hi_valid ? kModeSeg16 : kModeTwo16;
         seg = 16;
         R = (int)std::max<int64_t>(1, (m_hi + 15) / 16);
         np = 1;
     }
-    const bool two_streams = mode != kModePair;
-    if (two_streams) target *= 2;
+    const int spw = mode == kModePair ? 1 : mode == kModeTwo16 ? 4 : 2;   // streams per warp
+    const bool single = mode == kModeTwo || mode == kModeTwo16;
+    target *= spw;
     int32_t s = 0;
     while (s < ns) {
         const int64_t want = srow[s] + target;
@@ -202,13 +204,13 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
         t.s1 = e;
         t.npass = np;
         t.hi_valid = hi_valid ? 1 : 0;
-        t.two_streams = mode == kModeTwo;
+        t.two_streams = single;
         t.mode = mode;
         const int64_t rows = srow[e] - srow[s];
-        P.cells_padded += rows * seg * R * np * (mode == kModeTwo ? 1 : 2);
+        P.cells_padded += rows * seg * R * np * (single ? 1 : 2);
         P.tasks.push_back(t);
         P.task_R.push_back(R * 4 + mode);         // launch bin: register tile and mode
-        P.keys.push_back({rows * R * np / (two_streams ? 2 : 1), R * 4 + mode});
+        P.keys.push_back({rows * R * np / spw, R * 4 + mode});
         s = e;
     }
 }
@@ -280,7 +282,7 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     const int64_t stride = (std::max<int64_t>(plan.max_warp_rows, P.maxlen) + 64 + 1) & ~(int64_t)1;
     int max_ctas = 0;
     for (int R = 1; R <= 32; ++R)
-        for (int mode = 0; mode < 3; ++mode)
+        for (int mode = 0; mode < 4; ++mode)
             max_ctas = std::max(max_ctas, c->num_sms * sw16_occupancy(c, R, W, mode));
     const int64_t nwarps = std::max<int64_t>((int64_t)max_ctas * W,
                                              (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));

@@ -55,9 +55,11 @@ struct SwBlock {
 
 // Launch modes of the int16x2 kernel (see sw16_kernel): query pair over 32 lanes; single
 // query with two subject streams in the word halves; query pair with two subject streams,
-// one per 16-lane half-warp segment (short queries).
-enum SwMode : int32_t { kModePair = 0, kModeTwo = 1, kModeSeg16 = 2 };
-constexpr int kSeg16MaxCols = 16 * 32;   // longest query tile of the 16-lane mode
+// one per 16-lane half-warp segment; single query with four subject streams (two 16-lane
+// segments x two halves).  The 16-lane modes serve queries of at most kSeg16MaxCols.
+enum SwMode : int32_t { kModePair = 0, kModeTwo = 1, kModeSeg16 = 2, kModeTwo16 = 3 };
+constexpr int kSeg16MaxCols = 16 * 32;   // longest query tile of the 16-lane pair mode
+constexpr int kTwo16MaxCols = 16 * 25;   // ... of the 16-lane single-query mode (registers)
 
 // One CTA task.  Pair mode: the query pair (k, k+1) of a block against subjects [s0, s1),
 // the two queries in the two 16-bit halves, one subject stream per warp.  Single mode

@@ -38,7 +38,7 @@ struct cm_ctx {
     cm::DevBuf buf[cm::B_COUNT];
     void* ranker = nullptr;                 // learned ranker state (ranker.cu)
     void (*ranker_free)(void*) = nullptr;
-    int sw16_occ[3][33][3] = {};            // CTAs per SM by (W = 4/8/16, R, mode); 0 = unknown
+    int sw16_occ[3][33][4] = {};            // CTAs per SM by (W = 4/8/16, R, mode); 0 = unknown
 };
 
 namespace cm {
@@ -75,7 +75,7 @@ int ensure(cm_ctx* c, BufId id, size_t count, T** out)
 // B_FLAGS layout (int32 words): [1] kernel bounds-check flag, [2..3] int32-rerun list count and
 // ticket, [4..7] other kernels' tickets, [8 ..) one task ticket per (tile width, launch mode)
 // bin of the int16x2 kernel.
-constexpr int kTaskBins = 32 * 3;
+constexpr int kTaskBins = 32 * 4;
 constexpr int kFlagWords = 8 + kTaskBins;
 
 #define ENSURE(id, n, ptr)                                                                  \

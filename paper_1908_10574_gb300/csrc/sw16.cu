@@ -7,9 +7,9 @@ namespace cm {
 #define CM_DECL(w, m)                                                                     \
     cudaError_t launch_sw16_w##w##_m##m(int R, int grid, const SwArgs& a, cudaStream_t st); \
     int sw16_occ_w##w##_m##m(int R);
-CM_DECL(4, 0) CM_DECL(4, 1) CM_DECL(4, 2)
-CM_DECL(8, 0) CM_DECL(8, 1) CM_DECL(8, 2)
-CM_DECL(16, 0) CM_DECL(16, 1) CM_DECL(16, 2)
+CM_DECL(4, 0) CM_DECL(4, 1) CM_DECL(4, 2) CM_DECL(4, 3)
+CM_DECL(8, 0) CM_DECL(8, 1) CM_DECL(8, 2) CM_DECL(8, 3)
+CM_DECL(16, 0) CM_DECL(16, 1) CM_DECL(16, 2) CM_DECL(16, 3)
 #undef CM_DECL
 
 int sw16_ctas_per_sm(int R, int W, int mode)
@@ -17,7 +17,8 @@ int sw16_ctas_per_sm(int R, int W, int mode)
 #define CM_OCC_CASE(w)                                                                   \
     case w:                                                                              \
         return mode == kModePair ? sw16_occ_w##w##_m0(R)                                 \
-                                 : mode == kModeTwo ? sw16_occ_w##w##_m1(R) : sw16_occ_w##w##_m2(R);
+               : mode == kModeTwo ? sw16_occ_w##w##_m1(R)                                \
+               : mode == kModeSeg16 ? sw16_occ_w##w##_m2(R) : sw16_occ_w##w##_m3(R);
     switch (W) {
     CM_OCC_CASE(4)
     CM_OCC_CASE(8)
@@ -46,7 +47,8 @@ cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaS
     case w:                                                                              \
         return mode == kModePair ? launch_sw16_w##w##_m0(R, grid, a, st)                 \
                : mode == kModeTwo ? launch_sw16_w##w##_m1(R, grid, a, st)                \
-                                  : launch_sw16_w##w##_m2(R, grid, a, st);
+               : mode == kModeSeg16 ? launch_sw16_w##w##_m2(R, grid, a, st)              \
+                                    : launch_sw16_w##w##_m3(R, grid, a, st);
     switch (W) {
     CM_LAUNCH_CASE(4)
     CM_LAUNCH_CASE(8)

@@ -10,7 +10,7 @@ namespace {
 template <int R>
 constexpr int inst_smem()
 {
-    using G = Geo<R, (CM_MODE == kModeSeg16) ? 16 : 32>;
+    using G = Geo<R, (CM_MODE == kModeSeg16 || CM_MODE == kModeTwo16) ? 16 : 32>;
     return G::PROF_WORDS * 4 + 2 * G::COLS;
 }
 
@@ -41,11 +41,18 @@ int inst_occ()
 
 }  // namespace
 
-// The 32-lane pair mode only runs tiles wider than 16 lanes x 32 columns (shorter query pairs
-// take the 16-lane segment mode), so it is built for R = 17..32 only.
+// The 32-lane modes only run tiles wider than the 16-lane modes take (pair: 16 x 32 columns,
+// single query: 16 x 25), so they are built for R = 17..32 and 13..32.
 #if CM_MODE == 0
 #define CM_R_CASES(X) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \
                       X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
+#elif CM_MODE == 1
+#define CM_R_CASES(X) X(13) X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \
+                      X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
+#elif CM_MODE == 3
+#define CM_R_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
+                      X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \
+                      X(25)
 #else
 #define CM_R_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
                       X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \

@@ -97,37 +97,61 @@ __device__ __forceinline__ void store_score(const SwArgs& a, const SwBlock& B, i
     }
 }
 
-// One wavefront segment of SEG lanes (a whole warp, or a half-warp when SEG = 16): rows
-// [0, nrows) of its stream (every subject starts on a row that is a multiple of kRowGroup)
-// against the profile tile of this pass.  A step covers NR consecutive rows; row q of the step
-// trails row q-1 by one column inside the lane, so the NR rows form independent dependency
-// chains and the step's fixed costs (shuffles, residue and flag handling) are shared by NR
-// rows.  The segment's last lane writes one score per subject per query half after the
-// subject's last row.  All lanes of the warp run `nrows_max` (the longest segment's rows);
-// the other segment's lanes step through pad rows meanwhile.  Multi-pass tiles (boundary
-// columns in `bnd`) use SEG = 32 only.
-// Rows per step by tile width: four at every R (a row group; two-row steps are kept
-// available for tiles that would not fit the register budget).
-template <int R>
+// One wavefront segment of SEG lanes (a whole warp, or a half-warp when SEG = 16) against the
+// profile tile of this pass.  Every subject starts on a row that is a multiple of kRowGroup.
+//   pair (TWO = false): the two 16-bit halves are two queries; one subject stream `lo` of
+//     n_lo rows feeds both.
+//   single query (TWO = true): both halves hold the same query; the lo half runs stream `lo`
+//     (n_lo rows), the hi half stream `hi` (n_hi rows).  The profile then carries the score in
+//     its low half only, and the packed score word of a column is hi_row * 2^16 + lo_row (one
+//     multiply-add on the FMA pipe).
+// A step covers NR consecutive rows of each stream; row q of the step trails row q-1 by one
+// column inside the lane, so the NR rows form independent dependency chains and the step's
+// fixed costs (shuffles, residue and flag handling) are shared by NR rows.  The segment's
+// last lane writes one score per finished subject per half.  All lanes of the warp run
+// `nrows_max` rows (the warp's longest stream); shorter streams step through pad rows
+// meanwhile.  Multi-pass tiles (boundary columns in `bnd`) use SEG = 32 only.
+// Rows per step: four (a row group) in the pair modes.  The single-query modes carry a second
+// subject stream (a second residue-row lookup per row), which spills at four rows: two rows
+// for tiles up to 16 columns per lane, one above.
+template <int R, bool TWO>
 struct RowsPerStep {
-    static constexpr int value = 4;
+    static constexpr int value = !TWO ? 4 : (R <= 16 ? 2 : 1);
 };
 
 template <int NR> struct RowWord;
+template <> struct RowWord<1> { typedef uint8_t type; };
 template <> struct RowWord<2> { typedef uint16_t type; };
 template <> struct RowWord<4> { typedef uint32_t type; };
 
-template <int R, int SEG>
+// load the profile words of columns [c, c + 4) of one row (fewer at the tile's right edge;
+// the lane's row segment always holds whole 16-byte units)
+template <int R>
+__device__ __forceinline__ void load_cols(const uint32_t* p, int c, uint32_t (&v)[4])
+{
+    if (c + 3 <= R) {
+        const uint4 x = *reinterpret_cast<const uint4*>(p + c);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if (c + 2 == R) {
+        const uint2 x = *reinterpret_cast<const uint2*>(p + c);
+        v[0] = x.x; v[1] = x.y;
+    } else {
+        v[0] = p[c];
+    }
+}
+
+template <int R, int SEG, bool TWO>
 __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
                                           const uint32_t* __restrict__ prof,
-                                          const uint8_t* __restrict__ stream, int64_t nrows,
+                                          const uint8_t* __restrict__ st_lo, int64_t n_lo,
+                                          const uint8_t* __restrict__ st_hi, int64_t n_hi,
                                           int64_t nrows_max, int pass, int npass,
-                                          uint4* __restrict__ bnd, int32_t s_first,
+                                          uint2* __restrict__ bnd, int32_t s_lo0, int32_t s_hi0,
                                           int32_t k_lo, int32_t ns_lo, int32_t ns_hi,
                                           bool hi_valid)
 {
     using G = Geo<R, SEG>;
-    constexpr int NR = RowsPerStep<R>::value;
+    constexpr int NR = RowsPerStep<R, TWO>::value;
     typedef typename RowWord<NR>::type word_t;
     const int lane = threadIdx.x & (SEG - 1);    // lane within the segment
     const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
@@ -135,8 +159,12 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
     const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;   // H - o of an empty prefix; E, F floor
     const uint32_t O2 = (uint32_t)o * 0x10001u;
     const uint32_t NEGE = pack2(-ge, -ge);
-    const uint32_t PADW = (NR == 4) ? 0x14141414u : 0x1414u;      // kPadCode in every byte
-    uint32_t FIRSTBIT = kFirst, LASTBITS = 0;
+    const uint32_t PADW = 0x14141414u >> (32 - 8 * NR);          // kPadCode in every byte
+    // boundary records of one step: (H - o, E) of the last column of each of its rows, as
+    // uint4 pairs of rows (one uint2 when a step has one row)
+    constexpr int NB = (NR >= 2) ? NR / 2 : 1;
+    uint4* bnd4 = reinterpret_cast<uint4*>(bnd);
+    uint32_t LASTBITS = 0;
 #pragma unroll
     for (int q = 0; q < NR; ++q) LASTBITS |= (uint32_t)kLast << (8 * q);
 
@@ -150,29 +178,43 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
 #pragma unroll
     for (int q = 0; q < NR; ++q) { oh[q] = BMO2; oe[q] = BMO2; }
     uint32_t diag0 = BMO2;                        // left H - o of the previous step's last row
-    uint32_t cur = PADW, prev = PADW;
-    uint4 bv[NR / 2];
+    uint32_t cur = PADW, prev = PADW, cur2 = PADW, prev2 = PADW;
+    uint4 bv[NB];
 #pragma unroll
-    for (int q = 0; q < NR / 2; ++q) bv[q] = make_uint4(BMO2, BMO2, BMO2, BMO2);
-    int32_t s_cur = s_first;
+    for (int q = 0; q < NB; ++q) bv[q] = make_uint4(BMO2, BMO2, BMO2, BMO2);
+    int32_t s_lo = s_lo0, s_hi = s_hi0;
     const uint32_t* plane = prof + lane * G::LS;
-    const int nsup = (int)(nrows / NR);           // a warp stream holds < 2^31 rows
-    const int nsteps = (int)(nrows_max / NR) + SEG - 1;
-    const word_t* stw = reinterpret_cast<const word_t*>(stream);
+    const int nsup = (int)(n_lo / NR);            // a warp stream holds < 2^31 rows
+    const int nsup2 = TWO ? (int)(n_hi / NR) : 0;
+    const int nsup_max = (int)(nrows_max / NR);
+    const int nsteps = nsup_max + SEG - 1;
+    const word_t* stw = reinterpret_cast<const word_t*>(st_lo);
+    const word_t* stw2 = reinterpret_cast<const word_t*>(st_hi);
 
     for (int t = 0; t < nsteps; ++t) {
         const int j = t & (SEG - 1);
         if (j == 0) {
-            prev = cur;
             const int u = t + lane;
+            prev = cur;
             cur = (u < nsup) ? (uint32_t)stw[u] : PADW;
+            if (TWO) {
+                prev2 = cur2;
+                cur2 = (u < nsup2) ? (uint32_t)stw2[u] : PADW;
+            }
             if (SEG == 32 && pass > 0) {
+                if constexpr (NR >= 2) {
 #pragma unroll
-                for (int q = 0; q < NR / 2; ++q)
-                    bv[q] = (u < nsup) ? bnd[u * (NR / 2) + q] : make_uint4(BMO2, BMO2, BMO2, BMO2);
+                    for (int q = 0; q < NB; ++q)
+                        bv[q] = (u < nsup_max) ? bnd4[u * NB + q] : make_uint4(BMO2, BMO2, BMO2, BMO2);
+                } else {
+                    const uint2 v = (u < nsup_max) ? bnd[u] : make_uint2(BMO2, BMO2);
+                    bv[0] = make_uint4(v.x, v.y, BMO2, BMO2);
+                }
             }
         }
-        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & (SEG - 1), SEG);
+        const int src = (j - lane) & (SEG - 1);
+        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, src, SEG);
+        const uint32_t rw = TWO ? __shfl_sync(kFull, (lane <= j) ? cur2 : prev2, src, SEG) : 0u;
         uint32_t hL[NR], eL[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
@@ -182,10 +224,13 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
         uint32_t ai = __shfl_up_sync(kFull, out_acc, 1, SEG);
         if (SEG == 32 && pass > 0) {
 #pragma unroll
-            for (int q = 0; q < NR / 2; ++q) {
+            for (int q = 0; q < NB; ++q) {
                 const uint32_t x0 = __shfl_sync(kFull, bv[q].x, j), x1 = __shfl_sync(kFull, bv[q].y, j);
-                const uint32_t x2 = __shfl_sync(kFull, bv[q].z, j), x3 = __shfl_sync(kFull, bv[q].w, j);
-                if (lane == 0) { hL[2 * q] = x0; eL[2 * q] = x1; hL[2 * q + 1] = x2; eL[2 * q + 1] = x3; }
+                if (lane == 0) { hL[2 * q] = x0; eL[2 * q] = x1; }
+                if constexpr (NR >= 2) {
+                    const uint32_t x2 = __shfl_sync(kFull, bv[q].z, j), x3 = __shfl_sync(kFull, bv[q].w, j);
+                    if (lane == 0) { hL[2 * q + 1] = x2; eL[2 * q + 1] = x3; }
+                }
             }
         } else if (lane == 0) {
 #pragma unroll
@@ -197,16 +242,29 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
 #pragma unroll
         for (int q = 1; q < NR; ++q) dg[q] = hL[q - 1];
         diag0 = hL[NR - 1];
-        if (rv & FIRSTBIT) {                      // a subject starts at the step's first row
+        if (!TWO) {
+            if (rv & kFirst) {                    // a subject starts at the step's first row
 #pragma unroll
-            for (int k = 0; k < R; ++k) { hp[k] = BMO2; fp[k] = BMO2; }
-            best = BETA2;
-            dg[0] = BMO2;
+                for (int k = 0; k < R; ++k) { hp[k] = BMO2; fp[k] = BMO2; }
+                best = BETA2;
+                dg[0] = BMO2;
+            }
+        } else if ((rv | rw) & kFirst) {          // per half: whose stream starts a subject
+            const uint32_t keep = ((rv & kFirst) ? 0u : 0x0000ffffu) | ((rw & kFirst) ? 0u : 0xffff0000u);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                hp[k] = (hp[k] & keep) | (BMO2 & ~keep);
+                fp[k] = (fp[k] & keep) | (BMO2 & ~keep);
+            }
+            best = (best & keep) | (BETA2 & ~keep);
+            dg[0] = (dg[0] & keep) | (BMO2 & ~keep);
         }
         const uint32_t* prow[NR];
+        const uint32_t* prow2[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
             prow[q] = plane + min((rv >> (8 * q)) & 31u, (uint32_t)kPadCode) * G::ROWW;
+            if (TWO) prow2[q] = plane + min((rw >> (8 * q)) & 31u, (uint32_t)kPadCode) * G::ROWW;
             h[q] = hL[q];
             e[q] = eL[q];
         }
@@ -224,14 +282,13 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
                 const int c = k - q;
                 if (c < 0 || c >= R) continue;
                 if ((c & 3) == 0) {               // next (up to) four profile columns of row q
-                    if (c + 3 <= R) {             // the lane's row segment holds whole 16-byte units
-                        const uint4 v = *reinterpret_cast<const uint4*>(prow[q] + c);
-                        sq[q][0] = v.x; sq[q][1] = v.y; sq[q][2] = v.z; sq[q][3] = v.w;
-                    } else if (c + 2 == R) {
-                        const uint2 v = *reinterpret_cast<const uint2*>(prow[q] + c);
-                        sq[q][0] = v.x; sq[q][1] = v.y;
-                    } else {
-                        sq[q][0] = prow[q][c];
+                    load_cols<R>(prow[q], c, sq[q]);
+                    if (TWO) {
+                        uint32_t v2[4];
+                        load_cols<R>(prow2[q], c, v2);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (c + u < R) sq[q][u] = v2[u] * 0x10000u + sq[q][u];
                     }
                 }
                 e[q] = __viaddmax_s16x2(e[q], NEGE, h[q]);
@@ -250,152 +307,50 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
 #pragma unroll
         for (int q = 0; q < NR; ++q) { oh[q] = h[q]; oe[q] = e[q]; }
         out_acc = __vmaxs2(ai, best);
-        if (lane == SEG - 1 && (rv & LASTBITS)) {
-            const int32_t s = s_cur++;
+        if (lane == SEG - 1) {
             const int32_t lo = (int32_t)(int16_t)(out_acc & 0xffffu);
             const int32_t hi = (int32_t)(int16_t)(out_acc >> 16);
-            if (s < ns_lo) store_score(a, B, k_lo, s, lo, pass);
-            if (hi_valid && s < ns_hi) store_score(a, B, k_lo + 1, s, hi, pass);
+            if (!TWO) {
+                if (rv & LASTBITS) {
+                    const int32_t s = s_lo++;
+                    if (s < ns_lo) store_score(a, B, k_lo, s, lo, pass);
+                    if (hi_valid && s < ns_hi) store_score(a, B, k_lo + 1, s, hi, pass);
+                }
+            } else {
+                if (rv & LASTBITS) {
+                    const int32_t s = s_lo++;
+                    if (s < ns_lo) store_score(a, B, k_lo, s, lo, pass);
+                }
+                if (rw & LASTBITS) {
+                    const int32_t s = s_hi++;
+                    if (s < ns_lo) store_score(a, B, k_lo, s, hi, pass);
+                }
+            }
         }
         if (SEG == 32 && lane == 31 && pass + 1 < npass && t >= 31) {
+            if constexpr (NR >= 2) {
 #pragma unroll
-            for (int q = 0; q < NR / 2; ++q)
-                bnd[(t - 31) * (NR / 2) + q] = make_uint4(oh[2 * q], oe[2 * q], oh[2 * q + 1], oe[2 * q + 1]);
-        }
-    }
-}
-
-// Single-query mode: the lo and hi halves run two different subject streams (rows
-// [0, n_lo) of stream_lo and [0, n_hi) of stream_hi) against the same query.  The profile
-// holds (S, S) in both halves; per row the lo half is taken from the row of the lo residue
-// and the hi half from the row of the hi residue (one byte_perm per packed column).  First /
-// last flags, resets and score writes are per half.
-template <int R>
-__device__ __forceinline__ void warp_dp16_two(const SwArgs& a, const SwBlock& B,
-                                              const uint32_t* __restrict__ prof,
-                                              const uint8_t* __restrict__ st_lo, int64_t n_lo,
-                                              const uint8_t* __restrict__ st_hi, int64_t n_hi,
-                                              int pass, int npass, uint2* __restrict__ bnd,
-                                              int32_t s_lo0, int32_t s_hi0, int32_t k, int32_t ns)
-{
-    using G = Geo<R>;
-    const int lane = threadIdx.x & 31;
-    const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
-    const uint32_t BETA2 = (uint32_t)beta * 0x10001u;
-    const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;
-    const uint32_t O2 = (uint32_t)o * 0x10001u;
-    const uint32_t NEGE = pack2(-ge, -ge);
-
-    uint32_t hp[R], fp[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) { hp[q] = BMO2; fp[q] = BMO2; }
-    uint32_t best = BETA2, out_h = BMO2, out_e = BMO2, out_acc = BETA2, diag0 = BMO2;
-    const uint32_t padpair = (uint32_t)kPadCode | ((uint32_t)kPadCode << 8);
-    uint32_t cur = padpair, prev = padpair, bh = BMO2, be = BMO2;
-    int32_t s_lo = s_lo0, s_hi = s_hi0;
-    const uint32_t* plane = prof + lane * G::LS;
-    const int64_t nrows = n_lo > n_hi ? n_lo : n_hi;
-    const int64_t nsteps = nrows + 31;
-
-    for (int64_t t = 0; t < nsteps; ++t) {
-        const int j = (int)(t & 31);
-        if (j == 0) {
-            prev = cur;
-            const int64_t r = t + lane;
-            const uint32_t lo = (r < n_lo) ? (uint32_t)st_lo[r] : (uint32_t)kPadCode;
-            const uint32_t hi = (r < n_hi) ? (uint32_t)st_hi[r] : (uint32_t)kPadCode;
-            cur = lo | (hi << 8);
-            if (pass > 0) {
-                if (r < nrows) { const uint2 v = bnd[r]; bh = v.x; be = v.y; }
-                else { bh = BMO2; be = BMO2; }
-            }
-        }
-        const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-        uint32_t hl = __shfl_up_sync(kFull, out_h, 1);
-        uint32_t el = __shfl_up_sync(kFull, out_e, 1);
-        uint32_t ai = __shfl_up_sync(kFull, out_acc, 1);
-        if (pass > 0) {
-            const uint32_t x = __shfl_sync(kFull, bh, j);
-            const uint32_t y = __shfl_sync(kFull, be, j);
-            if (lane == 0) { hl = x; el = y; }
-        } else if (lane == 0) {
-            hl = BMO2; el = BMO2;
-        }
-        if (lane == 0) ai = BETA2;
-        uint32_t dg = diag0;
-        diag0 = hl;
-        if (rv & ((uint32_t)kFirst | ((uint32_t)kFirst << 8))) {
-            const uint32_t keep = ((rv & kFirst) ? 0u : 0x0000ffffu) |
-                                  ((rv & ((uint32_t)kFirst << 8)) ? 0u : 0xffff0000u);
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                hp[q] = (hp[q] & keep) | (BMO2 & ~keep);
-                fp[q] = (fp[q] & keep) | (BMO2 & ~keep);
-            }
-            best = (best & keep) | (BETA2 & ~keep);
-            dg = (dg & keep) | (BMO2 & ~keep);
-        }
-        const uint32_t* prow_lo = plane + min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-        const uint32_t* prow_hi = plane + min((rv >> 8) & 31u, (uint32_t)kPadCode) * G::ROWW;
-        uint32_t h = hl, e = el, hprev = BETA2;
-#pragma unroll
-        for (int j4 = 0; j4 < (R + 3) / 4; ++j4) {
-            uint32_t s4[4] = {0, 0, 0, 0};
-            if (4 * j4 + 3 <= R) {
-                const uint4 sl = *reinterpret_cast<const uint4*>(prow_lo + 4 * j4);
-                const uint4 sh = *reinterpret_cast<const uint4*>(prow_hi + 4 * j4);
-                s4[0] = __byte_perm(sl.x, sh.x, 0x7610); s4[1] = __byte_perm(sl.y, sh.y, 0x7610);
-                s4[2] = __byte_perm(sl.z, sh.z, 0x7610); s4[3] = __byte_perm(sl.w, sh.w, 0x7610);
-            } else if (4 * j4 + 2 == R) {
-                const uint2 sl = *reinterpret_cast<const uint2*>(prow_lo + 4 * j4);
-                const uint2 sh = *reinterpret_cast<const uint2*>(prow_hi + 4 * j4);
-                s4[0] = __byte_perm(sl.x, sh.x, 0x7610); s4[1] = __byte_perm(sl.y, sh.y, 0x7610);
+                for (int q = 0; q < NB; ++q)
+                    bnd4[(t - 31) * NB + q] = make_uint4(oh[2 * q], oe[2 * q], oh[2 * q + 1], oe[2 * q + 1]);
             } else {
-                s4[0] = __byte_perm(prow_lo[4 * j4], prow_hi[4 * j4], 0x7610);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = 4 * j4 + u;
-                if (q >= R) break;
-                e = __viaddmax_s16x2(e, NEGE, h);               // h, hp[]: H - o
-                const uint32_t f = __viaddmax_s16x2(fp[q], NEGE, hp[q]);
-                fp[q] = f;
-                const uint32_t d = __viaddmax_s16x2(dg, s4[u], BETA2);
-                dg = hp[q];
-                const uint32_t hh = __vimax3_s16x2(d, e, f);
-                if (u & 1) best = __vimax3_s16x2(best, hh, hprev); else hprev = hh;
-                h = hh - O2;
-                hp[q] = h;
+                bnd[t - 31] = make_uint2(oh[0], oe[0]);
             }
         }
-        if (R & 1) best = __vmaxs2(best, hprev);     // odd R: the last column has no partner
-        out_h = h;
-        out_e = e;
-        out_acc = __vmaxs2(ai, best);
-        if (lane == 31 && (rv & ((uint32_t)kLast | ((uint32_t)kLast << 8)))) {
-            if (rv & kLast) {
-                const int32_t sidx = s_lo++;
-                if (sidx < ns) store_score(a, B, k, sidx, (int32_t)(int16_t)(out_acc & 0xffffu), pass);
-            }
-            if (rv & ((uint32_t)kLast << 8)) {
-                const int32_t sidx = s_hi++;
-                if (sidx < ns) store_score(a, B, k, sidx, (int32_t)(int16_t)(out_acc >> 16), pass);
-            }
-        }
-        if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_uint2(out_h, out_e);
     }
 }
 
 // Persistent int16x2 kernel.  MODE kModePair: a query pair (two 16-bit halves) per task, one
 // subject stream per warp over 32 lanes.  kModeTwo: one query, two subject streams in the two
 // halves of each warp.  kModeSeg16: a query pair, two subject streams per warp, one per
-// half-warp segment of 16 lanes (short queries: 16 lanes x R columns).
+// half-warp segment of 16 lanes.  kModeTwo16: one query, four subject streams per warp (two
+// 16-lane segments x two halves).  The 16-lane modes serve short queries (16 lanes x R).
 template <int R, int W, int MODE>
 __global__ void __launch_bounds__(W * 32, 16 / W)
 sw16_kernel(const __grid_constant__ SwArgs a)
 {
-    constexpr bool TWO = (MODE == kModeTwo);
-    constexpr int SEG = (MODE == kModeSeg16) ? 16 : 32;
+    constexpr bool TWO = (MODE == kModeTwo || MODE == kModeTwo16);
+    constexpr int SEG = (MODE == kModeSeg16 || MODE == kModeTwo16) ? 16 : 32;
+    constexpr int SPW = (MODE == kModePair) ? 1 : (MODE == kModeTwo16) ? 4 : 2;   // streams per warp
     using G = Geo<R, SEG>;
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* prof = reinterpret_cast<uint32_t*>(smem);
@@ -409,7 +364,6 @@ sw16_kernel(const __grid_constant__ SwArgs a)
     __syncthreads();
 
     uint2* bnd = a.bnd + ((int64_t)blockIdx.x * W + warp) * a.bnd_stride;
-    uint4* bnd4 = reinterpret_cast<uint4*>(bnd);          // pair mode: one uint4 per two rows
     for (int it = 0;; ++it) {
         const int ti = s_task[it & 1];
         if (ti >= a.ntasks) break;
@@ -422,28 +376,34 @@ sw16_kernel(const __grid_constant__ SwArgs a)
         const int32_t q_hi = (!TWO && T.hi_valid) ? A_ids[T.k + 1] : q_lo;
         const int64_t qoff_lo = a.off[q_lo], m_lo = a.off[q_lo + 1] - qoff_lo;
         const int64_t qoff_hi = a.off[q_hi];
-        const int64_t m_hi = (TWO || T.hi_valid) ? a.off[q_hi + 1] - qoff_hi : 0;
+        const int64_t m_hi = (!TWO && T.hi_valid) ? a.off[q_hi + 1] - qoff_hi : 0;
         const int32_t ns_lo = (B.kind == kTri) ? T.k : B.nb;
         const int32_t ns_hi = (B.kind == kTri) ? T.k + 1 : B.nb;
         const int64_t* srow = a.srows + B.srow;
 
         // rows of this task split over the CTA's streams at subject boundaries
-        constexpr int NS = (MODE == kModePair) ? W : 2 * W;
+        constexpr int NS = W * SPW;
         const int64_t R0 = srow[T.s0], R1 = srow[T.s1];
-        const int u0 = (MODE == kModePair) ? warp : 2 * warp;
-        const int32_t sw0 = nearest_boundary(srow, T.s0, T.s1, R0 + (R1 - R0) * u0 / NS);
-        const int32_t sw1 = nearest_boundary(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 1) / NS);
-        const int32_t sw2 = (MODE == kModePair)
-                                ? sw1 : nearest_boundary(srow, T.s0, T.s1, R0 + (R1 - R0) * (u0 + 2) / NS);
-        const int64_t r_begin = srow[sw0];
-        int64_t nrows = srow[sw1] - r_begin;
-        int64_t nrows_hi = srow[sw2] - srow[sw1];
-        if (T.npass > 1 && (MODE == kModeSeg16 || nrows > a.bnd_stride || nrows_hi > a.bnd_stride)) {
-            if (lane == 0) atomicExch(a.err, 1);      // boundary buffer too small: refuse
-            nrows = nrows_hi = 0;
+        int32_t sb[SPW + 1];
+        int64_t nmax = 0;
+#pragma unroll
+        for (int i = 0; i <= SPW; ++i) {
+            sb[i] = nearest_boundary(srow, T.s0, T.s1, R0 + (R1 - R0) * (warp * SPW + i) / NS);
+            if (i > 0) nmax = max(nmax, srow[sb[i]] - srow[sb[i - 1]]);
         }
-        const uint8_t* stream = a.streams + B.stream + r_begin;
-        const uint8_t* stream_hi = a.streams + B.stream + srow[sw1];
+        // this lane's streams: index of the lo stream among the warp's SPW
+        const int seg = (SEG == 16) ? (lane >> 4) : 0;
+        const int i_lo = TWO ? 2 * seg : seg;
+        const int32_t slo0 = sb[i_lo], slo1 = sb[i_lo + 1];
+        const int32_t shi0 = TWO ? sb[i_lo + 1] : slo1, shi1 = TWO ? sb[i_lo + 2] : slo1;
+        int64_t n_lo = srow[slo1] - srow[slo0];
+        int64_t n_hi = srow[shi1] - srow[shi0];
+        if (T.npass > 1 && (SEG == 16 || nmax > a.bnd_stride)) {
+            if (lane == 0) atomicExch(a.err, 1);      // boundary buffer too small: refuse
+            n_lo = n_hi = nmax = 0;
+        }
+        const uint8_t* st_lo = a.streams + B.stream + srow[slo0];
+        const uint8_t* st_hi = a.streams + B.stream + srow[shi0];
 
         for (int pass = 0; pass < T.npass; ++pass) {
             const int64_t c0 = (int64_t)pass * G::COLS;
@@ -456,29 +416,17 @@ sw16_kernel(const __grid_constant__ SwArgs a)
                 const int x = i / G::COLS, c = i - x * G::COLS;
                 const int ln = c / R, k = c - ln * R;
                 const int ql = qres[c], qh = qres[G::COLS + c];
-                int sl = kSpad, sh = kSpad;
+                int sl = kSpad, sh = TWO ? 0 : kSpad;
                 if (x != kPadCode) {          // +o: the DP keeps H - o as its diagonal input
                     if (ql != kPadCode) sl = (B.swap ? s_mat[x * 20 + ql] : s_mat[ql * 20 + x]) + a.gap_open;
-                    if (qh != kPadCode) sh = (B.swap ? s_mat[x * 20 + qh] : s_mat[qh * 20 + x]) + a.gap_open;
+                    if (!TWO && qh != kPadCode) sh = (B.swap ? s_mat[x * 20 + qh] : s_mat[qh * 20 + x]) + a.gap_open;
                 }
                 prof[x * G::ROWW + ln * G::LS + k] = pack2(sl, sh);
             }
             __syncthreads();
-            if (MODE == kModeTwo) {
-                if (nrows > 0 || nrows_hi > 0)
-                    warp_dp16_two<R>(a, B, prof, stream, nrows, stream_hi, nrows_hi, pass, T.npass,
-                                     bnd, sw0, sw1, T.k, ns_lo);
-            } else if (MODE == kModeSeg16) {
-                const bool upper = lane >= 16;
-                const int64_t nmax = nrows > nrows_hi ? nrows : nrows_hi;
-                if (nmax > 0)
-                    warp_dp16<R, 16>(a, B, prof, upper ? stream_hi : stream,
-                                     upper ? nrows_hi : nrows, nmax, pass, T.npass, bnd4,
-                                     upper ? sw1 : sw0, T.k, ns_lo, ns_hi, T.hi_valid != 0);
-            } else if (nrows > 0) {
-                warp_dp16<R, 32>(a, B, prof, stream, nrows, nrows, pass, T.npass, bnd4, sw0, T.k,
-                                 ns_lo, ns_hi, T.hi_valid != 0);
-            }
+            if (nmax > 0)
+                warp_dp16<R, SEG, TWO>(a, B, prof, st_lo, n_lo, st_hi, n_hi, nmax, pass, T.npass,
+                                       bnd, slo0, shi0, T.k, ns_lo, ns_hi, T.hi_valid != 0);
             __syncthreads();
         }
     }
