@@ -11,7 +11,6 @@
 #include "ctx.h"
 
 namespace cm {
-int64_t compact_chunks(int64_t nslots);
 int sw32_ctas_per_sm();
 }  // namespace cm
 
@@ -358,11 +357,12 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     return CM_OK;
 }
 
-int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
-                 const std::vector<BlockReq>& req, std::vector<int32_t>& scores,
-                 std::vector<int64_t>& base, uint32_t flags)
+namespace {
+
+// Plan of a list of block requests (see score_blocks); returns the number of slots.
+int64_t plan_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
+                    const std::vector<BlockReq>& req, Plan& plan, std::vector<int64_t>& base)
 {
-    Plan plan;
     base.assign(req.size() + 1, 0);
     int64_t slots = 0;
     std::vector<int32_t> a_ids, b_ids;
@@ -419,8 +419,7 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
         }
     }
     base[req.size()] = slots;
-    scores.assign((size_t)slots, 0);
-    if (slots == 0) return CM_OK;
+    if (slots == 0) return 0;
     for (auto& B : plan.blocks) {
         B.b_ids += (int64_t)a_ids.size();
         B.a_ids = (B.a_ids < 0) ? B.b_ids : B.a_ids;
@@ -434,6 +433,19 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
     for (size_t s = 0; s + 1 < plan.srow.size(); ++s)
         maxlen_rows = std::max(maxlen_rows, plan.srow[s + 1] - plan.srow[s]);
     plan.max_warp_rows = 2 * c->rows_per_warp + 2 * maxlen_rows + 2 * target / c->W;
+    return slots;
+}
+
+}  // namespace
+
+int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
+                 const std::vector<BlockReq>& req, std::vector<int32_t>& scores,
+                 std::vector<int64_t>& base, uint32_t flags)
+{
+    Plan plan;
+    const int64_t slots = plan_blocks(c, P, ids, req, plan, base);
+    scores.assign((size_t)slots, 0);
+    if (slots == 0) return CM_OK;
     int32_t* out;
     ENSURE(B_OUT, slots, out);
     int r = run_plan(c, P, plan, out, nullptr, flags);
@@ -441,6 +453,46 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
     CUDA_TRY(cudaMemcpyAsync(scores.data(), out, slots * sizeof(int32_t), cudaMemcpyDeviceToHost,
                              c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+int score_blocks_sig(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
+                     const std::vector<BlockReq>& req, int32_t T,
+                     std::vector<std::pair<int64_t, int32_t>>& sig, std::vector<int64_t>& base,
+                     uint32_t flags)
+{
+    Plan plan;
+    const int64_t slots = plan_blocks(c, P, ids, req, plan, base);
+    sig.clear();
+    if (slots == 0) return CM_OK;
+    int32_t* out;
+    ENSURE(B_OUT, slots, out);
+    int r = run_plan(c, P, plan, out, nullptr, flags);
+    if (r) return r;
+    const cudaStream_t st = c->stream;
+    const int64_t nch = compact_chunks(slots);
+    int64_t* d_chunk;
+    ENSURE(B_CHUNK, nch + 2, d_chunk);
+    CUDA_TRY(launch_compact_slots(out, slots, T, nullptr, nullptr, d_chunk, nch, 0, st));
+    CUDA_TRY(launch_scan_chunks(d_chunk, nch, d_chunk + nch, st));
+    int64_t total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, d_chunk + nch, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->stats.launches += 2;
+    if (total == 0) return CM_OK;
+    int64_t* d_slots;
+    int32_t* d_sc;
+    ENSURE(B_POUT, total, d_slots);
+    ENSURE(B_SOUT, total, d_sc);
+    CUDA_TRY(launch_compact_slots(out, slots, T, d_slots, d_sc, d_chunk, nch, 1, st));
+    c->stats.launches += 1;
+    std::vector<int64_t> hs((size_t)total);
+    std::vector<int32_t> hv((size_t)total);
+    CUDA_TRY(cudaMemcpyAsync(hs.data(), d_slots, total * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hv.data(), d_sc, total * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    sig.resize((size_t)total);
+    for (int64_t k = 0; k < total; ++k) sig[k] = {hs[k], hv[k]};
     return CM_OK;
 }
 

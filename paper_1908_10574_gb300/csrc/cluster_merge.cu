@@ -51,6 +51,12 @@ struct Event {
 
 inline uint64_t key2(int32_t a, int32_t b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
 
+// a rep x rep pair of a merge with s > T: cs1 index, cs2 index, score
+struct SigPair {
+    int32_t i1, i2, s;
+    bool operator<(const SigPair& o) const { return i1 != o.i1 ? i1 < o.i1 : i2 < o.i2; }
+};
+
 inline double now_s()
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -92,12 +98,8 @@ int Driver::run_round(const std::vector<Merge>& ms)
     // least ranker_min_pairs pairs align only the pairs whose ranker logit reaches
     // prune_logit (one single-query block per cs1 rep); Algorithm 1 still visits cs2 in set
     // order, so the ranker changes which pairs are aligned, never the order of the loop. ----
-    std::vector<int32_t> S;
     std::vector<int64_t> base;
-    std::vector<std::vector<int32_t>> rowpos(nm);    // cs1 index -> row k in the block
     std::vector<char> ranked(nm, 0);
-    // ranked merges: per cs1 index, the kept (i2, score) in ascending i2
-    std::vector<std::vector<std::vector<std::pair<int32_t, int32_t>>>> cand(nm);
     double t0 = now_s();
     int r;
     std::vector<uint32_t> bitmap;
@@ -144,32 +146,30 @@ int Driver::run_round(const std::vector<Merge>& ms)
     std::vector<int32_t> ids;
     std::vector<BlockReq> req;
     std::vector<int64_t> block_of(nm, -1);                 // plain merges: their block
+    std::vector<std::vector<int32_t>> roworder(nm);        // plain merges: block row -> cs1 index
     std::vector<std::pair<int32_t, int32_t>> owner;        // ranked blocks: (merge, i1)
     for (size_t m = 0; m < nm; ++m) {
         const auto& cs1 = sets[ms[m].left];
         const auto& cs2 = sets[ms[m].right];
         if (!ranked[m]) {
-            std::vector<int32_t> order(cs1.size());
+            std::vector<int32_t>& order = roworder[m];
+            order.resize(cs1.size());
             std::iota(order.begin(), order.end(), 0);
             std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
                 return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
             });
-            rowpos[m].assign(cs1.size(), 0);
             BlockReq b{};
             b.kind = kCross;
             b.swap = 0;                                      // pair (rep1, rep2)
             b.a_begin = (int64_t)ids.size();
             b.a_count = (int64_t)cs1.size();
-            for (size_t k = 0; k < order.size(); ++k) {
-                rowpos[m][order[k]] = (int32_t)k;
-                ids.push_back(arena[cs1[order[k]]].rep);
-            }
+            for (size_t k = 0; k < order.size(); ++k) ids.push_back(arena[cs1[order[k]]].rep);
             b.b_begin = (int64_t)ids.size();
             b.b_count = (int64_t)cs2.size();
             for (int32_t ci : cs2) ids.push_back(arena[ci].rep);
             block_of[m] = (int64_t)req.size();
             req.push_back(b);
-            owner.push_back({-1, -1});
+            owner.push_back({(int32_t)m, -1});
         } else {
             for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
                 const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
@@ -184,34 +184,50 @@ int Driver::run_round(const std::vector<Merge>& ms)
                     for (uint32_t x = row[w]; x; x &= x - 1)
                         ids.push_back(arena[cs2[w * 32 + __builtin_ctz(x)]].rep);
                 b.b_count = (int64_t)ids.size() - b.b_begin;
+                selected += b.b_count;
                 if (b.b_count == 0) { ids.resize(b.a_begin); continue; }
                 req.push_back(b);
                 owner.push_back({(int32_t)m, i1});
             }
         }
     }
-    r = score_blocks(c, P, ids, req, S, base, flags);
+    // only the pairs with s > T can act in Algorithm 1 (every other visit is a `continue`),
+    // so only they come back from the device
+    std::vector<std::pair<int64_t, int32_t>> sig;
+    r = score_blocks_sig(c, P, ids, req, prm.T, sig, base, flags);
     if (r) return r;
-    scored += (int64_t)S.size();
-    for (size_t m = 0; m < nm; ++m)
-        if (ranked[m]) cand[m].assign(sets[ms[m].left].size(), {});
-    for (size_t bi = 0; bi < req.size(); ++bi) {
-        if (owner[bi].first < 0) continue;
-        const size_t m = (size_t)owner[bi].first;
-        const int32_t i1 = owner[bi].second;
-        const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
-        auto& lst = cand[m][i1];
-        int64_t q = 0;
-        for (int64_t w = 0; w < words[m]; ++w)
-            for (uint32_t x = row[w]; x; x &= x - 1, ++q)
-                lst.push_back({(int32_t)(w * 32 + __builtin_ctz(x)), S[base[bi] + q]});
-        selected += (int64_t)lst.size();
+    scored += base.empty() ? 0 : base.back();
+    // per merge: (i1, i2, s) with s > T in (i1, i2) order
+    std::vector<std::vector<SigPair>> sigm(nm);
+    {
+        size_t bi = 0;
+        for (const auto& e : sig) {
+            while (bi + 1 < req.size() && base[bi + 1] <= e.first) ++bi;
+            const size_t m = (size_t)owner[bi].first;
+            const int64_t local = e.first - base[bi];
+            if (!ranked[m]) {
+                const int64_t nb = req[bi].b_count;
+                sigm[m].push_back({roworder[m][local / nb], (int32_t)(local % nb), e.second});
+            } else {
+                // the local index is the rank of i2 among row i1's selected bits
+                const int32_t i1 = owner[bi].second;
+                const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
+                int64_t rank = local, w = 0;
+                for (;; ++w) {
+                    const int pc = __builtin_popcount(row[w]);
+                    if (rank < pc) break;
+                    rank -= pc;
+                }
+                uint32_t x = row[w];
+                for (int64_t k = 0; k < rank; ++k) x &= x - 1;
+                sigm[m].push_back({i1, (int32_t)(w * 32 + __builtin_ctz(x)), e.second});
+            }
+        }
+        for (size_t m = 0; m < nm; ++m)
+            if (!ranked[m]) std::sort(sigm[m].begin(), sigm[m].end());
     }
     t_rep += now_s() - t0;
     ++batches;
-    auto score_of = [&](size_t m, int32_t i1, int32_t i2) {
-        return S[base[block_of[m]] + (int64_t)rowpos[m][i1] * (int64_t)sets[ms[m].right].size() + i2];
-    };
 
     // ---- wave 2: alignment cells of every candidate full merge (s > mT and s > T) ----
     std::vector<int32_t> cp;
@@ -219,20 +235,12 @@ int Driver::run_round(const std::vector<Merge>& ms)
     for (size_t m = 0; m < nm; ++m) {
         const auto& cs1 = sets[ms[m].left];
         const auto& cs2 = sets[ms[m].right];
-        auto add = [&](int32_t i1, int32_t i2, int32_t s) {
-            if (s > prm.T && s > prm.mT) {
-                cidx[m].push_back({key2(i1, i2), (int64_t)cp.size() / 2});
-                cp.push_back(arena[cs1[i1]].rep);
-                cp.push_back(arena[cs2[i2]].rep);
+        for (const SigPair& e : sigm[m])
+            if (e.s > prm.mT) {
+                cidx[m].push_back({key2(e.i1, e.i2), (int64_t)cp.size() / 2});
+                cp.push_back(arena[cs1[e.i1]].rep);
+                cp.push_back(arena[cs2[e.i2]].rep);
             }
-        };
-        for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
-            if (ranked[m]) {
-                for (const auto& js : cand[m][i1]) add(i1, js.first, js.second);
-            } else {
-                for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2) add(i1, i2, score_of(m, i1, i2));
-            }
-        }
     }
     std::vector<int32_t> cells(cp.size() / 2 * 5);
     if (!cp.empty()) {
@@ -245,6 +253,9 @@ int Driver::run_round(const std::vector<Merge>& ms)
     }
 
     // ---- Algorithm 1 control flow per merge -> event list ----
+    // Visits are counted as Algorithm 1 makes them: i1's loop over cs2 (the plain merge) or
+    // over its selected candidates (a ranked merge), up to the break, skipping c2 already
+    // merged when i1's loop starts; the cs2 merged during i1's own loop were visited first.
     std::vector<std::vector<Event>> events(nm);
     std::vector<std::vector<int32_t>> out_sets(nm);
     for (size_t m = 0; m < nm; ++m) {
@@ -252,15 +263,18 @@ int Driver::run_round(const std::vector<Merge>& ms)
         const auto& cs2 = sets[ms[m].right];
         std::unordered_map<uint64_t, int64_t> cmap(cidx[m].begin(), cidx[m].end());
         std::vector<char> merged1(cs1.size(), 0), merged2(cs2.size(), 0);
+        std::vector<int32_t> merged_before;               // sorted cs2 indices merged so far
+        const std::vector<SigPair>& sg = sigm[m];
+        size_t p = 0;
         for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
-            const bool rk = ranked[m] != 0;
-            const int32_t nvisit = rk ? (int32_t)cand[m][i1].size() : (int32_t)cs2.size();
-            for (int32_t q = 0; q < nvisit; ++q) {
-                const int32_t i2 = rk ? cand[m][i1][q].first : q;
+            size_t p_end = p;
+            while (p_end < sg.size() && sg[p_end].i1 == i1) ++p_end;
+            int64_t end = (int64_t)cs2.size();            // visited range [0, end)
+            std::vector<int32_t> newly;
+            for (size_t q = p; q < p_end; ++q) {
+                const int32_t i2 = sg[q].i2;
                 if (merged2[i2]) continue;
-                const int32_t s = rk ? cand[m][i1][q].second : score_of(m, i1, i2);
-                ++rep_cmp;
-                if (s <= prm.T) continue;
+                const int32_t s = sg[q].s;
                 bool t21 = false, t12 = false;
                 if (s > prm.mT) {
                     const int32_t* cl = &cells[cmap.at(key2(i1, i2)) * 5];
@@ -274,16 +288,40 @@ int Driver::run_round(const std::vector<Merge>& ms)
                     events[m].push_back({kAbsorbInto2, i1, i2, s});
                     merged1[i1] = 1;
                     ++full_merges;
+                    end = (int64_t)i2 + 1;
                     break;
                 } else if (t12) {
                     events[m].push_back({kAbsorbInto1, i1, i2, s});
                     merged2[i2] = 1;
+                    newly.push_back(i2);
                     ++full_merges;
                 } else {
                     events[m].push_back({kExchange, i1, i2, s});
                     ++exchanges;
                 }
             }
+            const int64_t before = std::lower_bound(merged_before.begin(), merged_before.end(),
+                                                    (int32_t)std::min<int64_t>(end, INT32_MAX)) -
+                                   merged_before.begin();
+            if (!ranked[m]) {
+                rep_cmp += end - before;
+            } else {
+                const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
+                int64_t vis = 0;
+                for (int64_t w = 0; w * 32 < end; ++w) {
+                    uint32_t x = row[w];
+                    if ((w + 1) * 32 > end) x &= (1u << (end - w * 32)) - 1u;
+                    vis += __builtin_popcount(x);
+                }
+                for (int64_t k = 0; k < before; ++k) {
+                    const int32_t i2 = merged_before[k];
+                    vis -= (row[i2 >> 5] >> (i2 & 31)) & 1u;
+                }
+                rep_cmp += vis;
+            }
+            for (int32_t i2 : newly)
+                merged_before.insert(std::upper_bound(merged_before.begin(), merged_before.end(), i2), i2);
+            p = p_end;
         }
         for (size_t i1 = 0; i1 < cs1.size(); ++i1)
             if (!merged1[i1]) out_sets[m].push_back(cs1[i1]);

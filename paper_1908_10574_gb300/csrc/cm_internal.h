@@ -144,5 +144,9 @@ cudaError_t launch_compact_tri(const int32_t* out, int64_t nslots, int32_t k0,
                                int phase, cudaStream_t st);
 cudaError_t launch_scan_chunks(int64_t* counts, int64_t nchunks, int64_t* total,
                                cudaStream_t st);
+cudaError_t launch_compact_slots(const int32_t* out, int64_t nslots, int32_t T,
+                                 int64_t* slots_out, int32_t* scores_out, int64_t* chunk_counts,
+                                 int64_t nchunks, int phase, cudaStream_t st);
+int64_t compact_chunks(int64_t nslots);
 
 }  // namespace cm

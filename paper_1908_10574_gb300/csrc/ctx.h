@@ -157,6 +157,13 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
                  const std::vector<BlockReq>& req, std::vector<int32_t>& scores,
                  std::vector<int64_t>& base, uint32_t flags);
 
+// As score_blocks, but only the slots whose score exceeds T come back: (slot, score) in slot
+// order, compacted on the device (the full score array never leaves it).
+int score_blocks_sig(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
+                     const std::vector<BlockReq>& req, int32_t T,
+                     std::vector<std::pair<int64_t, int32_t>>& sig, std::vector<int64_t>& base,
+                     uint32_t flags);
+
 // Score and alignment cells (5 int32 per pair) of host pairs, on the device data of P.
 int run_cells(cm_ctx* c, const Prepared& P, const int32_t* host_pairs, int64_t n_pairs,
               int32_t* host_cells);

@@ -106,14 +106,18 @@ __global__ void collect_kernel(const int32_t* __restrict__ out, int64_t nslots,
     }
 }
 
-// Deterministic compaction of a triangle slice: slots [0, nslots) are pairs (k, s), s < k,
-// of the length order `order`, numbered tri(k) - tri(k0) + s.  Chunk = 256 threads x 32.
+// Deterministic compaction of the slots [0, nslots) whose score exceeds T, in slot order.
+// TRI: the slots are the pairs (k, s), s < k, of the length order `order`, numbered
+// tri(k) - tri(k0) + s, written as (min, max) sequence ids to pairs_out.  Otherwise the slot
+// index itself goes to slots_out.  Chunk = 256 threads x 32 slots; phase 0 counts per chunk,
+// phase 1 (after an exclusive scan of the counts) writes.
 constexpr int kCT = 256, kPer = 32, kChunk = kCT * kPer;
 
+template <bool TRI>
 __global__ void compact_kernel(const int32_t* __restrict__ out, int64_t nslots, int32_t k0,
                                const int32_t* __restrict__ order, int32_t T,
-                               int32_t* __restrict__ pairs_out, int32_t* __restrict__ scores_out,
-                               int64_t* chunk_counts, int phase)
+                               int32_t* __restrict__ pairs_out, int64_t* __restrict__ slots_out,
+                               int32_t* __restrict__ scores_out, int64_t* chunk_counts, int phase)
 {
     __shared__ int64_t s_warp[kCT / 32];
     const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kPer;
@@ -142,15 +146,19 @@ __global__ void compact_kernel(const int32_t* __restrict__ out, int64_t nslots, 
     }
     int64_t pos = chunk_counts[blockIdx.x] + wbase + incl - c;   // chunk_counts now exclusive
     if (c == 0) return;
-    const int64_t t0 = tri(k0);
+    const int64_t t0 = TRI ? tri(k0) : 0;
     for (int u = 0; u < kPer; ++u) {
         const int64_t i = base + u;
         if (i < nslots && out[i] > T) {
-            const int64_t k = tri_row(i + t0);
-            const int64_t s = i + t0 - tri(k);
-            const int32_t a = order[k], b = order[s];
-            pairs_out[2 * pos] = min(a, b);
-            pairs_out[2 * pos + 1] = max(a, b);
+            if (TRI) {
+                const int64_t k = tri_row(i + t0);
+                const int64_t s = i + t0 - tri(k);
+                const int32_t a = order[k], b = order[s];
+                pairs_out[2 * pos] = min(a, b);
+                pairs_out[2 * pos + 1] = max(a, b);
+            } else {
+                slots_out[pos] = i;
+            }
             scores_out[pos] = out[i];
             ++pos;
         }
@@ -238,8 +246,20 @@ cudaError_t launch_compact_tri(const int32_t* out, int64_t nslots, int32_t k0,
                                int phase, cudaStream_t st)
 {
     if (nchunks == 0) return cudaSuccess;
-    compact_kernel<<<(unsigned)nchunks, kCT, 0, st>>>(out, nslots, k0, order, T, pairs_out,
-                                                      scores_out, chunk_counts, phase);
+    compact_kernel<true><<<(unsigned)nchunks, kCT, 0, st>>>(out, nslots, k0, order, T, pairs_out,
+                                                            nullptr, scores_out, chunk_counts,
+                                                            phase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_slots(const int32_t* out, int64_t nslots, int32_t T,
+                                 int64_t* slots_out, int32_t* scores_out, int64_t* chunk_counts,
+                                 int64_t nchunks, int phase, cudaStream_t st)
+{
+    if (nchunks == 0) return cudaSuccess;
+    compact_kernel<false><<<(unsigned)nchunks, kCT, 0, st>>>(out, nslots, 0, nullptr, T, nullptr,
+                                                             slots_out, scores_out, chunk_counts,
+                                                             phase);
     return cudaGetLastError();
 }
 
