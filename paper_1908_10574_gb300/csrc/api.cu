@@ -187,6 +187,12 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
         seg = 16;
         R = (int)std::max<int64_t>(1, (m_hi + 15) / 16);
         np = 1;
+    } else if (!hi_valid) {
+        // single query over 32 lanes: column passes of at most 16 columns per lane, where the
+        // two-stream step still fits two rows into the register budget
+        np = (int)((m_hi + kTwoPassCols - 1) / kTwoPassCols);
+        const int64_t per = (m_hi + np - 1) / np;
+        R = (int)((per + 31) / 32);
     }
     const int spw = mode == kModePair ? 1 : mode == kModeTwo16 ? 4 : 2;   // streams per warp
     const bool single = mode == kModeTwo || mode == kModeTwo16;

@@ -59,7 +59,8 @@ struct SwBlock {
 // segments x two halves).  The 16-lane modes serve queries of at most kSeg16MaxCols.
 enum SwMode : int32_t { kModePair = 0, kModeTwo = 1, kModeSeg16 = 2, kModeTwo16 = 3 };
 constexpr int kSeg16MaxCols = 16 * 32;   // longest query tile of the 16-lane pair mode
-constexpr int kTwo16MaxCols = 16 * 25;   // ... of the 16-lane single-query mode (registers)
+constexpr int kTwo16MaxCols = 16 * 16;   // ... of the 16-lane single-query mode (registers)
+constexpr int kTwoPassCols = 32 * 16;    // column pass of the 32-lane single-query mode
 
 // One CTA task.  Pair mode: the query pair (k, k+1) of a block against subjects [s0, s1),
 // the two queries in the two 16-bit halves, one subject stream per warp.  Single mode

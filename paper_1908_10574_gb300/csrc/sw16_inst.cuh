@@ -41,18 +41,17 @@ int inst_occ()
 
 }  // namespace
 
-// The 32-lane modes only run tiles wider than the 16-lane modes take (pair: 16 x 32 columns,
-// single query: 16 x 25), so they are built for R = 17..32 and 13..32.
+// The tile widths each mode can be given: the 32-lane pair mode runs tiles wider than 16
+// lanes x 32 columns (R = 17..32); the single-query modes keep <= 16 columns per lane, over 16
+// lanes up to 256 residues (R = 1..16) and over 32 lanes in passes above (R = 9..16).
 #if CM_MODE == 0
 #define CM_R_CASES(X) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \
                       X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
 #elif CM_MODE == 1
-#define CM_R_CASES(X) X(13) X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \
-                      X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
+#define CM_R_CASES(X) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 #elif CM_MODE == 3
 #define CM_R_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
-                      X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \
-                      X(25)
+                      X(14) X(15) X(16)
 #else
 #define CM_R_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
                       X(14) X(15) X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) \

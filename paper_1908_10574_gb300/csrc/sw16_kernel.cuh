@@ -112,11 +112,12 @@ __device__ __forceinline__ void store_score(const SwArgs& a, const SwBlock& B, i
 // `nrows_max` rows (the warp's longest stream); shorter streams step through pad rows
 // meanwhile.  Multi-pass tiles (boundary columns in `bnd`) use SEG = 32 only.
 // Rows per step: four (a row group) in the pair modes.  The single-query modes carry a second
-// subject stream (a second residue-row lookup per row), which spills at four rows: two rows
-// for tiles up to 16 columns per lane, one above.
-template <int R, bool TWO>
+// subject stream (a second residue-row lookup per row) and fit four rows into the register
+// budget only for narrow tiles: four up to 7 columns per lane in 16-lane segments, two up
+// to 16 columns, one above (the host keeps single-query tiles at <= 16 columns per lane).
+template <int R, int SEG, bool TWO>
 struct RowsPerStep {
-    static constexpr int value = !TWO ? 4 : (R <= 16 ? 2 : 1);
+    static constexpr int value = !TWO ? 4 : (SEG == 16 && R <= 7) ? 4 : (R <= 16 ? 2 : 1);
 };
 
 template <int NR> struct RowWord;
@@ -151,7 +152,7 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
                                           bool hi_valid)
 {
     using G = Geo<R, SEG>;
-    constexpr int NR = RowsPerStep<R, TWO>::value;
+    constexpr int NR = RowsPerStep<R, SEG, TWO>::value;
     typedef typename RowWord<NR>::type word_t;
     const int lane = threadIdx.x & (SEG - 1);    // lane within the segment
     const int o = a.gap_open, ge = a.gap_extend, beta = a.beta;
