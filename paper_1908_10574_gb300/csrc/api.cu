@@ -176,7 +176,7 @@ void choose_R(int64_t m, int* R, int* npass)
 // (R per lane twice that of a 32-lane tile, 16-column granularity).  A task holds `target`
 // rows per stream of its warps.
 void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
-               const int64_t* srow, int64_t target)
+               const int64_t* srow, int64_t target, int64_t rows_total)
 {
     int R, np;
     choose_R(m_hi, &R, &np);
@@ -197,10 +197,17 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
     const int spw = mode == kModePair ? 1 : mode == kModeTwo16 ? 4 : 2;   // streams per warp
     const bool single = mode == kModeTwo || mode == kModeTwo16;
     target *= spw;
+    const int64_t ntask = srow ? 0 : std::max<int64_t>(1, (rows_total + target - 1) / target);
+    const int64_t per = srow ? 0 : (ns + ntask - 1) / ntask;
     int32_t s = 0;
     while (s < ns) {
-        const int64_t want = srow[s] + target;
-        int32_t e = (int32_t)(std::lower_bound(srow + s + 1, srow + ns + 1, want) - srow);
+        int32_t e;
+        if (srow) {
+            const int64_t want = srow[s] + target;
+            e = (int32_t)(std::lower_bound(srow + s + 1, srow + ns + 1, want) - srow);
+        } else {
+            e = (int32_t)std::min<int64_t>(ns, s + per);
+        }
         if (e > ns) e = ns;
         SwTask t{};
         t.block = block;
@@ -211,7 +218,7 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
         t.hi_valid = hi_valid ? 1 : 0;
         t.two_streams = single;
         t.mode = mode;
-        const int64_t rows = srow[e] - srow[s];
+        const int64_t rows = srow ? srow[e] - srow[s] : rows_total * (e - s) / std::max(ns, 1);
         P.cells_padded += rows * seg * R * np * (single ? 1 : 2);
         P.tasks.push_back(t);
         P.task_R.push_back(R * 4 + mode);         // launch bin: register tile and mode
@@ -247,22 +254,25 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     int64_t* d_first; int32_t* d_flags;
     ENSURE(B_BLOCKS, plan.blocks.size(), d_blocks);
     ENSURE(B_TASKS, plan.tasks.size(), d_tasks);
-    ENSURE(B_IDS, plan.ids.size(), d_ids);
-    ENSURE(B_SROW, plan.srow.size(), d_srow);
+    const int64_t nsub = plan.dev_lists ? plan.n_sub : (int64_t)plan.srow.size() - 1;
+    const int64_t n_ids = plan.dev_lists ? (int64_t)plan.ids.size() + plan.n_sub
+                                         : (int64_t)plan.ids.size();
+    ENSURE(B_IDS, n_ids, d_ids);
+    ENSURE(B_SROW, nsub + 1, d_srow);
     ENSURE(B_FIRST, plan.first_slot.size(), d_first);
     ENSURE(B_FLAGS, kFlagWords, d_flags);
-    const int64_t nrows_total = plan.srow.back();
+    const int64_t nrows_total = plan.dev_lists ? plan.total_rows : plan.srow.back();
     ENSURE(B_STREAM, nrows_total + 64, d_stream);
     int r;
     if ((r = copy_in(c, d_blocks, plan.blocks.data(), plan.blocks.size() * sizeof(SwBlock), false))) return r;
     if ((r = copy_in(c, d_tasks, plan.tasks.data(), plan.tasks.size() * sizeof(SwTask), false))) return r;
     if ((r = copy_in(c, d_ids, plan.ids.data(), plan.ids.size() * sizeof(int32_t), false))) return r;
-    if ((r = copy_in(c, d_srow, plan.srow.data(), plan.srow.size() * sizeof(int64_t), false))) return r;
+    if (!plan.dev_lists)
+        if ((r = copy_in(c, d_srow, plan.srow.data(), plan.srow.size() * sizeof(int64_t), false))) return r;
     if ((r = copy_in(c, d_first, plan.first_slot.data(), plan.first_slot.size() * sizeof(int64_t), false))) return r;
     CUDA_TRY(cudaMemsetAsync(d_flags, 0, kFlagWords * sizeof(int32_t), st));
     // the B subjects of all blocks form one list in the id pool after the A ids
-    const int64_t nsub = (int64_t)plan.srow.size() - 1;
-    const int64_t b_first = (int64_t)plan.ids.size() - nsub;
+    const int64_t b_first = n_ids - nsub;
     CUDA_TRY(launch_gather_stream(P.db, P.off, d_ids + b_first, (int32_t)nsub, d_srow, d_stream, st));
     c->stats.launches += 1;
 
@@ -475,6 +485,13 @@ int score_blocks_sig(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& i
     ENSURE(B_OUT, slots, out);
     int r = run_plan(c, P, plan, out, nullptr, flags);
     if (r) return r;
+    return compact_sig(c, out, slots, T, sig);
+}
+
+int compact_sig(cm_ctx* c, const int32_t* out, int64_t slots, int32_t T,
+                std::vector<std::pair<int64_t, int32_t>>& sig)
+{
+    sig.clear();
     const cudaStream_t st = c->stream;
     const int64_t nch = compact_chunks(slots);
     int64_t* d_chunk;

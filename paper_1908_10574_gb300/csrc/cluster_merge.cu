@@ -87,6 +87,11 @@ struct Driver {
     }
 
     int run_round(const std::vector<Merge>& ms);
+    int score_ranked(const std::vector<Merge>& ms, const std::vector<char>& ranked,
+                     const std::vector<uint32_t>& bitmap, const std::vector<int64_t>& bitbase,
+                     const std::vector<int64_t>& words, const std::vector<int64_t>& repb0,
+                     const uint32_t* d_bits, const int32_t* d_reps,
+                     std::vector<std::vector<SigPair>>& sigm);
     int finish(std::vector<int32_t>& final_set, cm_result* res);
 };
 
@@ -103,7 +108,9 @@ int Driver::run_round(const std::vector<Merge>& ms)
     double t0 = now_s();
     int r;
     std::vector<uint32_t> bitmap;
-    std::vector<int64_t> bitbase(nm, 0), words(nm, 0);
+    std::vector<int64_t> bitbase(nm, 0), words(nm, 0), repb0(nm, 0);
+    const uint32_t* d_bits = nullptr;
+    const int32_t* d_reps = nullptr;
     if (U) {
         std::vector<int32_t> rows;
         std::vector<SelTile> tiles;
@@ -119,6 +126,7 @@ int Driver::run_round(const std::vector<Merge>& ms)
             const int32_t a0 = (int32_t)rows.size();
             for (int32_t ci : cs1) rows.push_back(arena[ci].rep);
             const int32_t b0 = (int32_t)rows.size();
+            repb0[m] = b0;
             for (int32_t ci : cs2) rows.push_back(arena[ci].rep);
             for (int32_t i0 = 0; i0 < (int32_t)cs1.size(); i0 += 128)
                 for (int32_t j0 = 0; j0 < (int32_t)cs2.size(); j0 += 128) {
@@ -137,7 +145,7 @@ int Driver::run_round(const std::vector<Merge>& ms)
         }
         if (!tiles.empty()) {
             const double tr = now_s();
-            r = ranker_select(c, U, rows, tiles, prm.prune_logit, nwords, bitmap);
+            r = ranker_select(c, U, rows, tiles, prm.prune_logit, nwords, bitmap, &d_bits, &d_reps);
             if (r) return r;
             t_rank += now_s() - tr;
             ++batches;
@@ -170,62 +178,30 @@ int Driver::run_round(const std::vector<Merge>& ms)
             block_of[m] = (int64_t)req.size();
             req.push_back(b);
             owner.push_back({(int32_t)m, -1});
-        } else {
-            for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
-                const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
-                BlockReq b{};
-                b.kind = kCross;
-                b.swap = 0;
-                b.a_begin = (int64_t)ids.size();
-                b.a_count = 1;
-                ids.push_back(arena[cs1[i1]].rep);
-                b.b_begin = (int64_t)ids.size();
-                for (int64_t w = 0; w < words[m]; ++w)
-                    for (uint32_t x = row[w]; x; x &= x - 1)
-                        ids.push_back(arena[cs2[w * 32 + __builtin_ctz(x)]].rep);
-                b.b_count = (int64_t)ids.size() - b.b_begin;
-                selected += b.b_count;
-                if (b.b_count == 0) { ids.resize(b.a_begin); continue; }
-                req.push_back(b);
-                owner.push_back({(int32_t)m, i1});
-            }
         }
     }
     // only the pairs with s > T can act in Algorithm 1 (every other visit is a `continue`),
     // so only they come back from the device
     std::vector<std::pair<int64_t, int32_t>> sig;
-    r = score_blocks_sig(c, P, ids, req, prm.T, sig, base, flags);
-    if (r) return r;
-    scored += base.empty() ? 0 : base.back();
-    // per merge: (i1, i2, s) with s > T in (i1, i2) order
-    std::vector<std::vector<SigPair>> sigm(nm);
-    {
+    std::vector<std::vector<SigPair>> sigm(nm);       // per merge: (i1, i2, s), s > T
+    if (!req.empty()) {
+        r = score_blocks_sig(c, P, ids, req, prm.T, sig, base, flags);
+        if (r) return r;
+        scored += base.empty() ? 0 : base.back();
         size_t bi = 0;
         for (const auto& e : sig) {
             while (bi + 1 < req.size() && base[bi + 1] <= e.first) ++bi;
             const size_t m = (size_t)owner[bi].first;
             const int64_t local = e.first - base[bi];
-            if (!ranked[m]) {
-                const int64_t nb = req[bi].b_count;
-                sigm[m].push_back({roworder[m][local / nb], (int32_t)(local % nb), e.second});
-            } else {
-                // the local index is the rank of i2 among row i1's selected bits
-                const int32_t i1 = owner[bi].second;
-                const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
-                int64_t rank = local, w = 0;
-                for (;; ++w) {
-                    const int pc = __builtin_popcount(row[w]);
-                    if (rank < pc) break;
-                    rank -= pc;
-                }
-                uint32_t x = row[w];
-                for (int64_t k = 0; k < rank; ++k) x &= x - 1;
-                sigm[m].push_back({i1, (int32_t)(w * 32 + __builtin_ctz(x)), e.second});
-            }
+            const int64_t nb = req[bi].b_count;
+            sigm[m].push_back({roworder[m][local / nb], (int32_t)(local % nb), e.second});
         }
-        for (size_t m = 0; m < nm; ++m)
-            if (!ranked[m]) std::sort(sigm[m].begin(), sigm[m].end());
     }
+    if (d_bits) {
+        r = score_ranked(ms, ranked, bitmap, bitbase, words, repb0, d_bits, d_reps, sigm);
+        if (r) return r;
+    }
+    for (size_t m = 0; m < nm; ++m) std::sort(sigm[m].begin(), sigm[m].end());
     t_rep += now_s() - t0;
     ++batches;
 
@@ -430,6 +406,160 @@ int Driver::run_round(const std::vector<Merge>& ms)
     }
     for (size_t m = 0; m < nm; ++m) sets[ms[m].out] = std::move(out_sets[m]);
     merges += (int64_t)nm;
+    return CM_OK;
+}
+
+// Rep x rep scores of the ranked merges, planned on the device from the selection bitmap.
+// The cs1 reps of a merge are paired in length order; for a pair (a, b) the subjects both
+// select form one pair-mode block (both queries over one shared stream), those only a or
+// only b selects form single-query blocks, and an unpaired rep runs alone.  The subject
+// lists, their row tables and streams are expanded on the device; the host handles per-list
+// counts only.  Lists run in chunks of at most kRankedChunkRows stream rows.  Only the pairs
+// with s > T come back, appended to sigm[m] as (i1, i2, s).
+int Driver::score_ranked(const std::vector<Merge>& ms, const std::vector<char>& ranked,
+                         const std::vector<uint32_t>& bitmap, const std::vector<int64_t>& bitbase,
+                         const std::vector<int64_t>& words, const std::vector<int64_t>& repb0,
+                         const uint32_t* d_bits, const int32_t* d_reps,
+                         std::vector<std::vector<SigPair>>& sigm)
+{
+    constexpr int64_t kRankedChunkRows = (int64_t)8 << 30;
+    struct LMeta { int32_t m, a, b, op; int64_t count; };
+    std::vector<KeptList> lists;
+    std::vector<LMeta> meta;
+    auto derived = [&](const LMeta& L, int64_t w) -> uint32_t {
+        const uint32_t x = bitmap[bitbase[L.m] + (int64_t)L.a * words[L.m] + w];
+        if (L.op == kKeepA) return x;
+        const uint32_t y = bitmap[bitbase[L.m] + (int64_t)L.b * words[L.m] + w];
+        return L.op == kKeepAnd ? (x & y) : L.op == kKeepAOnly ? (x & ~y) : (y & ~x);
+    };
+    for (size_t m = 0; m < ms.size(); ++m) {
+        if (!ranked[m]) continue;
+        const auto& cs1 = sets[ms[m].left];
+        std::vector<int32_t> order(cs1.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
+        });
+        auto add = [&](int32_t a, int32_t b, int32_t op) {
+            LMeta L{(int32_t)m, a, b, op, 0};
+            for (int64_t w = 0; w < words[m]; ++w) L.count += __builtin_popcount(derived(L, w));
+            selected += L.count * (op == kKeepAnd ? 2 : 1);
+            if (L.count == 0) return;
+            KeptList K{};
+            K.row_a = bitbase[m] + (int64_t)a * words[m];
+            K.row_b = b >= 0 ? bitbase[m] + (int64_t)b * words[m] : K.row_a;
+            K.words = (int32_t)words[m];
+            K.op = op;
+            K.b0 = repb0[m];
+            lists.push_back(K);
+            meta.push_back(L);
+        };
+        size_t t = 0;
+        for (; t + 1 < order.size(); t += 2) {
+            add(order[t], order[t + 1], kKeepAnd);
+            add(order[t], order[t + 1], kKeepAOnly);
+            add(order[t], order[t + 1], kKeepBOnly);
+        }
+        if (t < order.size()) add(order[t], -1, kKeepA);
+    }
+    if (lists.empty()) return CM_OK;
+    const int32_t nl = (int32_t)lists.size();
+    const cudaStream_t st = c->stream;
+    KeptList* d_lists;
+    int64_t* d_tot;
+    ENSURE(B_KEPT, nl, d_lists);
+    ENSURE(B_KTOT, 2 * (int64_t)nl, d_tot);
+    int r;
+    if ((r = copy_in(c, d_lists, lists.data(), lists.size() * sizeof(KeptList), false))) return r;
+    CUDA_TRY(launch_kept_totals(d_lists, nl, d_bits, d_reps, P.off, d_tot, st));
+    std::vector<int64_t> tot(2 * (size_t)nl);
+    CUDA_TRY(cudaMemcpyAsync(tot.data(), d_tot, tot.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->stats.launches += 1;
+    const int64_t target = (int64_t)c->W * c->rows_per_warp;
+    for (int32_t l0 = 0; l0 < nl;) {
+        int32_t l1 = l0;
+        int64_t rows = 0;
+        while (l1 < nl && (l1 == l0 || rows + tot[2 * l1] <= kRankedChunkRows)) rows += tot[2 * l1++];
+        Plan plan;
+        plan.dev_lists = true;
+        plan.total_rows = rows;
+        std::vector<int64_t> first;
+        int64_t g = 0, rowbase = 0, slots = 0;
+        for (int32_t l = l0; l < l1; ++l) {
+            const LMeta& L = meta[l];
+            const auto& cs1 = sets[ms[L.m].left];
+            KeptList& K = lists[l];
+            K.g0 = g;
+            K.rowbase = rowbase;
+            const bool pair = L.op == kKeepAnd;
+            const int32_t qa = arena[cs1[L.op == kKeepBOnly ? L.b : L.a]].rep;
+            const int32_t qb = pair ? arena[cs1[L.b]].rep : qa;
+            SwBlock B{};
+            B.kind = kCross;
+            B.swap = 0;
+            B.na = pair ? 2 : 1;
+            B.nb = (int32_t)L.count;
+            B.a_ids = (int64_t)plan.ids.size();
+            plan.ids.push_back(qa);
+            if (pair) plan.ids.push_back(qb);
+            B.b_ids = -1;                                  // fixed up below (after the A ids)
+            B.stream = 0;
+            B.srow = g;
+            B.out_base = slots;
+            B.k0 = 0;
+            B.has_map = 0;
+            plan.blocks.push_back(B);
+            plan.first_slot.push_back(slots);
+            first.push_back(slots);
+            add_tasks(plan, (int32_t)plan.blocks.size() - 1, 0, (int32_t)L.count, pair, P.len(qb),
+                      nullptr, target, tot[2 * l]);
+            plan.cells += (P.len(qa) + (pair ? P.len(qb) : 0)) * tot[2 * l + 1];
+            slots += (int64_t)B.na * L.count;
+            g += L.count;
+            rowbase += tot[2 * l];
+        }
+        const int64_t nA = (int64_t)plan.ids.size();
+        for (auto& B : plan.blocks) B.b_ids = nA + B.srow;
+        plan.n_sub = g;
+        plan.nslots = plan.pairs = slots;
+        order_tasks(plan);
+        plan.max_warp_rows = 2 * c->rows_per_warp + 2 * stream_rows(P.maxlen) + 2 * target / c->W;
+        int32_t* d_ids;
+        int64_t* d_srow;
+        ENSURE(B_IDS, nA + g, d_ids);
+        ENSURE(B_SROW, g + 1, d_srow);
+        if ((r = copy_in(c, d_lists, lists.data() + l0, (size_t)(l1 - l0) * sizeof(KeptList), false))) return r;
+        CUDA_TRY(cudaMemsetAsync(d_srow, 0, sizeof(int64_t), st));
+        CUDA_TRY(launch_kept_expand(d_lists, l1 - l0, d_bits, d_reps, P.off, d_ids + nA, d_srow, st));
+        c->stats.launches += 1;
+        int32_t* out;
+        ENSURE(B_OUT, slots, out);
+        if ((r = run_plan(c, P, plan, out, nullptr, flags))) return r;
+        std::vector<std::pair<int64_t, int32_t>> sig;
+        if ((r = compact_sig(c, out, slots, prm.T, sig))) return r;
+        scored += slots;
+        for (const auto& e : sig) {
+            const int32_t l = l0 + (int32_t)(std::upper_bound(first.begin(), first.end(), e.first) -
+                                             first.begin()) - 1;
+            const LMeta& L = meta[l];
+            const int64_t local = e.first - first[l - l0];
+            const int64_t k = local / L.count;
+            int64_t rank = local % L.count, w = 0;
+            uint32_t x = 0;
+            for (;; ++w) {
+                x = derived(L, w);
+                const int pc = __builtin_popcount(x);
+                if (rank < pc) break;
+                rank -= pc;
+            }
+            for (int64_t q = 0; q < rank; ++q) x &= x - 1;
+            const int32_t i1 = (L.op == kKeepBOnly || (L.op == kKeepAnd && k == 1)) ? L.b : L.a;
+            sigm[L.m].push_back({i1, (int32_t)(w * 32 + __builtin_ctz(x)), e.second});
+        }
+        ++batches;
+        l0 = l1;
+    }
     return CM_OK;
 }
 

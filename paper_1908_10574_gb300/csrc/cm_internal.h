@@ -117,6 +117,20 @@ struct CellJob {
     int32_t pad;
 };
 
+// One subject list of a ranked block, selected by bitmap rows of the ranker's pair selection:
+// op 0 = row a, 1 = row a AND row b, 2 = row a AND NOT row b, 3 = row b AND NOT row a.  Bit i
+// of a row selects subject reps[b0 + i].  The list's subjects become global subjects g0 ..,
+// its stream rows start at rowbase.
+enum KeptOp : int32_t { kKeepA = 0, kKeepAnd = 1, kKeepAOnly = 2, kKeepBOnly = 3 };
+struct KeptList {
+    int64_t row_a, row_b;   // word offsets of the two bitmap rows (row_b unused for kKeepA)
+    int32_t words;          // words per row
+    int32_t op;             // KeptOp
+    int64_t b0;             // offset of the subject reps in `reps`
+    int64_t g0;             // first global subject index of the list
+    int64_t rowbase;        // first stream row of the list
+};
+
 // ---- launchers (sw16.cu) ---------------------------------------------------------------
 int sw16_ctas_per_sm(int R, int W, int mode);
 cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaStream_t st);
@@ -149,5 +163,13 @@ cudaError_t launch_compact_slots(const int32_t* out, int64_t nslots, int32_t T,
                                  int64_t* slots_out, int32_t* scores_out, int64_t* chunk_counts,
                                  int64_t nchunks, int phase, cudaStream_t st);
 int64_t compact_chunks(int64_t nslots);
+// per list: stream rows and residues of its subjects (totals[2*l], totals[2*l + 1])
+cudaError_t launch_kept_totals(const KeptList* lists, int32_t nlists, const uint32_t* bits,
+                               const int32_t* reps, const int64_t* off, int64_t* totals,
+                               cudaStream_t st);
+// per list: subject ids (ids[g0 + s]) and row table (srow[g0 + s + 1]) in bitmap order
+cudaError_t launch_kept_expand(const KeptList* lists, int32_t nlists, const uint32_t* bits,
+                               const int32_t* reps, const int64_t* off, int32_t* ids,
+                               int64_t* srow, cudaStream_t st);
 
 }  // namespace cm

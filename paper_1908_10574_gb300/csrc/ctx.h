@@ -18,7 +18,7 @@ struct DevBuf {
 enum BufId {
     B_DB, B_RAW, B_OFF, B_BLOCKS, B_TASKS, B_IDS, B_STREAM, B_SROW, B_OUT, B_OMAP, B_BND,
     B_FLAGS, B_PREF, B_FIRST, B_PAIRS, B_CELLS, B_SCRATCH, B_CHUNK, B_POUT, B_SOUT, B_MAT,
-    B_JOBS, B_RES, B_COUNT
+    B_JOBS, B_RES, B_KEPT, B_KTOT, B_COUNT
 };
 
 }  // namespace cm
@@ -118,7 +118,8 @@ int ranker_unit_vectors(cm_ctx* c, const Prepared& P, int64_t n, void** U_out);
 // ranker logit of (A row i, B row j) reaches thr; `bitmap` holds nwords words on return
 int ranker_select(cm_ctx* c, const void* U, const std::vector<int32_t>& rows,
                   const std::vector<SelTile>& tiles, float thr, int64_t nwords,
-                  std::vector<uint32_t>& bitmap);
+                  std::vector<uint32_t>& bitmap, const uint32_t** d_bits_out = nullptr,
+                  const int32_t** d_rows_out = nullptr);
 int ranker_alpha_beta(cm_ctx* c, float* ab);
 
 struct Plan {
@@ -132,11 +133,19 @@ struct Plan {
     int64_t nslots = 0;
     int64_t cells = 0, cells_padded = 0, pairs = 0;
     int64_t max_warp_rows = 0;
+    // Device-built subject lists: `ids` holds the A ids only; the B ids (n_sub of them) and the
+    // row table (n_sub + 1 entries, total_rows rows) already sit in the B_IDS (after the A ids)
+    // and B_SROW buffers; `srow` stays empty.
+    bool dev_lists = false;
+    int64_t n_sub = 0, total_rows = 0;
 };
 
 void choose_R(int64_t m, int* R, int* npass);
+// Tasks of one query pair (k, k+1) or single query k against the block's subjects [0, ns).
+// With `srow` the tasks split at subject boundaries by rows; without it (device-built lists)
+// into equal subject counts, `rows_total` being the rows of all ns subjects.
 void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
-               const int64_t* srow, int64_t target);
+               const int64_t* srow, int64_t target, int64_t rows_total = 0);
 void order_tasks(Plan& P);
 int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64_t* d_omap,
              uint32_t flags);
@@ -163,6 +172,10 @@ int score_blocks_sig(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& i
                      const std::vector<BlockReq>& req, int32_t T,
                      std::vector<std::pair<int64_t, int32_t>>& sig, std::vector<int64_t>& base,
                      uint32_t flags);
+
+// (slot, score) of the device slots [0, nslots) of `out` whose score exceeds T, slot order.
+int compact_sig(cm_ctx* c, const int32_t* out, int64_t nslots, int32_t T,
+                std::vector<std::pair<int64_t, int32_t>>& sig);
 
 // Score and alignment cells (5 int32 per pair) of host pairs, on the device data of P.
 int run_cells(cm_ctx* c, const Prepared& P, const int32_t* host_pairs, int64_t n_pairs,

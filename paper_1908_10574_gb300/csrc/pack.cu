@@ -192,6 +192,86 @@ __global__ void scan_kernel(int64_t* counts, int64_t n, int64_t* total)
     if (threadIdx.x == 0) *total = carry;
 }
 
+// ---- ranked subject lists: one warp per list, 32 bitmap words per iteration, bit order ----
+__device__ __forceinline__ uint32_t kept_word(const KeptList& L, const uint32_t* bits, int64_t w)
+{
+    const uint32_t a = bits[L.row_a + w];
+    if (L.op == kKeepA) return a;
+    const uint32_t b = bits[L.row_b + w];
+    return L.op == kKeepAnd ? (a & b) : L.op == kKeepAOnly ? (a & ~b) : (b & ~a);
+}
+
+__device__ __forceinline__ int64_t rows_of(int64_t len)
+{
+    return len <= 0 ? kRowGroup : (len + kRowGroup - 1) / kRowGroup * kRowGroup;
+}
+
+__global__ void kept_totals_kernel(const KeptList* __restrict__ lists, int32_t nlists,
+                                   const uint32_t* __restrict__ bits,
+                                   const int32_t* __restrict__ reps,
+                                   const int64_t* __restrict__ off, int64_t* __restrict__ totals)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (l >= nlists) return;
+    const KeptList L = lists[l];
+    int64_t rows = 0, res = 0;
+    for (int64_t w = lane; w < L.words; w += 32) {
+        for (uint32_t x = kept_word(L, bits, w); x; x &= x - 1) {
+            const int32_t id = reps[L.b0 + w * 32 + __ffs(x) - 1];
+            const int64_t len = off[id + 1] - off[id];
+            rows += rows_of(len);
+            res += len;
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        rows += __shfl_xor_sync(0xffffffffu, rows, d);
+        res += __shfl_xor_sync(0xffffffffu, res, d);
+    }
+    if (lane == 0) { totals[2 * l] = rows; totals[2 * l + 1] = res; }
+}
+
+__global__ void kept_expand_kernel(const KeptList* __restrict__ lists, int32_t nlists,
+                                   const uint32_t* __restrict__ bits,
+                                   const int32_t* __restrict__ reps,
+                                   const int64_t* __restrict__ off, int32_t* __restrict__ ids,
+                                   int64_t* __restrict__ srow)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (l >= nlists) return;
+    const KeptList L = lists[l];
+    int64_t g = L.g0, row = L.rowbase;          // next subject index and its first row
+    for (int64_t w0 = 0; w0 < L.words; w0 += 32) {
+        const int64_t w = w0 + lane;
+        const uint32_t x0 = (w < L.words) ? kept_word(L, bits, w) : 0u;
+        // rows of this lane's selected subjects, then an exclusive scan over the lanes
+        int64_t myrows = 0;
+        for (uint32_t x = x0; x; x &= x - 1) {
+            const int32_t id = reps[L.b0 + w * 32 + __ffs(x) - 1];
+            myrows += rows_of(off[id + 1] - off[id]);
+        }
+        int32_t cnt = __popc(x0);
+        int64_t rincl = myrows;
+        int32_t cincl = cnt;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t ry = __shfl_up_sync(0xffffffffu, rincl, d);
+            const int32_t cy = __shfl_up_sync(0xffffffffu, cincl, d);
+            if (lane >= d) { rincl += ry; cincl += cy; }
+        }
+        int64_t gi = g + cincl - cnt, ri = row + rincl - myrows;
+        for (uint32_t x = x0; x; x &= x - 1) {
+            const int32_t id = reps[L.b0 + w * 32 + __ffs(x) - 1];
+            ri += rows_of(off[id + 1] - off[id]);
+            ids[gi] = id;
+            srow[gi + 1] = ri;
+            ++gi;
+        }
+        g += __shfl_sync(0xffffffffu, cincl, 31);
+        row += __shfl_sync(0xffffffffu, rincl, 31);
+    }
+}
+
 int grid_for(int64_t n, int threads)
 {
     int64_t g = (n + threads - 1) / threads;
@@ -271,5 +351,25 @@ cudaError_t launch_scan_chunks(int64_t* counts, int64_t nchunks, int64_t* total,
 }
 
 int64_t compact_chunks(int64_t nslots) { return (nslots + kChunk - 1) / kChunk; }
+
+cudaError_t launch_kept_totals(const KeptList* lists, int32_t nlists, const uint32_t* bits,
+                               const int32_t* reps, const int64_t* off, int64_t* totals,
+                               cudaStream_t st)
+{
+    if (nlists == 0) return cudaSuccess;
+    kept_totals_kernel<<<(unsigned)(((int64_t)nlists * 32 + 255) / 256), 256, 0, st>>>(
+        lists, nlists, bits, reps, off, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kept_expand(const KeptList* lists, int32_t nlists, const uint32_t* bits,
+                               const int32_t* reps, const int64_t* off, int32_t* ids,
+                               int64_t* srow, cudaStream_t st)
+{
+    if (nlists == 0) return cudaSuccess;
+    kept_expand_kernel<<<(unsigned)(((int64_t)nlists * 32 + 255) / 256), 256, 0, st>>>(
+        lists, nlists, bits, reps, off, ids, srow);
+    return cudaGetLastError();
+}
 
 }  // namespace cm

@@ -833,7 +833,8 @@ int ranker_alpha_beta(cm_ctx* c, float* ab)
 // Bitmaps of the (A row, B row) pairs of every tile whose ranker logit reaches thr.
 int ranker_select(cm_ctx* c, const void* Uv, const std::vector<int32_t>& rows,
                   const std::vector<SelTile>& tiles, float thr, int64_t nwords,
-                  std::vector<uint32_t>& bitmap)
+                  std::vector<uint32_t>& bitmap, const uint32_t** d_bits_out,
+                  const int32_t** d_rows_out)
 {
     const bf16* U = static_cast<const bf16*>(Uv);
     bitmap.assign((size_t)nwords, 0u);
@@ -859,6 +860,8 @@ int ranker_select(cm_ctx* c, const void* Uv, const std::vector<int32_t>& rows,
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(bitmap.data(), d_bits, nwords * 4, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (d_bits_out) *d_bits_out = d_bits;
+    if (d_rows_out) *d_rows_out = d_rows;
     return CM_OK;
 }
 
