@@ -329,7 +329,7 @@ def main():
     ap.add_argument("--train-seqs", type=int, default=100000)
     ap.add_argument("--train-pairs", type=int, default=1000000)
     ap.add_argument("--epochs", type=int, default=10)
-    ap.add_argument("--keep", type=float, default=0.999)
+    ap.add_argument("--keep", type=float, default=0.9995)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--transductive", action="store_true",
                     help="cm: train the ranker on the set being clustered (as the 100k setup)")

@@ -170,6 +170,59 @@ def test_ranked_merge_prune_everything_large_matches_oracle(ctx):
         assert st["ranker_selected"] == 0
 
 
+def _standardized_params(ss, seed):
+    """Random ranker weights with the last conv layer rescaled so that every output channel
+    of the sequence vectors has zero mean and unit variance over `ss` (float64, oracle side)."""
+    flat = R.init_params(seed).astype(np.float32).astype(np.float64)
+    p = R.unpack(flat)
+    V = R.embed(ss.seqs, ss.offsets, flat)
+    mu, sd = V.mean(0), V.std(0) + 1e-6
+    p["W3"][...] = p["W3"] / sd[None, None, :]
+    p["b3"][...] = (p["b3"] - mu) / sd
+    return flat.astype(np.float32)
+
+
+def test_ranked_merge_partial_pruning_matches_oracle(ctx):
+    """A threshold inside the logit distribution selects part of every large merge's rep pairs
+    (pair-mode lists of shared selections and single-query lists of the rest).  The oracle
+    merge with keep = (its float64 logit >= threshold) must give the same clusters and pairs.
+    The threshold is placed so that every pair within BF16 reach of it scores <= T: pruning
+    such a pair or visiting it is the same `continue` in Algorithm 1, so only the
+    rep-comparison count may differ, by at most the number of those pairs."""
+    rng = np.random.default_rng(31)     # 4 families of 10 + 60 singletons: few significant pairs
+    ss = synth.families(4, 10, rng.integers(60, 301, size=4), 31, singletons=60,
+                        singleton_lengths=rng.integers(60, 301, size=60))
+    n = len(ss)
+    tri = oracle.triangle_pairs(n)
+    truth, scores = oracle.all_pairs(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, T=100)
+    M = np.zeros((n, n), np.int64)
+    M[np.triu_indices(n, 1)] = scores
+    M = M + M.T
+    params = _standardized_params(ss, 7)
+    z = R.logits(ss.seqs, ss.offsets, params.astype(np.float64), tri)
+    Z = np.zeros((n, n))
+    Z[tri[:, 0], tri[:, 1]] = z
+    Z = Z + Z.T
+    sig = M[tri[:, 0], tri[:, 1]] > 100
+    band = 0.08
+    cands = np.quantile(z, np.linspace(0.3, 0.7, 81))
+    ok = [t for t in cands if not sig[np.abs(z - t) < band].any()]
+    assert ok, "no threshold with only non-significant pairs near it"
+    thr = float(ok[len(ok) // 2])
+    ambiguous = int((np.abs(z - thr) < band).sum())
+    want = oracle.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, T=100, mT=138, mU=15,
+                                score_matrix=M, keep=lambda a, b: Z[a, b] >= thr, min_pairs=4)
+    ctx.ranker_set_params(params)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, 100, 138, 15,
+                            use_ranker=True, prune_logit=thr, ranker_min_pairs=4)
+    assert got["clusters"] == want["clusters"]
+    assert got["pairs"].tolist() == want["pairs"].tolist()
+    st, ws = got["stats"], want["stats"]
+    assert (st["exchange_comparisons"], st["intra_comparisons"]) == (ws["exchange"], ws["intra"])
+    assert abs(st["rep_comparisons"] - ws["rep"]) <= ambiguous
+    assert 0 < st["ranker_selected"] < n * (n - 1) // 2
+
+
 def test_selection_kernel_keeps_the_pairs_above_threshold(ctx):
     """With full merges disabled every pair of sequences meets exactly once as a rep pair, so
     the tensor-core selection must keep exactly the pairs whose logit (computed by the separate
