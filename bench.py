@@ -221,8 +221,10 @@ def run_cluster_merge(args):
     8 plus 20,000 singletons); recall against the GPU all-against-all when --recall."""
     import torch
     import paper_1908_10574_gb300 as cm
-    n = args.cm_seqs
-    ss = synth.proteome(n, family_size=8, singleton_frac=0.2, stream=3)
+    ss = synth.proteome(args.cm_seqs, family_size=8, singleton_frac=0.2, stream=3)
+    if args.long_tail:
+        ss = synth.long_tail(ss, args.long_tail, args.long_motifs)
+    n = len(ss)
     ctx = cm.Context(0)
     T, mT, mU = T_SIG, M_T, M_U
     ranker = None
@@ -246,8 +248,10 @@ def run_cluster_merge(args):
     out = {"metric": "ClusterMerge seconds", "value": dt, "unit": "s", "n_gpus": 1,
            "higher_is_better": False, "data": "synthetic", "dtype": "int16",
            "config": {"workload": "ClusterMerge of %d synthetic proteins (lognormal lengths, "
-                                  "families of 8 + 20%% singletons), BLOSUM62 11/1, T=%d, mT=%d, "
-                                  "mU=%d" % (n, T, mT, mU)},
+                                  "families of 8 + 20%% singletons%s), BLOSUM62 11/1, T=%d, mT=%d, "
+                                  "mU=%d" % (n, (", + %d tandem repeats of 10,000-35,000 residues in "
+                                                 "%d motif families" % (args.long_tail, args.long_motifs))
+                                             if args.long_tail else "", T, mT, mU)},
            "clusters": len(res["clusters"]), "similar_pairs": len(res["pairs"]),
            "stats": res["stats"], "ranker": ranker}
     if args.recall:
@@ -325,6 +329,9 @@ def main():
                     help="allpairs: SW GCUPS (default); cm: ClusterMerge seconds")
     ap.add_argument("--cm-seqs", type=int, default=100000)
     ap.add_argument("--recall", action="store_true")
+    ap.add_argument("--long-tail", type=int, default=0,
+                    help="cm: add this many long tandem repeats (the long-tail workload)")
+    ap.add_argument("--long-motifs", type=int, default=10)
     ap.add_argument("--ranker", action="store_true", help="cm: also run the learned-ranker merge")
     ap.add_argument("--train-seqs", type=int, default=100000)
     ap.add_argument("--train-pairs", type=int, default=1000000)

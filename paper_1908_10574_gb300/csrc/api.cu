@@ -355,6 +355,15 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
         if (cnt == 0) break;
         const int32_t n = std::min(cnt, cap);
         c->stats.saturated += n;
+        if (n > 1) {        // longest pairs first: the persistent warps claim them in order
+            std::vector<PairRef> lst((size_t)n);
+            CUDA_TRY(cudaMemcpyAsync(lst.data(), d_pref, n * sizeof(PairRef), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            std::stable_sort(lst.begin(), lst.end(), [&](const PairRef& x, const PairRef& y) {
+                return P.len(x.q) * P.len(x.x) > P.len(y.q) * P.len(y.x);
+            });
+            if ((r = copy_in(c, d_pref, lst.data(), lst.size() * sizeof(PairRef), false))) return r;
+        }
         const int grid = (int)std::min<int64_t>(n, (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
         CUDA_TRY(launch_sw32(16, grid, a, d_pref, n, d_flags + 3, st));
         c->stats.launches += 1;
@@ -524,11 +533,18 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
     if (n_pairs == 0) return CM_OK;
     if (n_pairs >= ((int64_t)1 << 31)) return fail(c, CM_ERR_ARG, "n_pairs must be < 2^31");
     const cudaStream_t st = c->stream;
+    // jobs longest first (the persistent warps claim them in order), pad = the pair's index
+    auto lpt = [](std::vector<CellJob>& v) {
+        std::stable_sort(v.begin(), v.end(), [](const CellJob& x, const CellJob& y) {
+            return (int64_t)x.m * x.n > (int64_t)y.m * y.n;
+        });
+    };
     std::vector<CellJob> jobs((size_t)n_pairs);
     for (int64_t k = 0; k < n_pairs; ++k) {
         const int32_t x = hp[2 * k], y = hp[2 * k + 1];
-        jobs[k] = CellJob{x, y, (int32_t)P.len(x), (int32_t)P.len(y), 0, 0};
+        jobs[k] = CellJob{x, y, (int32_t)P.len(x), (int32_t)P.len(y), 0, (int32_t)k};
     }
+    lpt(jobs);
     CellJob* d_jobs;
     int32_t *d_res, *d_flags;
     uint2* d_bnd;
@@ -565,15 +581,17 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
         if (dir == 0) {
             fwd = res;
             std::vector<CellJob> rev;
-            for (int64_t k = 0; k < n_pairs; ++k) {
+            for (size_t q = 0; q < jobs.size(); ++q) {
+                const int64_t k = jobs[q].pad;
                 int32_t* cl = hcells + 5 * k;
-                cl[0] = fwd[3 * k];
+                cl[0] = fwd[3 * q];
                 cl[1] = cl[2] = cl[3] = cl[4] = 0;
-                if (fwd[3 * k] > 0)
-                    rev.push_back(CellJob{jobs[k].a, jobs[k].b, fwd[3 * k + 1] + 1,
-                                          fwd[3 * k + 2] + 1, 1, (int32_t)k});
+                if (fwd[3 * q] > 0)
+                    rev.push_back(CellJob{jobs[q].a, jobs[q].b, fwd[3 * q + 1] + 1,
+                                          fwd[3 * q + 2] + 1, 1, (int32_t)k});
             }
             if (rev.empty()) break;
+            lpt(rev);
             jobs.swap(rev);
         } else {
             for (size_t q = 0; q < jobs.size(); ++q) {

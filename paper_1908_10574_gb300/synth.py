@@ -205,9 +205,12 @@ def proteome(n_seqs=20000, family_size=10, singleton_frac=0.0, stream=2):
                     singletons=n_single, singleton_lengths=lognormal_lengths(rng, n_single))
 
 
-def tandem_repeat(rng, length, motif_len=40, sub_rate=0.05):
-    """Long self-similar sequence: copies of one random motif, each copy with 5 % substitutions."""
-    motif = random_seq(rng, motif_len)
+def tandem_repeat(rng, length, motif_len=40, sub_rate=0.05, motif=None):
+    """Long self-similar sequence: copies of one motif (random unless given), each copy with
+    5 % substitutions."""
+    if motif is None:
+        motif = random_seq(rng, motif_len)
+    motif_len = len(motif)
     reps = []
     while sum(len(r) for r in reps) < length:
         c = motif.copy()
@@ -215,6 +218,21 @@ def tandem_repeat(rng, length, motif_len=40, sub_rate=0.05):
         c[m] = random_seq(rng, int(m.sum()))
         reps.append(c)
     return np.concatenate(reps)[:length]
+
+
+def long_tail(base, n_long, n_motifs, stream=5, lo=10000, hi=35000, motif_len=40):
+    """`base` plus `n_long` long tandem repeats of lengths uniform [lo, hi], in `n_motifs`
+    families that share a 40-residue motif (members of one family align over their whole
+    length with scores far above the int16 range).  The long sequences are appended after
+    base's; family labels continue base's."""
+    rng = _rng(500 + stream)
+    motifs = [random_seq(rng, motif_len) for _ in range(n_motifs)]
+    longs = [tandem_repeat(rng, int(rng.integers(lo, hi + 1)), motif=motifs[i % n_motifs])
+             for i in range(n_long)]
+    fam0 = int(base.family.max()) + 1 if base.family is not None and len(base) else 0
+    fam = None if base.family is None else np.concatenate(
+        [base.family, fam0 + np.arange(n_long, dtype=np.int32) % n_motifs])
+    return SeqSet.from_list([base[i] for i in range(len(base))] + longs, fam)
 
 
 def random_pairs(n_seqs, n_pairs, stream=3):

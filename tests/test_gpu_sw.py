@@ -99,6 +99,32 @@ def test_every_tile_width_single_query_mode_exact(ctx):
     assert np.array_equal(got, want)
 
 
+def test_long_tail_tandem_repeats_exact(ctx):
+    """Long tandem repeats sharing a motif align over their whole length with scores far above
+    the int16 range (int32 rerun); pairs with short proteins and across motifs stay small."""
+    base = synth.proteome(30, family_size=10, stream=9)
+    ss = synth.long_tail(base, 6, 2, stream=9, lo=8000, hi=12000)
+    n = len(ss)
+    longs = list(range(30, n))
+    pairs = np.array([(i, j) for i in longs for j in longs if i < j] +
+                     [(i, j) for i in longs for j in range(0, 30, 7)], dtype=np.int32)
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert np.array_equal(got, want)
+    assert (want > 32767).sum() >= 6                  # same-motif pairs overflow int16
+    st = ctx.stats()
+    assert st["saturated"] > 0
+    # the same pairs through the all-against-all path (significant set and scores)
+    p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, 100)
+    tri = oracle.triangle_pairs(n)
+    sel = np.isin(tri[:, 0], longs) | np.isin(tri[:, 1], longs)
+    ws = oracle.sw_batch(ss.seqs, ss.offsets, tri[sel], S62, 11, 1)
+    want_sig = {(int(i), int(j)): int(v) for (i, j), v in zip(tri[sel], ws) if v > 100}
+    got_sig = {(int(i), int(j)): int(v) for (i, j), v in zip(np.asarray(p), np.asarray(s))
+               if int(i) in longs or int(j) in longs}
+    assert got_sig == want_sig
+
+
 def test_empty_sequences(ctx):
     rng = np.random.default_rng(3)
     seqs = [np.zeros(0, np.uint8), synth.random_seq(rng, 50), np.zeros(0, np.uint8),
