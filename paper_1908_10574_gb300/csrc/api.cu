@@ -299,8 +299,9 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     for (int R = 1; R <= 32; ++R)
         for (int mode = 0; mode < 4; ++mode)
             max_ctas = std::max(max_ctas, c->num_sms * sw16_occupancy(c, R, W, mode));
-    const int64_t nwarps = std::max<int64_t>((int64_t)max_ctas * W,
-                                             (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
+    const int64_t nwarps = std::max<int64_t>(std::max<int64_t>((int64_t)max_ctas * W,
+                                             (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm())),
+                                             (int64_t)c->num_sms * kLongSlots);
     uint2* d_bnd;
     ENSURE(B_BND, 2 * nwarps * stride, d_bnd);     // one half per stream
     a.bnd_stride = stride;
@@ -345,7 +346,7 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     const int32_t cap = (int32_t)std::min<int64_t>(std::max<int64_t>(plan.nslots, 1), 1 << 20);
     ENSURE(B_PREF, cap, d_pref);
     for (int round = 0;; ++round) {
-        CUDA_TRY(cudaMemsetAsync(d_flags + 2, 0, 2 * sizeof(int32_t), st));
+        CUDA_TRY(cudaMemsetAsync(d_flags + 2, 0, 4 * sizeof(int32_t), st));
         CUDA_TRY(launch_collect_saturated(out, plan.nslots, d_blocks, (int32_t)plan.blocks.size(),
                                           d_first, d_ids, d_omap, d_pref, d_flags + 2, cap, st));
         int32_t cnt = 0;
@@ -355,23 +356,38 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
         if (cnt == 0) break;
         const int32_t n = std::min(cnt, cap);
         c->stats.saturated += n;
-        if (n > 1) {        // longest pairs first: the persistent warps claim them in order
-            std::vector<PairRef> lst((size_t)n);
-            CUDA_TRY(cudaMemcpyAsync(lst.data(), d_pref, n * sizeof(PairRef), cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(cudaStreamSynchronize(st));
-            std::stable_sort(lst.begin(), lst.end(), [&](const PairRef& x, const PairRef& y) {
-                return P.len(x.q) * P.len(x.x) > P.len(y.q) * P.len(y.x);
-            });
-            if ((r = copy_in(c, d_pref, lst.data(), lst.size() * sizeof(PairRef), false))) return r;
+        // Long pairs (many column passes) first, on whole CTAs; the rest longest first on one
+        // warp each (the persistent warps claim them in order).
+        std::vector<PairRef> lst((size_t)n);
+        CUDA_TRY(cudaMemcpyAsync(lst.data(), d_pref, n * sizeof(PairRef), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        auto is_long = [&](const PairRef& x) {
+            return P.len(x.q) >= kLongMinCols && P.len(x.x) >= kLongMinRows;
+        };
+        std::stable_sort(lst.begin(), lst.end(), [&](const PairRef& x, const PairRef& y) {
+            const bool lx = is_long(x), ly = is_long(y);
+            if (lx != ly) return lx;
+            return P.len(x.q) * P.len(x.x) > P.len(y.q) * P.len(y.x);
+        });
+        if ((r = copy_in(c, d_pref, lst.data(), lst.size() * sizeof(PairRef), false))) return r;
+        int32_t nlong = 0;
+        while (nlong < n && is_long(lst[nlong])) ++nlong;
+        if (nlong > 0) {
+            CUDA_TRY(launch_long_sw32((int)std::min<int64_t>(nlong, c->num_sms), a, d_pref, nlong,
+                                      d_flags + 5, st));
+            c->stats.launches += 1;
         }
-        const int grid = (int)std::min<int64_t>(n, (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
-        CUDA_TRY(launch_sw32(16, grid, a, d_pref, n, d_flags + 3, st));
-        c->stats.launches += 1;
+        if (n > nlong) {
+            const int grid = (int)std::min<int64_t>(n - nlong, (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
+            CUDA_TRY(launch_sw32(16, grid, a, d_pref + nlong, n - nlong, d_flags + 3, st));
+            c->stats.launches += 1;
+        }
         if (round > 64) return fail(c, CM_ERR_INTERNAL, "int32 rerun did not converge");
     }
     int32_t kerr = 0;
     CUDA_TRY(cudaMemcpyAsync(&kerr, d_flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (kerr == 2) return fail(c, CM_ERR_TIMEOUT, "a long-pair pipeline wait gave up");
     if (kerr) return fail(c, CM_ERR_INTERNAL, "kernel bounds check fired (boundary buffer)");
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
@@ -534,8 +550,12 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
     if (n_pairs >= ((int64_t)1 << 31)) return fail(c, CM_ERR_ARG, "n_pairs must be < 2^31");
     const cudaStream_t st = c->stream;
     // jobs longest first (the persistent warps claim them in order), pad = the pair's index
-    auto lpt = [](std::vector<CellJob>& v) {
-        std::stable_sort(v.begin(), v.end(), [](const CellJob& x, const CellJob& y) {
+    // long jobs (many column passes) first, for whole CTAs; the rest longest first
+    auto is_long = [](const CellJob& x) { return x.n >= kLongMinCols && x.m >= kLongMinRows; };
+    auto lpt = [&](std::vector<CellJob>& v) {
+        std::stable_sort(v.begin(), v.end(), [&](const CellJob& x, const CellJob& y) {
+            const bool lx = is_long(x), ly = is_long(y);
+            if (lx != ly) return lx;
             return (int64_t)x.m * x.n > (int64_t)y.m * y.n;
         });
     };
@@ -554,7 +574,7 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
     const int occ = std::max(1, cells_wf_ctas_per_sm());
     const int grid = (int)std::min<int64_t>(n_pairs, (int64_t)c->num_sms * occ);
     const int64_t stride = P.maxlen + 64;
-    ENSURE(B_BND, (int64_t)grid * stride, d_bnd);
+    ENSURE(B_BND, std::max<int64_t>(grid, (int64_t)c->num_sms * kLongSlots) * stride, d_bnd);
     SwArgs a{};
     a.db = P.db;
     a.off = P.off;
@@ -569,14 +589,26 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
         int r = copy_in(c, d_jobs, jobs.data(), jobs.size() * sizeof(CellJob), false);
         if (r) return r;
         CUDA_TRY(cudaMemsetAsync(d_flags, 0, kFlagWords * sizeof(int32_t), st));
-        CUDA_TRY(launch_cells_wf(grid, a, d_jobs, (int32_t)jobs.size(), d_flags + 4, d_res, st));
-        c->stats.launches += 1;
+        int32_t nlong = 0;
+        while (nlong < (int32_t)jobs.size() && is_long(jobs[nlong])) ++nlong;
+        if (nlong > 0) {
+            CUDA_TRY(launch_long_cells((int)std::min<int64_t>(nlong, c->num_sms), a, d_jobs, nlong,
+                                       d_flags + 6, d_res, st));
+            c->stats.launches += 1;
+        }
+        const int32_t nshort = (int32_t)jobs.size() - nlong;
+        if (nshort > 0) {
+            CUDA_TRY(launch_cells_wf((int)std::min<int64_t>(grid, nshort), a, d_jobs + nlong, nshort,
+                                     d_flags + 4, d_res + 3 * (int64_t)nlong, st));
+            c->stats.launches += 1;
+        }
         std::vector<int32_t> res(jobs.size() * 3);
         int32_t kerr = 0;
         CUDA_TRY(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaMemcpyAsync(&kerr, d_flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        if (kerr == 2) return fail(c, CM_ERR_TIMEOUT, "a long-pair pipeline wait gave up");
         if (kerr) return fail(c, CM_ERR_INTERNAL, "cells kernel bounds check fired");
         if (dir == 0) {
             fwd = res;

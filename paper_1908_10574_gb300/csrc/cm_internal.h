@@ -138,6 +138,14 @@ cudaError_t launch_sw32(int R, int grid, const SwArgs& a, const PairRef* pr, int
                         int32_t* counter, cudaStream_t st);
 int sw32_smem_bytes(int R);
 int cells_wf_ctas_per_sm();
+// long pairs on a whole CTA (longpair.cu): one CTA per SM, kLongSlots boundary slots per CTA
+constexpr int kLongSlots = 8;
+constexpr int64_t kLongMinCols = 2048, kLongMinRows = 512;
+int long_pair_smem();
+cudaError_t launch_long_sw32(int grid, const SwArgs& a, const PairRef* pr, int32_t npairs,
+                             int32_t* counter, cudaStream_t st);
+cudaError_t launch_long_cells(int grid, const SwArgs& a, const CellJob* jobs, int32_t njobs,
+                              int32_t* counter, int32_t* res, cudaStream_t st);
 cudaError_t launch_cells_wf(int grid, const SwArgs& a, const CellJob* jobs, int32_t njobs,
                             int32_t* counter, int32_t* res, cudaStream_t st);
 

@@ -123,6 +123,13 @@ def test_long_tail_tandem_repeats_exact(ctx):
     got_sig = {(int(i), int(j)): int(v) for (i, j), v in zip(np.asarray(p), np.asarray(s))
                if int(i) in longs or int(j) in longs}
     assert got_sig == want_sig
+    # alignment cells of long pairs (whole-CTA pipeline: >= 2,048 columns, >= 512 rows),
+    # same-motif and cross-motif, both orientations, plus long x short
+    cp = np.array([(longs[0], longs[2]), (longs[2], longs[0]), (longs[1], longs[3]),
+                   (longs[0], longs[1]), (longs[4], 3), (5, longs[5])], dtype=np.int32)
+    cells = ctx.sw_cells_batch(ss.seqs, ss.offsets, cp, S62, 11, 1)
+    for k, (x, y) in enumerate(cp):
+        assert tuple(cells[k]) == oracle.sw_cells(ss[x], ss[y], S62, 11, 1), (k, x, y)
 
 
 def test_empty_sequences(ctx):
