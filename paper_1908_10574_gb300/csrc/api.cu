@@ -174,7 +174,7 @@ void choose_R(int64_t m, int* R, int* npass)
 // subject streams per 32-lane warp, or four over two 16-lane segments); a pair runs over 32
 // lanes or, when its longer query fits 16 lanes x 32 columns, in the 16-lane segment mode
 // (R per lane twice that of a 32-lane tile, 16-column granularity).  A task holds `target`
-// rows per stream of its warps.
+// rows per stream of its warps, divided by the query's column passes.
 void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
                const int64_t* srow, int64_t target, int64_t rows_total)
 {
@@ -196,7 +196,9 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
     }
     const int spw = mode == kModePair ? 1 : mode == kModeTwo16 ? 4 : 2;   // streams per warp
     const bool single = mode == kModeTwo || mode == kModeTwo16;
-    target *= spw;
+    // a task streams its rows once per column pass: size it by work (rows x passes), so that
+    // the tasks of long queries stay as long as everyone else's
+    target = std::max<int64_t>(target * spw / np, 2048);
     const int64_t ntask = srow ? 0 : std::max<int64_t>(1, (rows_total + target - 1) / target);
     const int64_t per = srow ? 0 : (ns + ntask - 1) / ntask;
     int32_t s = 0;

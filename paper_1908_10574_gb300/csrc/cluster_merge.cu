@@ -51,6 +51,9 @@ struct Event {
 
 inline uint64_t key2(int32_t a, int32_t b) { return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b; }
 
+// Longest sequence streamed as a subject (one warp's rows); longer ones are made queries.
+constexpr int64_t kLongSubject = 4096;
+
 // a rep x rep pair of a merge with s > T: cs1 index, cs2 index, score
 struct SigPair {
     int32_t i1, i2, s;
@@ -153,31 +156,53 @@ int Driver::run_round(const std::vector<Merge>& ms)
     }
     std::vector<int32_t> ids;
     std::vector<BlockReq> req;
-    std::vector<int64_t> block_of(nm, -1);                 // plain merges: their block
-    std::vector<std::vector<int32_t>> roworder(nm);        // plain merges: block row -> cs1 index
-    std::vector<std::pair<int32_t, int32_t>> owner;        // ranked blocks: (merge, i1)
+    // Plain merges: queries = cs1 reps (length order) against the cs2 reps in set order.  A
+    // subject is one warp's stream and cannot be split, so cs2 reps longer than kLongSubject
+    // become queries of a second block against the cs1 reps instead (f is symmetric here).
+    std::vector<std::vector<int32_t>> qorder(nm), sorder(nm);   // block rows / subjects -> index
+    std::vector<std::vector<int32_t>> lorder(nm);                 // long cs2 reps (queries)
+    std::vector<std::pair<int32_t, int32_t>> owner;        // plain blocks: (merge, 0 | 1 transposed)
     for (size_t m = 0; m < nm; ++m) {
         const auto& cs1 = sets[ms[m].left];
         const auto& cs2 = sets[ms[m].right];
-        if (!ranked[m]) {
-            std::vector<int32_t>& order = roworder[m];
-            order.resize(cs1.size());
-            std::iota(order.begin(), order.end(), 0);
+        if (ranked[m]) continue;
+        auto by_len = [&](const std::vector<int32_t>& cs, std::vector<int32_t>& order) {
             std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-                return P.len(arena[cs1[x]].rep) < P.len(arena[cs1[y]].rep);
+                return P.len(arena[cs[x]].rep) < P.len(arena[cs[y]].rep);
             });
+        };
+        std::vector<int32_t>& order = qorder[m];
+        order.resize(cs1.size());
+        std::iota(order.begin(), order.end(), 0);
+        by_len(cs1, order);
+        for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2)
+            (P.len(arena[cs2[i2]].rep) > kLongSubject ? lorder[m] : sorder[m]).push_back(i2);
+        by_len(cs2, lorder[m]);
+        if (!sorder[m].empty()) {
             BlockReq b{};
             b.kind = kCross;
             b.swap = 0;                                      // pair (rep1, rep2)
             b.a_begin = (int64_t)ids.size();
             b.a_count = (int64_t)cs1.size();
-            for (size_t k = 0; k < order.size(); ++k) ids.push_back(arena[cs1[order[k]]].rep);
+            for (int32_t k : order) ids.push_back(arena[cs1[k]].rep);
             b.b_begin = (int64_t)ids.size();
-            b.b_count = (int64_t)cs2.size();
-            for (int32_t ci : cs2) ids.push_back(arena[ci].rep);
-            block_of[m] = (int64_t)req.size();
+            b.b_count = (int64_t)sorder[m].size();
+            for (int32_t i2 : sorder[m]) ids.push_back(arena[cs2[i2]].rep);
             req.push_back(b);
-            owner.push_back({(int32_t)m, -1});
+            owner.push_back({(int32_t)m, 0});
+        }
+        if (!lorder[m].empty()) {
+            BlockReq b{};
+            b.kind = kCross;
+            b.swap = 1;                                      // pair (rep1, rep2) = (subject, query)
+            b.a_begin = (int64_t)ids.size();
+            b.a_count = (int64_t)lorder[m].size();
+            for (int32_t i2 : lorder[m]) ids.push_back(arena[cs2[i2]].rep);
+            b.b_begin = (int64_t)ids.size();
+            b.b_count = (int64_t)cs1.size();
+            for (int32_t ci : cs1) ids.push_back(arena[ci].rep);
+            req.push_back(b);
+            owner.push_back({(int32_t)m, 1});
         }
     }
     // only the pairs with s > T can act in Algorithm 1 (every other visit is a `continue`),
@@ -194,7 +219,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
             const size_t m = (size_t)owner[bi].first;
             const int64_t local = e.first - base[bi];
             const int64_t nb = req[bi].b_count;
-            sigm[m].push_back({roworder[m][local / nb], (int32_t)(local % nb), e.second});
+            if (owner[bi].second == 0)
+                sigm[m].push_back({qorder[m][local / nb], sorder[m][local % nb], e.second});
+            else
+                sigm[m].push_back({(int32_t)(local % nb), lorder[m][local / nb], e.second});
         }
     }
     if (d_bits) {
@@ -376,8 +404,28 @@ int Driver::run_round(const std::vector<Merge>& ms)
         std::vector<int32_t> reps;
         for (auto& kv : need) reps.push_back(kv.first);
         std::sort(reps.begin(), reps.end());
+        std::vector<std::pair<int32_t, int32_t>> eown;    // block -> (rep, -1) or (rep, long member)
         for (int32_t rp : reps) {
             auto& mv = need[rp];
+            std::vector<int32_t> shortm;
+            for (int32_t x : mv) {
+                if (P.len(x) > kLongSubject) {              // a long member is a query (see wave 1)
+                    BlockReq b{};
+                    b.kind = kCross;
+                    b.swap = 0;                             // pair (member, rep)
+                    b.a_begin = (int64_t)eids.size();
+                    b.a_count = 1;
+                    eids.push_back(x);
+                    b.b_begin = (int64_t)eids.size();
+                    b.b_count = 1;
+                    eids.push_back(rp);
+                    ereq.push_back(b);
+                    eown.push_back({rp, x});
+                } else {
+                    shortm.push_back(x);
+                }
+            }
+            if (shortm.empty()) continue;
             BlockReq b{};
             b.kind = kCross;
             b.swap = 1;
@@ -385,9 +433,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
             b.a_count = 1;
             eids.push_back(rp);
             b.b_begin = (int64_t)eids.size();
-            b.b_count = (int64_t)mv.size();
-            eids.insert(eids.end(), mv.begin(), mv.end());
+            b.b_count = (int64_t)shortm.size();
+            eids.insert(eids.end(), shortm.begin(), shortm.end());
             ereq.push_back(b);
+            eown.push_back({rp, -1});
         }
         std::vector<int32_t> ES;
         std::vector<int64_t> ebase;
@@ -398,7 +447,11 @@ int Driver::run_round(const std::vector<Merge>& ms)
         scored += (int64_t)ES.size();
         ++batches;
         for (size_t b = 0; b < ereq.size(); ++b) {
-            const int32_t rp = eids[ereq[b].a_begin];
+            const int32_t rp = eown[b].first;
+            if (eown[b].second >= 0) {
+                memo[key2(eown[b].second, rp)] = ES[ebase[b]];
+                continue;
+            }
             for (int64_t s = 0; s < ereq[b].b_count; ++s)
                 memo[key2(eids[ereq[b].b_begin + s], rp)] = ES[ebase[b] + s];
         }

@@ -82,3 +82,16 @@ def test_proteome_subset_with_singletons_exact_and_recall(ctx):
     p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, T=T)
     assert sorted(zip(p[:, 0].tolist(), p[:, 1].tolist(), s.tolist())) == \
         sorted(map(tuple, truth.tolist()))
+
+
+@pytest.mark.parametrize("T,mT,mU", [(100, 138, 15), (60, 10 ** 6, 15)])
+def test_long_sequences_exact(ctx, T, mT, mU):
+    """Tandem repeats of 4,500-7,000 residues among ordinary proteins: reps longer than the
+    subject limit are scored as queries (rep waves and exchange waves), same-motif pairs
+    overflow int16 and take the whole-CTA int32 path; results must not change."""
+    base = synth.proteome(60, family_size=6, singleton_frac=0.3, stream=4)
+    ss = synth.long_tail(base, 6, 2, stream=4, lo=4500, hi=7000)
+    want = _oracle_cm(ss, T, mT, mU)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T, mT, mU)
+    _check(got, want)
+
