@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -66,10 +67,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, directory):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+        self.path = os.path.join(directory, "clocks_rank%d.csv" % device_index)
 
     def start(self):
         try:
@@ -343,6 +344,8 @@ def main():
     ap.add_argument("--min-pairs", type=int, default=100000,
                     help="cm: merges with fewer rep x rep pairs stay unpruned")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
+                    help="where the SM-clock samples of the timed region are written")
     ap.add_argument("--parts-per-gpu", type=int, default=PARTS_PER_GPU,
                     help="split of the triangle; a larger value gives shorter steps (profiling)")
     ap.add_argument("--part-offset", type=int, default=0,
@@ -396,7 +399,7 @@ def main():
     ctx.reset_stats()
     if args.steps < 1:
         return
-    clk = ClockSampler(local)
+    clk = ClockSampler(local, args.clocks_dir)
     clk.start()
     barrier(world)
     torch.cuda.synchronize()
@@ -432,7 +435,7 @@ def main():
             "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
             "kernel": "sw16_kernel (int16x2 DPX wavefront)",
             "peak_basis": "%d SMs x median SM clock under load x 64 DPX/ALU-pipe lane-ops per "
-                          "clk per SM x 2 cells per 4.5 ops (derived, see DESIGN.md)" % n_sm,
+                          "clk per SM x 2 cells per 4.5 ops (derived from the measured DPX pipe rate)" % n_sm,
             "sw16_ms_per_launch": st["sw16_ms"] / max(st["sw16_launches"], 1),
             "cells_per_launch": st["cells"] / max(st["sw16_launches"], 1),
             "padded_cell_fraction": (st["cells"] / st["cells_padded"]) if st["cells_padded"] else None}

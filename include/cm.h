@@ -185,8 +185,8 @@ void cm_result_free(cm_result *result);
 
 /* ---- learned representative ranker (orders and prunes rep x rep comparisons) ----
  * The paper has no learned component; this network only decides which representative pairs
- * are aligned (and in which order) inside Algorithm 1 — the exact Smith-Waterman score stays
- * the sole judge of similarity.  Model: residue embedding (20 x 32) -> conv1d 32->128 (width
+ * are aligned (and in which order) inside Algorithm 1 — the exact Smith-Waterman score alone
+ * decides similarity.  Model: residue embedding (20 x 32) -> conv1d 32->128 (width
  * 9) + ReLU -> conv1d 128->128 + ReLU -> conv1d 128->128 -> mean over the sequence -> v (128-d);
  * logit(a, b) = alpha * cos(v_a, v_b) + beta, cos = <a,b> / sqrt((|a|^2+1e-6)(|b|^2+1e-6)),
  * trained with binary cross-entropy on labels

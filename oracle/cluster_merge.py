@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here:
   * significance is f > T everywhere (Sec. 3 defines significant pairs by f(i, j) > T); the
     `continue` test of Algorithm 1 is therefore "s <= T".
   * the typo IsMerged in Algorithm 1 means HasBeenMerged.

@@ -1,6 +1,6 @@
 // Learned representative ranker: a small 1-D convolutional sequence embedding whose dot
 // products order and prune the representative comparisons of ClusterMerge; the exact
-// Smith-Waterman score remains the only judge of similarity.
+// Smith-Waterman score alone decides similarity.
 //
 // Network (per sequence of length L, rows = residues):
 //   X0 = E[code]                       (20 x 32 embedding)
