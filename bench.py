@@ -232,11 +232,18 @@ def run_cluster_merge(args):
     if args.ranker:
         ranker = train_ranker(ctx, args.train_seqs, args.train_pairs, args.epochs, args.keep,
                               lr=args.lr, train_set=ss if args.transductive else None)
+    elif args.ranker_untrained is not None:
+        # profiling the ranked path without training: standardised random weights, pruning at
+        # a quantile of random-pair logits (the pruning is not meaningful, the work is)
+        ctx.ranker_init(13)
+        ctx.ranker_standardize(ss.seqs, ss.offsets, max_sample=2048)
+        z = ctx.ranker_logits(ss.seqs, ss.offsets, synth.random_pairs(len(ss), 20000, stream=21))
+        ranker = {"untrained": True, "prune_logit": float(np.quantile(z, args.ranker_untrained))}
     t0 = time.perf_counter()
     res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT, mU)
     dt = time.perf_counter() - t0
     ranked = None
-    if args.ranker:
+    if ranker is not None:
         t1 = time.perf_counter()
         ranked = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT,
                                    mU, use_ranker=True, prune_logit=ranker["prune_logit"],
@@ -334,6 +341,9 @@ def main():
                     help="cm: add this many long tandem repeats (the long-tail workload)")
     ap.add_argument("--long-motifs", type=int, default=10)
     ap.add_argument("--ranker", action="store_true", help="cm: also run the learned-ranker merge")
+    ap.add_argument("--ranker-untrained", type=float, default=None, metavar="Q",
+                    help="cm: run the ranked merge with untrained (standardised) weights, pruning "
+                         "at the Q-quantile of random-pair logits (profiling the ranked path)")
     ap.add_argument("--train-seqs", type=int, default=100000)
     ap.add_argument("--train-pairs", type=int, default=1000000)
     ap.add_argument("--epochs", type=int, default=10)
