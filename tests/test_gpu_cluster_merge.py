@@ -95,3 +95,22 @@ def test_long_sequences_exact(ctx, T, mT, mU):
     got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T, mT, mU)
     _check(got, want)
 
+
+
+def test_empty_and_tiny_sequences_exact(ctx):
+    """Empty and one-residue proteins among ordinary ones: their scores are 0, they never join
+    a cluster by similarity, and the counts still match the sequential algorithm."""
+    base = synth.proteome(50, family_size=5, singleton_frac=0.2, stream=6)
+    rng = np.random.default_rng(6)
+    seqs = [base[i] for i in range(len(base))]
+    for k in (0, 7, 19, 33, 49):
+        seqs.insert(k, np.zeros(0, np.uint8) if k % 2 == 0 else synth.random_seq(rng, 1))
+    ss = synth.SeqSet.from_list(seqs)
+    want = _oracle_cm(ss, 100, 138, 15)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 100, 138, 15)
+    _check(got, want)
+    ctx.ranker_init(5)                    # keeps every pair below: the weights do not matter
+    ranked = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 100, 138, 15, use_ranker=True,
+                               prune_logit=-1e30, ranker_min_pairs=0)
+    assert ranked["clusters"] == want["clusters"]
+    assert ranked["pairs"].tolist() == want["pairs"].tolist()
