@@ -264,3 +264,33 @@ def test_autotune_choice_cache_and_unchanged_scores(ctx, tmp_path):
     after = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
     assert np.array_equal(before, after)
     assert np.array_equal(after, oracle.sw_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1))
+
+
+def test_full_size_allpairs_sampled_exact(ctx):
+    """The all-against-all of 20,000 proteome-shaped proteins in the autotuned launch
+    configuration and the 16-part split the benchmark times.  Checked on a 100,000-pair random
+    sample (significant exactly when the oracle scores > T, with the same score) and on the
+    scores of every significant pair near or above the int16 range plus 5,000 others."""
+    ss = synth.proteome(20000, 10)
+    n = len(ss)
+    ctx.autotune(ss.seqs, ss.offsets, S62, 11, 1, sample_seqs=3000)
+    sig = {}
+    for part in range(16):
+        p, s = ctx.sw_allpairs(ss.seqs, ss.offsets, S62, 11, 1, 100, part, 16, capacity=1 << 20)
+        sig.update({(int(i), int(j)): int(v) for (i, j), v in zip(p, s)})
+    rng = np.random.default_rng(2020)
+    a = rng.integers(0, n, 120000)
+    b = rng.integers(0, n, 120000)
+    keep = a != b
+    pairs = np.unique(np.stack([np.minimum(a, b), np.maximum(a, b)], 1)[keep], axis=0)[:100000]
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs.astype(np.int32), S62, 11, 1)
+    for (i, j), w in zip(pairs, want):
+        if w > 100:
+            assert sig.get((int(i), int(j))) == int(w), (i, j, w)
+        else:
+            assert (int(i), int(j)) not in sig, (i, j, w)
+    keys = np.array(list(sig.keys()), dtype=np.int32)
+    vals = np.array(list(sig.values()))
+    pick = np.concatenate([np.flatnonzero(vals >= 32767 - 11),
+                           rng.choice(len(keys), 5000, replace=False)])
+    assert np.array_equal(oracle.sw_batch(ss.seqs, ss.offsets, keys[pick], S62, 11, 1), vals[pick])
