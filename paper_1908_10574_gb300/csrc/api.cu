@@ -218,7 +218,6 @@ void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int
         t.s1 = e;
         t.npass = np;
         t.hi_valid = hi_valid ? 1 : 0;
-        t.two_streams = single;
         t.mode = mode;
         const int64_t rows = srow ? srow[e] - srow[s] : rows_total * (e - s) / std::max(ns, 1);
         P.cells_padded += rows * seg * R * np * (single ? 1 : 2);

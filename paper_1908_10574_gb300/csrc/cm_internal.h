@@ -62,18 +62,17 @@ constexpr int kSeg16MaxCols = 16 * 32;   // longest query tile of the 16-lane pa
 constexpr int kTwo16MaxCols = 16 * 16;   // ... of the 16-lane single-query mode (registers)
 constexpr int kTwoPassCols = 32 * 16;    // column pass of the 32-lane single-query mode
 
-// One CTA task.  Pair mode: the query pair (k, k+1) of a block against subjects [s0, s1),
-// the two queries in the two 16-bit halves, one subject stream per warp.  Single mode
-// (two_streams = 1): query k alone against subjects [s0, s1), each warp running two subject
-// streams in the two halves.  `mode` is the kernel's SwMode.
+// One CTA task: query k (single-query modes) or the query pair (k, k+1) (pair modes, the two
+// queries in the two 16-bit halves) of a block against subjects [s0, s1), whose rows are split
+// over the CTA's subject streams.  `mode` is the SwMode of the launch the task belongs to.
 struct SwTask {
     int32_t block;
     int32_t k;          // lo query index; hi = k+1 (if hi_valid)
-    int32_t s0, s1;     // subjects covered (rows split over the CTA's warps)
-    int32_t npass;      // column passes of 32*R columns
-    int32_t hi_valid;   // pair mode: 0 when the lo query has no partner
-    int32_t two_streams;
+    int32_t s0, s1;     // subjects covered (rows split over the CTA's streams)
+    int32_t npass;      // column passes of SEG*R columns
+    int32_t hi_valid;   // 0 when the lo query has no partner
     int32_t mode;
+    int32_t pad;
 };
 
 struct SwArgs {
