@@ -58,6 +58,12 @@ def total_cells(ss):
     return int((L.sum() ** 2 - (L ** 2).sum()) / 2)
 
 
+# DRAM bytes per cell of the int16 kernel, from one ncu capture of the small case
+# (`--parts-per-gpu 512 --part-offset 50 --warps 16 --rows 8192`): 6,589,184 bytes read and 0
+# written for 64,034,019,251 cells; sequence rows are re-read from L2, not HBM.
+DRAM_BYTES_PER_CELL = 6589184 / 64034019251
+
+
 def part_sequence(n_parts, count, offset=0):
     return [((3 + 5 * (i + offset)) % n_parts) for i in range(count)]
 
@@ -441,8 +447,13 @@ def main():
     clk_mhz = clocks["sm_mhz"] if clocks else None
     achieved = st["cells"] / (st["sw16_ms"] * 1e-3) / 1e9 if st["sw16_ms"] > 0 else None
     peak = n_sm * (clk_mhz * 1e6) * CELLS_PER_CLK_PER_SM / 1e9 if clk_mhz else None
+    cells_per_launch = st["cells"] / max(st["sw16_launches"], 1)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
-            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "frac": (achieved / peak) if (achieved and peak) else None,
+            "traffic": DRAM_BYTES_PER_CELL * cells_per_launch,
+            "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the "
+                             "small case (part 253 of 512: sw16_kernel<22,16,0>, 6.40e10 cells, "
+                             "6.59 MB read, 0 written), scaled by cells per launch",
             "kernel": "sw16_kernel (int16x2 DPX wavefront)",
             "peak_basis": "%d SMs x median SM clock under load x 64 DPX/ALU-pipe lane-ops per "
                           "clk per SM x 2 cells per 4.5 ops (derived from the measured DPX pipe rate)" % n_sm,
