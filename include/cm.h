@@ -48,7 +48,7 @@ extern "C" {
 #define CM_ERR_RESIDUE    -2   /* residue code >= 20, or non-amino-acid letter with CM_ASCII */
 #define CM_ERR_OOM        -3   /* device or host allocation failed */
 #define CM_ERR_CUDA       -4   /* a CUDA call failed; message in cm_last_error() */
-#define CM_ERR_TIMEOUT    -5   /* a bounded device wait gave up (work queue never filled) */
+#define CM_ERR_TIMEOUT    -5   /* a bounded device wait gave up (a long pair's pass pipeline) */
 #define CM_ERR_CAPACITY   -6   /* output capacity too small; *n_found holds the needed size */
 #define CM_ERR_INTERNAL   -7   /* a kernel's own bounds check fired (a library bug) */
 
