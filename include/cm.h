@@ -202,6 +202,12 @@ int cm_ranker_set_params(cm_ctx *ctx, const float *params, int64_t n);
 int cm_ranker_standardize(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets,
                           int32_t n_seqs, int32_t max_sample, uint32_t flags);
 int cm_ranker_get_params(cm_ctx *ctx, float *params, int64_t n);
+/* Save the parameters to a file / load them from one: 8 bytes "CMRANK01", the parameter count
+ * as a little-endian int64, then the parameters as little-endian float32, in the order above.
+ * Errors: CM_ERR_ARG for a null path, an unreadable or unwritable file, or a file whose tag or
+ * count does not match (nothing is loaded then); saving needs parameters to be set. */
+int cm_ranker_save(cm_ctx *ctx, const char *path);
+int cm_ranker_load(cm_ctx *ctx, const char *path);
 /* mean BCE loss of the pairs and its gradient w.r.t. every parameter (grad may be NULL) */
 int cm_ranker_loss_grad(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
                         const int32_t *pairs, const float *labels, int64_t n_pairs,

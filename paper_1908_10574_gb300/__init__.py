@@ -9,6 +9,7 @@ The library is loaded on first use; importing the package does not need a GPU.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -238,6 +239,14 @@ class Context:
         out = np.empty(self.ranker_num_params(), dtype=np.float32)
         _L.check(self._h, _L.lib().cm_ranker_get_params(self._h, _ptr(out), len(out)))
         return out
+
+    def ranker_save(self, path):
+        """Write the ranker parameters to `path` (see cm_ranker_save)."""
+        _L.check(self._h, _L.lib().cm_ranker_save(self._h, os.fsencode(path)))
+
+    def ranker_load(self, path):
+        """Read ranker parameters saved by ranker_save (see cm_ranker_load)."""
+        _L.check(self._h, _L.lib().cm_ranker_load(self._h, os.fsencode(path)))
 
     def ranker_standardize(self, seqs, offsets, max_sample=1024, flags=0):
         seqs, offsets = self._host_seqs(seqs, offsets)

@@ -91,6 +91,8 @@ def lib():
         "cm_ranker_init": (ctypes.c_int, [p, ctypes.c_uint64]),
         "cm_ranker_set_params": (ctypes.c_int, [p, p, i64]),
         "cm_ranker_get_params": (ctypes.c_int, [p, p, i64]),
+        "cm_ranker_save": (ctypes.c_int, [p, ctypes.c_char_p]),
+        "cm_ranker_load": (ctypes.c_int, [p, ctypes.c_char_p]),
         "cm_ranker_standardize": (ctypes.c_int, [p, p, p, i32, i32, u32]),
         "cm_ranker_loss_grad": (ctypes.c_int, [p, p, p, i32, p, p, i64, p, p, u32]),
         "cm_ranker_train": (ctypes.c_int, [p, p, p, i32, p, p, i64, i32, i32, ctypes.c_float,

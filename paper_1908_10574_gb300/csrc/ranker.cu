@@ -957,6 +957,45 @@ int cm_ranker_get_params(cm_ctx* c, float* params, int64_t n)
     return CM_OK;
 }
 
+// file layout: tag, parameter count, parameters (all little-endian, as the host stores them:
+// the supported hosts, x86-64 and Arm64, are little-endian)
+static const char kRankerTag[8] = {'C', 'M', 'R', 'A', 'N', 'K', '0', '1'};
+
+int cm_ranker_save(cm_ctx* c, const char* path)
+{
+    if (!c) return CM_ERR_ARG;
+    if (!path) return fail(c, CM_ERR_ARG, "null path");
+    std::vector<float> h((size_t)kNumParams);
+    int r = cm_ranker_get_params(c, h.data(), kNumParams);
+    if (r) return r;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(c, CM_ERR_ARG, std::string("cannot write ") + path);
+    const int64_t n = kNumParams;
+    const bool ok = std::fwrite(kRankerTag, 1, 8, f) == 8 && std::fwrite(&n, 8, 1, f) == 1 &&
+                    std::fwrite(h.data(), 4, h.size(), f) == h.size();
+    if (std::fclose(f) != 0 || !ok) return fail(c, CM_ERR_ARG, std::string("write failed: ") + path);
+    return CM_OK;
+}
+
+int cm_ranker_load(cm_ctx* c, const char* path)
+{
+    if (!c) return CM_ERR_ARG;
+    if (!path) return fail(c, CM_ERR_ARG, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, CM_ERR_ARG, std::string("cannot read ") + path);
+    char tag[8];
+    int64_t n = 0;
+    std::vector<float> h((size_t)kNumParams);
+    bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, kRankerTag, 8) == 0 &&
+              std::fread(&n, 8, 1, f) == 1 && n == kNumParams &&
+              std::fread(h.data(), 4, h.size(), f) == h.size();
+    char extra;
+    ok = ok && std::fread(&extra, 1, 1, f) == 0;      // nothing after the parameters
+    std::fclose(f);
+    if (!ok) return fail(c, CM_ERR_ARG, std::string("not a ranker parameter file: ") + path);
+    return cm_ranker_set_params(c, h.data(), kNumParams);
+}
+
 int cm_ranker_loss_grad(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
                         const int32_t* pairs, const float* labels, int64_t n_pairs,
                         float* loss, float* grad, uint32_t flags)

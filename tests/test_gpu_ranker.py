@@ -244,3 +244,27 @@ def test_selection_kernel_keeps_the_pairs_above_threshold(ctx):
     truth, _ = oracle.all_pairs(ss.seqs, ss.offsets, synth.BLOSUM62, 11, 1, T=100)
     tset = {(int(i), int(j)) for i, j, _ in truth}
     assert all((int(i), int(j)) in tset for i, j, _ in res["pairs"])
+
+
+def test_save_and_load_parameters(ctx, tmp_path):
+    """Parameters written by ranker_save come back bit for bit, logits included; a file with a
+    wrong tag or size is refused without touching the loaded parameters."""
+    ss = _set()
+    ctx.ranker_init(31)
+    ctx.ranker_standardize(ss.seqs, ss.offsets, max_sample=64)
+    p0 = ctx.ranker_get_params()
+    pairs = np.array([[0, 1], [2, 3], [4, 5]], dtype=np.int32)
+    z0 = ctx.ranker_logits(ss.seqs, ss.offsets, pairs)
+    path = tmp_path / "ranker.bin"
+    ctx.ranker_save(path)
+    assert path.stat().st_size == 16 + 4 * ctx.ranker_num_params()
+    ctx.ranker_init(32)
+    assert not np.array_equal(ctx.ranker_get_params(), p0)
+    ctx.ranker_load(path)
+    assert np.array_equal(ctx.ranker_get_params(), p0)
+    assert np.array_equal(ctx.ranker_logits(ss.seqs, ss.offsets, pairs), z0)
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(path.read_bytes()[:-4])
+    with pytest.raises(cm.CMError):
+        ctx.ranker_load(bad)
+    assert np.array_equal(ctx.ranker_get_params(), p0)
