@@ -30,8 +30,8 @@ struct cm_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
     cm_stats stats{};
-    int W = 8;
-    int rows_per_warp = 16384;
+    int W = 16;                             // the autotuner's usual choice on GB300
+    int rows_per_warp = 8192;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t aux = nullptr;             // second stream: alternate length bins overlap tails
     cudaEvent_t fork = nullptr, join = nullptr;
