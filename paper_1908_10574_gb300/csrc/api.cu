@@ -804,6 +804,7 @@ int sw_score_batch(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32
                    int32_t gap_open, int32_t gap_extend, int32_t* scores_out, uint32_t flags)
 {
     if (!c) return CM_ERR_ARG;
+    NvtxRange range("sw_score_batch");
     CUDA_TRY(cudaSetDevice(c->device));
     if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !scores_out)))
         return fail(c, CM_ERR_ARG, "bad pairs / scores_out");
@@ -1014,6 +1015,7 @@ int sw_allpairs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t 
                 int64_t capacity, int64_t* n_found, uint32_t flags)
 {
     if (!c) return CM_ERR_ARG;
+    NvtxRange range("sw_allpairs");
     CUDA_TRY(cudaSetDevice(c->device));
     if (!n_found || n_parts < 1 || part < 0 || part >= n_parts || capacity < 0 ||
         (capacity > 0 && (!pairs_out || !scores_out)))

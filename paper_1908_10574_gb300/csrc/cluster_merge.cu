@@ -101,6 +101,9 @@ struct Driver {
 int Driver::run_round(const std::vector<Merge>& ms)
 {
     const size_t nm = ms.size();
+    char label[64];
+    std::snprintf(label, sizeof(label), "cm round %lld (%zu merges)", (long long)rounds, nm);
+    NvtxRange range(label);
     // ---- wave 1: rep x rep scores.  Every merge's full cross product is one CROSS block
     // (queries = cs1 reps by length).  With the ranker, merges whose cross product has at
     // least ranker_min_pairs pairs align only the pairs whose ranker logit reaches
@@ -475,6 +478,7 @@ int Driver::score_ranked(const std::vector<Merge>& ms, const std::vector<char>& 
                          const uint32_t* d_bits, const int32_t* d_reps,
                          std::vector<std::vector<SigPair>>& sigm)
 {
+    NvtxRange range("cm ranked rep wave");
     constexpr int64_t kRankedChunkRows = (int64_t)8 << 30;
     struct LMeta { int32_t m, a, b, op; int64_t count; };
     std::vector<KeptList> lists;
@@ -618,6 +622,7 @@ int Driver::score_ranked(const std::vector<Merge>& ms, const std::vector<char>& 
 
 int Driver::finish(std::vector<int32_t>& final_set, cm_result* res)
 {
+    NvtxRange range("cm intra-cluster pairs");
     // intra-cluster all-against-all: one TRI block per cluster (members in length order)
     std::vector<int32_t> ids;
     std::vector<BlockReq> req;
@@ -721,6 +726,7 @@ int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_
                   const cm_params* params, cm_result** out, uint32_t flags)
 {
     if (!c) return CM_ERR_ARG;
+    NvtxRange range("cluster_merge");
     if (!out || !params) return fail(c, CM_ERR_ARG, "null params / out");
     *out = nullptr;
     CUDA_TRY(cudaSetDevice(c->device));

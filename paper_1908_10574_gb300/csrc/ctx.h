@@ -3,8 +3,11 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdio>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "cm_internal.h"
 
@@ -44,6 +47,14 @@ struct cm_ctx {
 namespace cm {
 
 int fail(cm_ctx* c, int code, const std::string& msg);
+
+// NVTX range for the lifetime of a scope (a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // resident CTAs per SM of the int16x2 kernel (W, R, mode), queried once per context
 inline int sw16_occupancy(cm_ctx* c, int R, int W, int mode)
