@@ -12,7 +12,16 @@ sequences go host->device and the significant pairs device->host inside every st
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank scores its own parts (weak scaling, no collective on the
-data path); rank 0 prints one JSON line.
+data path); rank 0 prints one JSON line.  `--impl reference` times the CPU oracle (scalar int64
+Gotoh on the host cores) on a bounded sample of the same workload.  The roofline object reports
+the SW kernel against the derived DPX-pipe peak at the sampled SM clock, and its DRAM traffic
+per launch from an ncu capture scaled by cells.
+
+ClusterMerge experiments (`--workload cm`): plain merge of a proteome-shaped set
+(`--cm-seqs`, default 100,000; `--long-tail K` adds K long tandem repeats); `--ranker
+[--transductive]` trains the learned ranker and runs the ranked merge too; `--recall` scores the
+GPU all-against-all for recall; `--ranker-untrained Q` runs the ranked path with untrained
+weights (profiling).
 """
 from __future__ import annotations
 
