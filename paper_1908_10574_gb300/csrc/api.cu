@@ -383,7 +383,10 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
             CUDA_TRY(launch_sw32(16, grid, a, d_pref + nlong, n - nlong, d_flags + 3, st));
             c->stats.launches += 1;
         }
-        if (round > 64) return fail(c, CM_ERR_INTERNAL, "int32 rerun did not converge");
+        // every full round rescored `cap` distinct slots (a rescored slot no longer holds the
+        // saturation mark), so more rounds than slots / cap means no progress
+        if ((int64_t)round * cap > plan.nslots)
+            return fail(c, CM_ERR_INTERNAL, "int32 rerun did not converge");
     }
     int32_t kerr = 0;
     CUDA_TRY(cudaMemcpyAsync(&kerr, d_flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

@@ -345,7 +345,12 @@ int Driver::run_round(const std::vector<Merge>& ms)
     }
     std::vector<std::vector<int32_t>> snap(involved.size());
     for (size_t i = 0; i < involved.size(); ++i) snap[i] = arena[involved[i]].objs;
-    for (int wave = 0;; ++wave) {
+    // A wave resolves at least the first event of each merge that still misses a score (the
+    // state before that event is already exact), so a merge needs at most its event count
+    // plus one waves; more than that means no progress.
+    size_t max_events = 0;
+    for (size_t m = 0; m < nm; ++m) max_events = std::max(max_events, events[m].size());
+    for (int64_t wave = 0;; ++wave) {
         if (wave > 0) {
             for (size_t i = 0; i < involved.size(); ++i) {
                 Cluster& cl = arena[involved[i]];
@@ -458,7 +463,8 @@ int Driver::run_round(const std::vector<Merge>& ms)
             for (int64_t s = 0; s < ereq[b].b_count; ++s)
                 memo[key2(eids[ereq[b].b_begin + s], rp)] = ES[ebase[b] + s];
         }
-        if (wave > 4096) return fail(c, CM_ERR_INTERNAL, "exchange replay did not converge");
+        if (wave > (int64_t)max_events)
+            return fail(c, CM_ERR_INTERNAL, "exchange replay did not converge");
     }
     for (size_t m = 0; m < nm; ++m) sets[ms[m].out] = std::move(out_sets[m]);
     merges += (int64_t)nm;
