@@ -78,6 +78,13 @@ int cm_set_stream(cm_ctx *ctx, void *cuda_stream);
  * warp stream (256 .. 65536).  0 keeps the current value.  The autotuner sets these. */
 int cm_set_tuning(cm_ctx *ctx, int32_t warps_per_cta, int32_t rows_per_warp);
 
+/* Upper bound on the pair slots (4 bytes of device memory each, plus the subjects' row
+ * streams) of one device batch of ClusterMerge's representative wave (Algorithm 2 rounds,
+ * Sec. 5's merges of large sets).  A round whose rep x rep cross products exceed it runs as
+ * several batches, cut between query rows, with the same results.  max_slots >= 1024;
+ * 0 restores the default of 2^32. */
+int cm_set_batch_limit(cm_ctx *ctx, int64_t max_slots);
+
 /* Autotuner: scores the all-against-all of a length-stratified sample of `sample_seqs` of the
  * given sequences (0 = 3000) under every CTA width (4, 8, 16 warps) and warp-stream length
  * (4096 .. 32768 rows), keeps the fastest (CUDA-event time of the int16x2 kernel per cell) as

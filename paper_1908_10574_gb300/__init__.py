@@ -119,6 +119,10 @@ class Context:
     def set_tuning(self, warps_per_cta=0, rows_per_warp=0):
         _L.check(self._h, _L.lib().cm_set_tuning(self._h, int(warps_per_cta), int(rows_per_warp)))
 
+    def set_batch_limit(self, max_slots=0):
+        """Pair slots of one device batch of ClusterMerge's representative wave (0: default)."""
+        _L.check(self._h, _L.lib().cm_set_batch_limit(self._h, int(max_slots)))
+
     # ---- entry points ---------------------------------------------------------------------
     def sw_score_batch(self, seqs, offsets, pairs, matrix, gap_open, gap_extend, flags=0,
                        out=None):

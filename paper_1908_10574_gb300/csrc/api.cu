@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "batches.h"
 #include "ctx.h"
 
 namespace cm {
@@ -504,17 +505,56 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
 int score_blocks_sig(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
                      const std::vector<BlockReq>& req, int32_t T,
                      std::vector<std::pair<int64_t, int32_t>>& sig, std::vector<int64_t>& base,
-                     uint32_t flags)
+                     uint32_t flags, int64_t* n_batches)
 {
-    Plan plan;
-    const int64_t slots = plan_blocks(c, P, ids, req, plan, base);
+    if (n_batches) *n_batches = 1;
+    std::vector<BlockShape> shape(req.size());
+    int64_t total = 0;
+    for (size_t b = 0; b < req.size(); ++b) {
+        shape[b] = {req[b].kind == kTri, req[b].a_count, req[b].b_count};
+        total += block_slots(shape[b]);
+    }
     sig.clear();
-    if (slots == 0) return CM_OK;
-    int32_t* out;
-    ENSURE(B_OUT, slots, out);
-    int r = run_plan(c, P, plan, out, nullptr, flags);
-    if (r) return r;
-    return compact_sig(c, out, slots, T, sig);
+    if (total <= c->max_batch_slots) {          // one device batch
+        Plan plan;
+        const int64_t slots = plan_blocks(c, P, ids, req, plan, base);
+        if (slots == 0) return CM_OK;
+        int32_t* out;
+        ENSURE(B_OUT, slots, out);
+        int r = run_plan(c, P, plan, out, nullptr, flags);
+        if (r) return r;
+        return compact_sig(c, out, slots, T, sig);
+    }
+    // Several batches, cut between query rows: each batch's significant slots are mapped back
+    // to the slot numbering of the whole list, so the caller sees one batch's result.
+    base.assign(req.size() + 1, 0);
+    for (size_t b = 0; b < req.size(); ++b) base[b + 1] = base[b] + block_slots(shape[b]);
+    const std::vector<std::vector<BlockPiece>> batches = split_batches(shape, c->max_batch_slots);
+    if (n_batches) *n_batches = (int64_t)batches.size();
+    for (const std::vector<BlockPiece>& batch : batches) {
+        std::vector<BlockReq> sub;
+        sub.reserve(batch.size());
+        for (const BlockPiece& pc : batch) {
+            BlockReq q = req[pc.block];
+            if (q.kind != kTri) {
+                q.a_begin += pc.row0;
+                q.a_count = pc.rows;
+            }
+            sub.push_back(q);
+        }
+        Plan plan;
+        std::vector<int64_t> sbase;
+        const int64_t slots = plan_blocks(c, P, ids, sub, plan, sbase);
+        if (slots == 0) continue;
+        int32_t* out;
+        ENSURE(B_OUT, slots, out);
+        int r = run_plan(c, P, plan, out, nullptr, flags);
+        if (r) return r;
+        std::vector<std::pair<int64_t, int32_t>> part;
+        if ((r = compact_sig(c, out, slots, T, part))) return r;
+        append_batch_slots(batch, sbase, part, sig);
+    }
+    return CM_OK;
 }
 
 int compact_sig(cm_ctx* c, const int32_t* out, int64_t slots, int32_t T,
@@ -785,6 +825,15 @@ int cm_set_tuning(cm_ctx* c, int32_t warps, int32_t rows)
         return fail(c, CM_ERR_ARG, "rows_per_warp must be in [256, 65536]");
     if (warps) c->W = warps;
     if (rows) c->rows_per_warp = rows;
+    return CM_OK;
+}
+
+int cm_set_batch_limit(cm_ctx* c, int64_t max_slots)
+{
+    if (!c) return CM_ERR_ARG;
+    if (max_slots != 0 && max_slots < 1024)
+        return fail(c, CM_ERR_ARG, "max_slots must be 0 or >= 1024");
+    c->max_batch_slots = max_slots ? max_slots : ((int64_t)1 << 32);
     return CM_OK;
 }
 

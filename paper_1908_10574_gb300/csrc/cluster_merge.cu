@@ -213,8 +213,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
     std::vector<std::pair<int64_t, int32_t>> sig;
     std::vector<std::vector<SigPair>> sigm(nm);       // per merge: (i1, i2, s), s > T
     if (!req.empty()) {
-        r = score_blocks_sig(c, P, ids, req, prm.T, sig, base, flags);
+        int64_t dev_batches = 1;
+        r = score_blocks_sig(c, P, ids, req, prm.T, sig, base, flags, &dev_batches);
         if (r) return r;
+        batches += std::max<int64_t>(dev_batches - 1, 0);   // the wave counts one below
         scored += base.empty() ? 0 : base.back();
         size_t bi = 0;
         for (const auto& e : sig) {

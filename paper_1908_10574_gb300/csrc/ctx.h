@@ -35,6 +35,7 @@ struct cm_ctx {
     cm_stats stats{};
     int W = 16;                             // the autotuner's usual choice on GB300
     int rows_per_warp = 8192;
+    int64_t max_batch_slots = (int64_t)1 << 32;   // slots of one rep-wave device batch
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t aux = nullptr;             // second stream: alternate length bins overlap tails
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -178,11 +179,13 @@ int score_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
                  std::vector<int64_t>& base, uint32_t flags);
 
 // As score_blocks, but only the slots whose score exceeds T come back: (slot, score) in slot
-// order, compacted on the device (the full score array never leaves it).
+// order, compacted on the device (the full score array never leaves it).  Lists of more than
+// the context's max_batch_slots slots run as several device batches cut between query rows
+// (same result); *n_batches (may be null) receives the number of batches.
 int score_blocks_sig(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& ids,
                      const std::vector<BlockReq>& req, int32_t T,
                      std::vector<std::pair<int64_t, int32_t>>& sig, std::vector<int64_t>& base,
-                     uint32_t flags);
+                     uint32_t flags, int64_t* n_batches = nullptr);
 
 // (slot, score) of the device slots [0, nslots) of `out` whose score exceeds T, slot order.
 int compact_sig(cm_ctx* c, const int32_t* out, int64_t nslots, int32_t T,

@@ -1,0 +1,65 @@
+"""GPU ClusterMerge with the representative wave cut into small device batches
+(cm_set_batch_limit): rounds whose rep x rep cross products exceed the limit run as several
+batches cut between query rows, and clusters, similar pairs and comparison counts must still
+equal those of the oracle's sequential Algorithms 1 and 2 exactly.  (A 1M-protein proteome's
+top merges exceed device memory as one batch; the limit here is set low so that small inputs
+take the same path.)"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1908_10574_gb300 as cm
+from paper_1908_10574_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+S62 = synth.BLOSUM62
+
+
+def _oracle_cm(ss, T, mT, mU):
+    _, scores = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=T)
+    n = len(ss)
+    M = np.zeros((n, n), np.int64)
+    M[np.triu_indices(n, 1)] = scores
+    M = M + M.T
+    return oracle.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T=T, mT=mT, mU=mU,
+                                score_matrix=M)
+
+
+def _check(got, want):
+    assert got["clusters"] == want["clusters"]
+    assert got["pairs"].tolist() == want["pairs"].tolist()
+    st, ws = got["stats"], want["stats"]
+    assert st["rep_comparisons"] == ws["rep"]
+    assert st["exchange_comparisons"] == ws["exchange"]
+    assert st["intra_comparisons"] == ws["intra"]
+    assert st["full_merges"] == ws["full_merges"]
+    assert st["exchanges"] == ws["exchanges"]
+    assert st["merges"] == ws["merges"]
+
+
+@pytest.fixture(scope="module")
+def case():
+    full = synth.proteome(5000, family_size=8, singleton_frac=0.2, stream=7)
+    ss = full.subset(np.arange(600))
+    return ss, _oracle_cm(ss, 100, 138, 15)
+
+
+@pytest.mark.parametrize("limit", [1024, 5000])
+def test_batched_rep_wave_matches_oracle(case, limit):
+    ss, want = case
+    ctx = cm.Context(0)
+    one = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 100, 138, 15)
+    _check(one, want)
+    ctx.set_batch_limit(limit)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 100, 138, 15)
+    _check(got, want)
+    # the larger rounds' cross products exceed the limit and ran as several device batches
+    assert got["stats"]["gpu_batches"] > one["stats"]["gpu_batches"]
+    assert got["stats"]["comparisons_scored"] == one["stats"]["comparisons_scored"]
+
+
+def test_batch_limit_argument_checks():
+    ctx = cm.Context(0)
+    with pytest.raises(cm.CMError):
+        ctx.set_batch_limit(1000)
+    ctx.set_batch_limit(0)
