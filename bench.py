@@ -18,10 +18,15 @@ the SW kernel against the derived DPX-pipe peak at the sampled SM clock, and its
 per launch from an ncu capture scaled by cells.
 
 ClusterMerge experiments (`--workload cm`): plain merge of a proteome-shaped set
-(`--cm-seqs`, default 100,000; `--long-tail K` adds K long tandem repeats); `--ranker
-[--transductive]` trains the learned ranker and runs the ranked merge too; `--recall` scores the
-GPU all-against-all for recall; `--ranker-untrained Q` runs the ranked path with untrained
-weights (profiling).
+(`--cm-seqs`, default 100,000; `--family-size`, `--singleton-frac`; `--long-tail K` adds K long
+tandem repeats); `--ranker [--transductive]` trains the learned ranker and runs the ranked merge
+too; `--recall` scores the GPU all-against-all for recall (`--recall-sample F`: of a random
+fraction F of the proteins only); `--recall-families` adds recall over every within-family pair
+with s > T; `--batch-slots` bounds one device batch of the rep wave; `--ranker-untrained Q` runs
+the ranked path with untrained weights (profiling).  The 1M-protein long-tail configuration:
+
+  python bench.py --workload cm --cm-seqs 1000000 --family-size 10 --singleton-frac 0 \
+      --long-tail 1000 --recall --recall-sample 0.01 --recall-families [--ranker --transductive]
 """
 from __future__ import annotations
 
@@ -232,16 +237,61 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def subset_recall(found, subset, truth_sub):
+    """Recall of similar pairs restricted to a sequence subset: `found` holds the (i, j) global
+    ids of the pairs a merge reported, `subset` the sorted global ids of the sample and
+    `truth_sub` the all-against-all similar pairs of the sample in sample numbering.  Returns
+    (recall, truth pairs, found pairs inside the sample)."""
+    subset = np.asarray(subset, dtype=np.int64)
+    found = np.asarray(found, dtype=np.int64).reshape(-1, 2)
+    a = np.searchsorted(subset, found[:, 0])
+    b = np.searchsorted(subset, found[:, 1])
+    a_in = (a < len(subset)) & (subset[np.minimum(a, len(subset) - 1)] == found[:, 0])
+    b_in = (b < len(subset)) & (subset[np.minimum(b, len(subset) - 1)] == found[:, 1])
+    keep = a_in & b_in
+    fs = set(zip(np.minimum(a, b)[keep].tolist(), np.maximum(a, b)[keep].tolist()))
+    t = np.asarray(truth_sub, dtype=np.int64).reshape(-1, 2)
+    ts = set(zip(t.min(axis=1).tolist(), t.max(axis=1).tolist()))
+    return len(fs & ts) / max(len(ts), 1), len(ts), len(fs)
+
+
+def family_pairs(family):
+    """Every (i, j), i < j, of two proteins with the same planted family label."""
+    family = np.asarray(family)
+    order = np.argsort(family, kind="stable")
+    bounds = np.flatnonzero(np.diff(family[order])) + 1
+    out = []
+    for g in np.split(order, bounds):
+        if len(g) > 1:
+            g = np.sort(g)
+            i, j = np.triu_indices(len(g), 1)
+            out.append(np.stack([g[i], g[j]], axis=1))
+    return np.concatenate(out).astype(np.int32) if out else np.zeros((0, 2), np.int32)
+
+
+def stratum_recall(found, truth, n):
+    """Fraction of the pairs of `truth` (any order within a pair) that `found` contains."""
+    def keys(p):
+        p = np.asarray(p, dtype=np.int64).reshape(-1, 2)
+        return p.min(axis=1) * n + p.max(axis=1)
+    t = keys(truth)
+    return float(np.isin(t, keys(found)).mean()) if len(t) else 1.0
+
+
 def run_cluster_merge(args):
-    """ClusterMerge end to end on the 100k proteome set (80,000 proteins in 10,000 families of
-    8 plus 20,000 singletons); recall against the GPU all-against-all when --recall."""
+    """ClusterMerge end to end on a proteome-shaped set (default: 100,000 proteins, 80,000 in
+    10,000 families of 8 plus 20,000 singletons); recall against the GPU all-against-all when
+    --recall, of the whole set or (--recall-sample F) of a random fraction F of its proteins."""
     import torch
     import paper_1908_10574_gb300 as cm
-    ss = synth.proteome(args.cm_seqs, family_size=8, singleton_frac=0.2, stream=3)
+    ss = synth.proteome(args.cm_seqs, family_size=args.family_size,
+                        singleton_frac=args.singleton_frac, stream=3)
     if args.long_tail:
         ss = synth.long_tail(ss, args.long_tail, args.long_motifs)
     n = len(ss)
     ctx = cm.Context(0)
+    if args.batch_slots:
+        ctx.set_batch_limit(args.batch_slots)
     T, mT, mU = T_SIG, M_T, M_U
     ranker = None
     if args.ranker:
@@ -271,13 +321,36 @@ def run_cluster_merge(args):
     out = {"metric": "ClusterMerge seconds", "value": dt, "unit": "s", "n_gpus": 1,
            "higher_is_better": False, "data": "synthetic", "dtype": "int16",
            "config": {"workload": "ClusterMerge of %d synthetic proteins (lognormal lengths, "
-                                  "families of 8 + 20%% singletons%s), BLOSUM62 11/1, T=%d, mT=%d, "
-                                  "mU=%d" % (n, (", + %d tandem repeats of 10,000-35,000 residues in "
-                                                 "%d motif families" % (args.long_tail, args.long_motifs))
+                                  "families of %d + %d%% singletons%s), BLOSUM62 11/1, T=%d, mT=%d, "
+                                  "mU=%d" % (n, args.family_size, round(100 * args.singleton_frac),
+                                             (", + %d tandem repeats of 10,000-35,000 residues in "
+                                              "%d motif families" % (args.long_tail, args.long_motifs))
                                              if args.long_tail else "", T, mT, mU)},
            "clusters": len(res["clusters"]), "similar_pairs": len(res["pairs"]),
            "stats": res["stats"], "ranker": ranker}
-    if args.recall:
+    if args.recall and args.recall_sample > 0:
+        # the all-against-all of a random sample of the proteins (a 1M set's whole
+        # all-against-all is ~9e16 cells); recall counts the sample's pairs only
+        t1 = time.perf_counter()
+        rng = np.random.default_rng(1908)
+        m = max(2, int(round(args.recall_sample * n)))
+        subset = np.sort(rng.choice(n, size=m, replace=False))
+        sub = ss.subset(subset)
+        tp = []
+        parts = max(1, int(total_cells(sub) / 2e12))
+        for part in range(parts):
+            p, s = ctx.sw_allpairs(sub.seqs, sub.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T,
+                                   part, parts, capacity=1 << 22)
+            tp.append(p.astype(np.int64))
+        truth_sub = np.concatenate(tp) if tp else np.zeros((0, 2), np.int64)
+        r, nt, nf = subset_recall(res["pairs"][:, :2], subset, truth_sub)
+        out["all_pairs_seconds"] = time.perf_counter() - t1
+        out["recall_sample"] = {"fraction": args.recall_sample, "proteins": m,
+                                "truth_pairs": nt, "found_pairs": nf}
+        out["recall"] = r
+        if ranked is not None:
+            ranker["recall"] = subset_recall(ranked["pairs"][:, :2], subset, truth_sub)[0]
+    elif args.recall:
         t1 = time.perf_counter()
         truth = set()
         parts = max(1, int(total_cells(ss) / 2e12))
@@ -292,9 +365,22 @@ def run_cluster_merge(args):
         if ranked is not None:
             fr = set(zip(ranked["pairs"][:, 0].tolist(), ranked["pairs"][:, 1].tolist()))
             ranker["recall"] = len(fr & truth) / max(len(truth), 1)
-        out["comparisons_fraction"] = (res["stats"]["rep_comparisons"] +
-                                       res["stats"]["exchange_comparisons"] +
-                                       res["stats"]["intra_comparisons"]) / (n * (n - 1) / 2)
+    if args.recall_families:
+        # recall over the planted homologs: every within-family pair scored exactly, those
+        # with s > T the truth of this stratum (millions of pairs at 1M proteins)
+        t1 = time.perf_counter()
+        fp = family_pairs(ss.family)
+        sc = ctx.sw_score_batch(ss.seqs, ss.offsets, fp, synth.BLOSUM62, GAP_OPEN, GAP_EXT)
+        truth_f = fp[sc > T]
+        out["family_recall"] = {"within_family_pairs": int(len(fp)),
+                                "similar": int(len(truth_f)),
+                                "recall": stratum_recall(res["pairs"][:, :2], truth_f, n),
+                                "seconds": time.perf_counter() - t1}
+        if ranked is not None:
+            ranker["family_recall"] = stratum_recall(ranked["pairs"][:, :2], truth_f, n)
+    out["comparisons_fraction"] = (res["stats"]["rep_comparisons"] +
+                                   res["stats"]["exchange_comparisons"] +
+                                   res["stats"]["intra_comparisons"]) / max(n * (n - 1) / 2, 1)
     print(json.dumps(out), flush=True)
 
 
@@ -352,6 +438,16 @@ def main():
                     help="allpairs: SW GCUPS (default); cm: ClusterMerge seconds")
     ap.add_argument("--cm-seqs", type=int, default=100000)
     ap.add_argument("--recall", action="store_true")
+    ap.add_argument("--recall-sample", type=float, default=0.0, metavar="F",
+                    help="cm: measure recall on the all-against-all of a random fraction F of "
+                         "the proteins (0: the whole set)")
+    ap.add_argument("--recall-families", action="store_true",
+                    help="cm: recall over every within-family pair with s > T (planted homologs)")
+    ap.add_argument("--family-size", type=int, default=8, help="cm: proteins per family")
+    ap.add_argument("--singleton-frac", type=float, default=0.2,
+                    help="cm: fraction of proteins outside any family")
+    ap.add_argument("--batch-slots", type=int, default=0,
+                    help="cm: pair slots of one device batch of the rep wave (0: library default)")
     ap.add_argument("--long-tail", type=int, default=0,
                     help="cm: add this many long tandem repeats (the long-tail workload)")
     ap.add_argument("--long-motifs", type=int, default=10)
