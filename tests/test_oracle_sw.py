@@ -108,6 +108,34 @@ def test_self_score_closed_form():
         assert oracle.sw_score(a, a, S62, 11, 1) == int(d[a].sum())
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_runs_split_by_a_gap_closed_form(mode):
+    """a = x^n against b = x^p y^k x^q (n = p + q, S(x,y) < 0).  An alignment either stays
+    inside one run of b (best S(x,x) max(p,q)) or crosses the y block; a crossing alignment
+    that gaps g of the k y's (one gap: a second would only add an opening) pairs the other
+    k - g with x's of a, so it has n - (k - g) x-x columns, k - g x-y columns and one gap of
+    g, and every other crossing alignment drops positive x-x columns.  So the score is the
+    largest of those counts' totals."""
+    rng = np.random.default_rng(12 + mode)
+    for _ in range(150):
+        x = int(rng.integers(0, 20))
+        ys = [y for y in range(20) if S62[x, y] < 0]
+        y = int(rng.choice(ys))
+        p, q, k = int(rng.integers(0, 13)), int(rng.integers(0, 13)), int(rng.integers(1, 9))
+        o, e = [(11, 1), (5, 2), (3, 3), (1, 0), (20, 1)][int(rng.integers(0, 5))]
+        n = p + q
+        a = np.full(n, x, np.uint8)
+        b = np.concatenate([np.full(p, x), np.full(k, y), np.full(q, x)]).astype(np.uint8)
+
+        def gap(g):
+            return 0 if g == 0 else (o + (g - 1) * e if mode == 0 else o + g * e)
+        sxx, sxy = int(S62[x, x]), int(S62[x, y])
+        cands = [sxx * max(p, q)]
+        cands += [sxx * (n - k + g) + sxy * (k - g) - gap(g) for g in range(k + 1) if k - g <= n]
+        assert oracle.sw_score(a, b, S62, o, e, mode) == max(cands), (x, y, p, q, k, o, e)
+        assert oracle.sw_score(b, a, S62, o, e, mode) == max(cands)
+
+
 def test_huge_gaps_reduce_to_best_ungapped_segment():
     rng = np.random.default_rng(4)
     for _ in range(40):
