@@ -158,93 +158,6 @@ int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t
     return CM_OK;
 }
 
-// ---- planning ---------------------------------------------------------------------------
-void choose_R(int64_t m, int* R, int* npass)
-{
-    if (m <= 0) { *R = 1; *npass = 1; return; }
-    const int np = (int)((m + 1023) / 1024);
-    const int64_t per = (m + np - 1) / np;
-    int r = (int)((per + 31) / 32);              // register tiles of 1..32 columns per lane
-    r = std::max(1, std::min(32, r));
-    *R = r;
-    *npass = np;
-}
-
-// Cut the subjects [0, ns) of one query pair into CTA tasks of about `target` rows per stream
-// and pick the kernel mode.  A query without a partner runs in a single-query mode (two
-// subject streams per 32-lane warp, or four over two 16-lane segments); a pair runs over 32
-// lanes or, when its longer query fits 16 lanes x 32 columns, in the 16-lane segment mode
-// (R per lane twice that of a 32-lane tile, 16-column granularity).  A task holds `target`
-// rows per stream of its warps, divided by the query's column passes.
-void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
-               const int64_t* srow, int64_t target, int64_t rows_total)
-{
-    int R, np;
-    choose_R(m_hi, &R, &np);
-    int mode = hi_valid ? kModePair : kModeTwo;
-    int seg = 32;
-    if (m_hi <= (hi_valid ? kSeg16MaxCols : kTwo16MaxCols)) {   // (32-lane kernels: wider R only)
-        mode = hi_valid ? kModeSeg16 : kModeTwo16;
-        seg = 16;
-        R = (int)std::max<int64_t>(1, (m_hi + 15) / 16);
-        np = 1;
-    } else if (!hi_valid) {
-        // single query over 32 lanes: column passes of at most 16 columns per lane, where the
-        // two-stream step still fits two rows into the register budget
-        np = (int)((m_hi + kTwoPassCols - 1) / kTwoPassCols);
-        const int64_t per = (m_hi + np - 1) / np;
-        R = (int)((per + 31) / 32);
-    }
-    const int spw = mode == kModePair ? 1 : mode == kModeTwo16 ? 4 : 2;   // streams per warp
-    const bool single = mode == kModeTwo || mode == kModeTwo16;
-    // a task streams its rows once per column pass: size it by work (rows x passes), so that
-    // the tasks of long queries stay as long as everyone else's
-    target = std::max<int64_t>(target * spw / np, 2048);
-    const int64_t ntask = srow ? 0 : std::max<int64_t>(1, (rows_total + target - 1) / target);
-    const int64_t per = srow ? 0 : (ns + ntask - 1) / ntask;
-    int32_t s = 0;
-    while (s < ns) {
-        int32_t e;
-        if (srow) {
-            const int64_t want = srow[s] + target;
-            e = (int32_t)(std::lower_bound(srow + s + 1, srow + ns + 1, want) - srow);
-        } else {
-            e = (int32_t)std::min<int64_t>(ns, s + per);
-        }
-        if (e > ns) e = ns;
-        SwTask t{};
-        t.block = block;
-        t.k = k;
-        t.s0 = s;
-        t.s1 = e;
-        t.npass = np;
-        t.hi_valid = hi_valid ? 1 : 0;
-        t.mode = mode;
-        const int64_t rows = srow ? srow[e] - srow[s] : rows_total * (e - s) / std::max(ns, 1);
-        P.cells_padded += rows * seg * R * np * (single ? 1 : 2);
-        P.tasks.push_back(t);
-        P.task_R.push_back(R * 4 + mode);         // launch bin: register tile and mode
-        P.keys.push_back({rows * R * np / spw, R * 4 + mode});
-        s = e;
-    }
-}
-
-void order_tasks(Plan& P)
-{
-    const auto& keys = P.keys;
-    std::vector<size_t> idx(P.tasks.size());
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
-        if (keys[x].second != keys[y].second) return keys[x].second > keys[y].second;
-        return keys[x].first > keys[y].first;
-    });
-    std::vector<SwTask> t2(idx.size());
-    std::vector<int> r2(idx.size());
-    for (size_t i = 0; i < idx.size(); ++i) { t2[i] = P.tasks[idx[i]]; r2[i] = P.task_R[idx[i]]; }
-    P.tasks.swap(t2);
-    P.task_R.swap(r2);
-}
-
 // ---- execution --------------------------------------------------------------------------
 int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64_t* d_omap,
              uint32_t flags)

@@ -10,6 +10,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "cm_internal.h"
+#include "plan.h"
 
 namespace cm {
 
@@ -134,31 +135,6 @@ int ranker_select(cm_ctx* c, const void* U, const std::vector<int32_t>& rows,
                   const int32_t** d_rows_out = nullptr);
 int ranker_alpha_beta(cm_ctx* c, float* ab);
 
-struct Plan {
-    std::vector<SwBlock> blocks;
-    std::vector<int64_t> first_slot;     // per block, ascending
-    std::vector<int32_t> ids;            // A ids then B ids
-    std::vector<int64_t> srow;           // global row table over all B subjects (+1)
-    std::vector<SwTask> tasks;           // grouped by R, cost descending inside a group
-    std::vector<int> task_R;             // R per task (parallel to tasks)
-    std::vector<std::pair<int64_t, int>> keys;   // (cost, R) per task, for ordering
-    int64_t nslots = 0;
-    int64_t cells = 0, cells_padded = 0, pairs = 0;
-    int64_t max_warp_rows = 0;
-    // Device-built subject lists: `ids` holds the A ids only; the B ids (n_sub of them) and the
-    // row table (n_sub + 1 entries, total_rows rows) already sit in the B_IDS (after the A ids)
-    // and B_SROW buffers; `srow` stays empty.
-    bool dev_lists = false;
-    int64_t n_sub = 0, total_rows = 0;
-};
-
-void choose_R(int64_t m, int* R, int* npass);
-// Tasks of one query pair (k, k+1) or single query k against the block's subjects [0, ns).
-// With `srow` the tasks split at subject boundaries by rows; without it (device-built lists)
-// into equal subject counts, `rows_total` being the rows of all ns subjects.
-void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_valid, int64_t m_hi,
-               const int64_t* srow, int64_t target, int64_t rows_total = 0);
-void order_tasks(Plan& P);
 int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64_t* d_omap,
              uint32_t flags);
 
