@@ -609,19 +609,26 @@ int get_ranker(cm_ctx* c, Ranker** out)
     if (!c->ranker) {
         Ranker* K = new (std::nothrow) Ranker();
         if (!K) return fail(c, CM_ERR_OOM, "host allocation failed");
-        c->ranker = K;
-        c->ranker_free = ranker_free;
         const size_t nb = kNumParams * sizeof(float);
-        CUDA_TRY(cudaMalloc(&K->params, nb));
-        CUDA_TRY(cudaMalloc(&K->grad, nb));
-        CUDA_TRY(cudaMalloc(&K->m, nb));
-        CUDA_TRY(cudaMalloc(&K->v, nb));
-        CUDA_TRY(cudaMalloc(&K->E, 20 * kEmb * sizeof(bf16)));
         const size_t w1 = (size_t)kTaps * kEmb * kCh * sizeof(bf16);
         const size_t w2 = (size_t)kTaps * kCh * kCh * sizeof(bf16);
-        CUDA_TRY(cudaMalloc(&K->W1, w1)); CUDA_TRY(cudaMalloc(&K->W1T, w1));
-        CUDA_TRY(cudaMalloc(&K->W2, w2)); CUDA_TRY(cudaMalloc(&K->W2T, w2));
-        CUDA_TRY(cudaMalloc(&K->W3, w2)); CUDA_TRY(cudaMalloc(&K->W3T, w2));
+        const std::pair<void**, size_t> bufs[] = {
+            {(void**)&K->params, nb}, {(void**)&K->grad, nb}, {(void**)&K->m, nb},
+            {(void**)&K->v, nb}, {(void**)&K->E, 20 * kEmb * sizeof(bf16)},
+            {(void**)&K->W1, w1}, {(void**)&K->W1T, w1}, {(void**)&K->W2, w2},
+            {(void**)&K->W2T, w2}, {(void**)&K->W3, w2}, {(void**)&K->W3T, w2}};
+        cudaError_t e = cudaSuccess;
+        for (const auto& b : bufs)
+            if (e == cudaSuccess) e = cudaMalloc(b.first, b.second);
+        if (e != cudaSuccess) {
+            // no half-built ranker stays on the context: a later call starts over
+            cudaGetLastError();
+            ranker_free(K);
+            return fail(c, CM_ERR_OOM, std::string("device allocation of the ranker failed: ") +
+                                           cudaGetErrorString(e));
+        }
+        c->ranker = K;
+        c->ranker_free = ranker_free;
     }
     *out = static_cast<Ranker*>(c->ranker);
     return CM_OK;
