@@ -255,6 +255,12 @@ def subset_recall(found, subset, truth_sub):
     return len(fs & ts) / max(len(ts), 1), len(ts), len(fs)
 
 
+def progress(phase, info):
+    """One JSON line per finished phase of a long ClusterMerge run, on stderr (the result line
+    on stdout stays the only one there)."""
+    print(json.dumps({"phase": phase, **info}), file=sys.stderr, flush=True)
+
+
 def family_pairs(family):
     """Every (i, j), i < j, of two proteins with the same planted family label."""
     family = np.asarray(family)
@@ -297,6 +303,7 @@ def run_cluster_merge(args):
     if args.ranker:
         ranker = train_ranker(ctx, args.train_seqs, args.train_pairs, args.epochs, args.keep,
                               lr=args.lr, train_set=ss if args.transductive else None)
+        progress("ranker training", ranker)
     elif args.ranker_untrained is not None:
         # profiling the ranked path without training: standardised random weights, pruning at
         # a quantile of random-pair logits (the pruning is not meaningful, the work is)
@@ -307,6 +314,8 @@ def run_cluster_merge(args):
     t0 = time.perf_counter()
     res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT, mU)
     dt = time.perf_counter() - t0
+    progress("plain merge", {"seconds": dt, "clusters": len(res["clusters"]),
+                             "similar_pairs": len(res["pairs"]), "stats": res["stats"]})
     ranked = None
     if ranker is not None:
         t1 = time.perf_counter()
@@ -316,6 +325,8 @@ def run_cluster_merge(args):
         ranker["ranker_min_pairs"] = args.min_pairs
         ranker["cluster_merge_seconds"] = time.perf_counter() - t1
         ranker["stats"] = ranked["stats"]
+        progress("ranked merge", {"seconds": ranker["cluster_merge_seconds"],
+                                  "similar_pairs": len(ranked["pairs"]), "stats": ranked["stats"]})
         ranker["clusters"] = len(ranked["clusters"])
         ranker["similar_pairs"] = len(ranked["pairs"])
     out = {"metric": "ClusterMerge seconds", "value": dt, "unit": "s", "n_gpus": 1,
