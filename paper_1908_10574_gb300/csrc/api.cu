@@ -905,7 +905,7 @@ int cm_autotune(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t 
     while (bucket < 30 && ((int64_t)1 << bucket) < sl[sl.size() / 2]) ++bucket;
     cudaDeviceProp prop;
     CUDA_TRY(cudaGetDeviceProperties(&prop, c->device));
-    char key[256];
+    char key[sizeof(prop.name) + 32];          // name, SM count and bucket always fit
     std::snprintf(key, sizeof(key), "%s|%d|%d", prop.name, prop.multiProcessorCount, bucket);
     for (char* q = key; *q; ++q)
         if (*q == ' ') *q = '_';

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "mock_ranked.h"
 
 using namespace cm;
 
@@ -36,11 +37,8 @@ struct Instance {
 
 const Instance* g = nullptr;
 std::map<int, std::vector<char>> g_buf;             // mock device buffers by BufId
-std::vector<uint32_t> g_bits;                        // "device" selection bitmap
-std::vector<int32_t> g_rows;                         // "device" rows of the selection
 int g_dummy;
 
-int64_t rows_of(int64_t len) { return len <= 0 ? kRowGroup : (len + kRowGroup - 1) / kRowGroup * kRowGroup; }
 int64_t tri(int64_t k) { return k * (k - 1) / 2; }
 
 int32_t pair_score(int32_t x, int32_t y, int32_t swap)
@@ -67,14 +65,6 @@ void all_scores(const std::vector<int32_t>& ids, const std::vector<BlockReq>& re
         }
         base[b + 1] = (int64_t)scores.size();
     }
-}
-
-uint32_t kept_word(const KeptList& L, const uint32_t* bits, int64_t w)
-{
-    const uint32_t a = bits[L.row_a + w];
-    if (L.op == kKeepA) return a;
-    const uint32_t b = bits[L.row_b + w];
-    return L.op == kKeepAnd ? (a & b) : L.op == kKeepAOnly ? (a & ~b) : (b & ~a);
 }
 
 }  // namespace
@@ -216,18 +206,9 @@ int ranker_select(cm_ctx*, const void*, const std::vector<int32_t>& rows,
                   std::vector<uint32_t>& bitmap, const uint32_t** d_bits_out,
                   const int32_t** d_rows_out)
 {
-    bitmap.assign((size_t)nwords, 0u);
-    for (const SelTile& t : tiles)
-        for (int32_t i = 0; i < t.na; ++i)
-            for (int32_t j = 0; j < t.nb; ++j)
-                if (g->keep[(size_t)rows[t.a + i] * g->n + rows[t.b + j]]) {
-                    const int64_t col = t.j0 + j;
-                    bitmap[t.bits + (int64_t)(t.i0 + i) * t.words + (col >> 5)] |= 1u << (col & 31);
-                }
-    g_bits = bitmap;
-    g_rows = rows;
-    if (d_bits_out) *d_bits_out = g_bits.data();
-    if (d_rows_out) *d_rows_out = g_rows.data();
+    mock::select_pairs(rows, tiles, nwords, bitmap);
+    if (d_bits_out) *d_bits_out = mock::selection().bits.data();
+    if (d_rows_out) *d_rows_out = mock::selection().rows.data();
     return CM_OK;
 }
 
@@ -235,17 +216,7 @@ cudaError_t launch_kept_totals(const KeptList* lists, int32_t nlists, const uint
                                const int32_t* reps, const int64_t* off, int64_t* totals,
                                cudaStream_t)
 {
-    for (int32_t l = 0; l < nlists; ++l) {
-        int64_t rows = 0, res = 0;
-        for (int64_t w = 0; w < lists[l].words; ++w)
-            for (uint32_t x = kept_word(lists[l], bits, w); x; x &= x - 1) {
-                const int32_t id = reps[lists[l].b0 + w * 32 + __builtin_ctz(x)];
-                rows += rows_of(off[id + 1] - off[id]);
-                res += off[id + 1] - off[id];
-            }
-        totals[2 * l] = rows;
-        totals[2 * l + 1] = res;
-    }
+    mock::kept_totals(lists, nlists, bits, reps, off, totals);
     return cudaSuccess;
 }
 
@@ -253,17 +224,7 @@ cudaError_t launch_kept_expand(const KeptList* lists, int32_t nlists, const uint
                                const int32_t* reps, const int64_t* off, int32_t* ids,
                                int64_t* srow, cudaStream_t)
 {
-    for (int32_t l = 0; l < nlists; ++l) {
-        int64_t gi = lists[l].g0, row = lists[l].rowbase;
-        for (int64_t w = 0; w < lists[l].words; ++w)
-            for (uint32_t x = kept_word(lists[l], bits, w); x; x &= x - 1) {
-                const int32_t id = reps[lists[l].b0 + w * 32 + __builtin_ctz(x)];
-                row += rows_of(off[id + 1] - off[id]);
-                ids[gi] = id;
-                srow[gi + 1] = row;
-                ++gi;
-            }
-    }
+    mock::kept_expand(lists, nlists, bits, reps, off, ids, srow);
     return cudaSuccess;
 }
 
@@ -292,6 +253,7 @@ int main()
         for (auto& v : I.keep) { int b; std::cin >> b; v = (char)b; }
         g = &I;
         g_buf.clear();
+        mock::selection().keep = [](int32_t x, int32_t y) { return g->keep[(size_t)x * g->n + y] != 0; };
         cm_ctx ctx;
         cm_params prm{};
         prm.T = T;
