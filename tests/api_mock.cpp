@@ -466,8 +466,11 @@ int main()
             std::vector<int32_t> p((size_t)(2 * k));
             for (auto& v : p) std::cin >> v;
             std::vector<int32_t> o((size_t)(cmd == "score" ? k : 5 * k));
+            std::vector<uint8_t> in = seqs;
+            if (flags & CM_ASCII)                      // the same residues as letters
+                for (auto& ch : in) ch = (uint8_t)"arndcqeghilkmfpstwyv"[ch];
             const int r = cmd == "score"
-                ? sw_score_batch(ctx, seqs.data(), g_off.data(), n, p.data(), k, mat, 11, 1, o.data(), flags)
+                ? sw_score_batch(ctx, in.data(), g_off.data(), n, p.data(), k, mat, 11, 1, o.data(), flags)
                 : sw_cells_batch(ctx, seqs.data(), g_off.data(), n, p.data(), k, mat, 11, 1, o.data(), 0);
             if (r) { std::printf("error %d %s\n", r, cm_last_error(ctx)); continue; }
             std::printf("%s %lld\n", cmd.c_str(), (long long)o.size());

@@ -20,7 +20,7 @@ ocm = importlib.import_module("oracle.cluster_merge")
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_1908_10574_gb300", "csrc")
 M64 = (1 << 64) - 1
-CM_FORCE_INT32 = 0x8
+CM_DEVICE_PTRS, CM_ASCII, CM_FORCE_INT32 = 0x1, 0x2, 0x8
 
 
 def _cuda_include():
@@ -155,6 +155,8 @@ def test_score_batch_cells_and_rerun(exe):
         want = [_score(a, b, L, False) for a, b in p]
         H.add("score 0 %d %s" % (k, flat), _expect_values("score", want))
         H.add("score %d %d %s" % (CM_FORCE_INT32, k, flat), _expect_values("score", want))
+        extra = [CM_DEVICE_PTRS, CM_ASCII, CM_ASCII | CM_DEVICE_PTRS][trial % 3]
+        H.add("score %d %d %s" % (extra, k, flat), _expect_values("score", want))
         wc = [v for a, b in p for v in _cells(a, b, L, False)]
         H.add("cells %d %s" % (k, flat), _expect_values("cells", wc))
     H.add("score 0 1 0 %d" % 10 ** 6, _expect_error(-1))       # pair index out of range
