@@ -604,23 +604,30 @@ int Driver::score_ranked(const std::vector<Merge>& ms, const std::vector<char>& 
         std::vector<std::pair<int64_t, int32_t>> sig;
         if ((r = compact_sig(c, out, slots, prm.T, sig))) return r;
         scored += slots;
+        // `sig` is in slot order, so the ranks of one list row ascend: one forward scan of the
+        // list's bitmap words per (list, query row) finds the subject of every significant slot
+        int32_t cur_l = -1;
+        int64_t cur_k = -1, cur_w = 0, before = 0;     // set bits in words [0, cur_w)
         for (const auto& e : sig) {
             const int32_t l = l0 + (int32_t)(std::upper_bound(first.begin(), first.end(), e.first) -
                                              first.begin()) - 1;
             const LMeta& L = meta[l];
             const int64_t local = e.first - first[l - l0];
-            const int64_t k = local / L.count;
-            int64_t rank = local % L.count, w = 0;
-            uint32_t x = 0;
-            for (;; ++w) {
-                x = derived(L, w);
-                const int pc = __builtin_popcount(x);
-                if (rank < pc) break;
-                rank -= pc;
+            const int64_t k = local / L.count, rank = local % L.count;
+            if (l != cur_l || k != cur_k) {
+                cur_l = l;
+                cur_k = k;
+                cur_w = 0;
+                before = 0;
             }
-            for (int64_t q = 0; q < rank; ++q) x &= x - 1;
+            uint32_t x = derived(L, cur_w);
+            while (rank >= before + __builtin_popcount(x)) {
+                before += __builtin_popcount(x);
+                x = derived(L, ++cur_w);
+            }
+            for (int64_t q = before; q < rank; ++q) x &= x - 1;
             const int32_t i1 = (L.op == kKeepBOnly || (L.op == kKeepAnd && k == 1)) ? L.b : L.a;
-            sigm[L.m].push_back({i1, (int32_t)(w * 32 + __builtin_ctz(x)), e.second});
+            sigm[L.m].push_back({i1, (int32_t)(cur_w * 32 + __builtin_ctz(x)), e.second});
         }
         ++batches;
         l0 = l1;
