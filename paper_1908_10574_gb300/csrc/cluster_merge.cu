@@ -273,6 +273,7 @@ int Driver::run_round(const std::vector<Merge>& ms)
         std::unordered_map<uint64_t, int64_t> cmap(cidx[m].begin(), cidx[m].end());
         std::vector<char> merged1(cs1.size(), 0), merged2(cs2.size(), 0);
         std::vector<int32_t> merged_before;               // sorted cs2 indices merged so far
+        std::vector<uint32_t> merged_bits(ranked[m] ? (size_t)words[m] : 0, 0u);   // same, as bits
         const std::vector<SigPair>& sg = sigm[m];
         size_t p = 0;
         for (int32_t i1 = 0; i1 < (int32_t)cs1.size(); ++i1) {
@@ -315,21 +316,20 @@ int Driver::run_round(const std::vector<Merge>& ms)
             if (!ranked[m]) {
                 rep_cmp += end - before;
             } else {
+                // selected cs2 below the break, less those merged before i1's loop started
                 const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
                 int64_t vis = 0;
                 for (int64_t w = 0; w * 32 < end; ++w) {
-                    uint32_t x = row[w];
+                    uint32_t x = row[w] & ~merged_bits[w];
                     if ((w + 1) * 32 > end) x &= (1u << (end - w * 32)) - 1u;
                     vis += __builtin_popcount(x);
                 }
-                for (int64_t k = 0; k < before; ++k) {
-                    const int32_t i2 = merged_before[k];
-                    vis -= (row[i2 >> 5] >> (i2 & 31)) & 1u;
-                }
                 rep_cmp += vis;
             }
-            for (int32_t i2 : newly)
+            for (int32_t i2 : newly) {
                 merged_before.insert(std::upper_bound(merged_before.begin(), merged_before.end(), i2), i2);
+                if (ranked[m]) merged_bits[i2 >> 5] |= 1u << (i2 & 31);
+            }
             p = p_end;
         }
         for (size_t i1 = 0; i1 < cs1.size(); ++i1)
