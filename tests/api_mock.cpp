@@ -19,6 +19,8 @@
 // Commands on stdin (tokens): "seqs n len..." | "sym 0|1" | "sparse 0|1" | "limit S" | "tuning W rows" |
 // "score flags k a0 b0 ..." | "cells k a0 b0 ..." | "allpairs T part nparts capacity" |
 // "cm T mT mU use_ranker min_pairs".  Each prints one result block or "error code message".
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -82,9 +84,10 @@ void fake_cells(int32_t a, int32_t b, int64_t c[5])
 }
 
 int64_t tri(int64_t k) { return k * (k - 1) / 2; }
-int64_t tri_row(int64_t v)
+int64_t tri_row(int64_t v)          // k with tri(k) <= v < tri(k + 1)
 {
-    int64_t k = 0;
+    int64_t k = (int64_t)((1.0 + std::sqrt(1.0 + 8.0 * (double)v)) * 0.5);
+    while (k > 0 && tri(k) > v) --k;
     while (tri(k + 1) <= v) ++k;
     return k;
 }
@@ -305,8 +308,7 @@ cudaError_t launch_collect_saturated(const int32_t* out, int64_t nslots, const S
                                      int32_t* count, int32_t cap, cudaStream_t)
 {
     for (int64_t i = 0; i < nslots; ++i) {
-        int32_t b = 0;
-        while (b + 1 < nblocks && first_slot[b + 1] <= i) ++b;
+        int32_t b = (int32_t)(std::upper_bound(first_slot, first_slot + nblocks, i) - first_slot) - 1;
         const SwBlock& B = blocks[b];
         const int64_t v = i - B.out_base;
         int64_t k, s;
