@@ -356,16 +356,16 @@ int64_t plan_blocks(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& id
         plan.blocks.push_back(B);
         const int32_t bidx = (int32_t)plan.blocks.size() - 1;
         const int64_t* srow = plan.srow.data() + B.srow;
+        // residues of the subjects before s, so a query's cells are one product
+        std::vector<int64_t> pre((size_t)r.b_count + 1, 0);
+        for (int64_t s = 0; s < r.b_count; ++s) pre[s + 1] = pre[s] + P.len(ids[r.b_begin + s]);
         for (int64_t k = 0; k < r.a_count; k += 2) {
             const bool hi = k + 1 < r.a_count;
             const int32_t qhi = ids[r.a_begin + (hi ? k + 1 : k)];
             int32_t ns = (int32_t)r.b_count;
             if (r.kind == kTri) ns = (int32_t)(hi ? k + 1 : k);
-            for (int64_t q = k; q < k + (hi ? 2 : 1); ++q) {
-                const int64_t mq = P.len(ids[r.a_begin + q]);
-                const int64_t nsq = (r.kind == kTri) ? q : r.b_count;
-                for (int64_t s = 0; s < nsq; ++s) plan.cells += mq * P.len(ids[r.b_begin + s]);
-            }
+            for (int64_t q = k; q < k + (hi ? 2 : 1); ++q)
+                plan.cells += P.len(ids[r.a_begin + q]) * pre[(r.kind == kTri) ? q : r.b_count];
             if (ns > 0) add_tasks(plan, bidx, (int32_t)k, ns, hi, P.len(qhi), srow, target);
         }
         if (nslots == 0) {   // keep first_slot strictly usable by the saturated-pair scan

@@ -4,7 +4,8 @@
 // the launch bins, the int16 -> int32 rerun loop, the slot maps, compaction, the cells pipeline,
 // the bounded batches and the ClusterMerge driver do not depend on what the scores mean) and
 // check the launch contracts the real kernels rely on: a zeroed task ticket per launch, every
-// task in its launch's (tile, mode) bin, long pairs only on the whole-CTA kernels.  Device
+// task in its launch's (tile, mode) bin, long pairs only on the whole-CTA kernels; after every
+// call the library's cell count must equal the cells the mock int16 kernel computed.  Device
 // memory is host memory filled with garbage when allocated.
 //
 // fake score of the ordered pair (a, b): 0 if either is empty; else, with
@@ -103,6 +104,7 @@ bool contract_error(const SwArgs& a, const char* what)
 }
 
 constexpr int64_t kMockChunk = 64;   // compaction chunk of the mock (small: many chunks)
+int64_t g_cells_done = 0;            // cells of every slot the mock int16 kernel computed
 
 }  // namespace
 
@@ -226,6 +228,7 @@ cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaS
                                                             : (int64_t)(q - B.k0) * B.nb + s);
                 if (B.has_map) slot = a.out_map[slot];
                 const int32_t qid = a.ids[B.a_ids + q], xid = a.ids[B.b_ids + s];
+                g_cells_done += len_of(qid) * len_of(xid);
                 const int32_t f = fake_score(first_of(qid, xid, B.swap), second_of(qid, xid, B.swap));
                 a.out[slot] = (a.sat_thr < 0 || f + a.beta >= a.sat_thr) ? kSat : f;
             }
@@ -512,6 +515,12 @@ int main()
             std::printf("error unknown command %s\n", cmd.c_str());
             return 1;
         }
+        // the library's cell count must be the cells its int16 launches computed
+        cm_stats st{};
+        cm_get_stats(ctx, &st);
+        if (st.cells != g_cells_done)
+            std::fprintf(stderr, "mock contract violated: cells counted %lld, computed %lld\n",
+                         (long long)st.cells, (long long)g_cells_done);
         std::fflush(stdout);
     }
     cm_destroy(ctx);
