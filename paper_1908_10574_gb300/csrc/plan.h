@@ -7,7 +7,6 @@
 
 #include <algorithm>
 #include <cstdint>
-#include <numeric>
 #include <utility>
 #include <vector>
 
@@ -115,19 +114,26 @@ inline void add_tasks(Plan& P, int32_t block, int32_t k, int32_t ns, bool hi_val
     }
 }
 
-// Groups the tasks by launch bin (descending), most work first inside a bin.
+// Groups the tasks by launch bin (descending), most work first inside a bin, ties in the
+// order the tasks were made.  (The keys are sorted with their task index, not through it, so
+// the sort stays cache-friendly for the millions of tasks of a large merge.)
 inline void order_tasks(Plan& P)
 {
-    const auto& keys = P.keys;
-    std::vector<size_t> idx(P.tasks.size());
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
-        if (keys[x].second != keys[y].second) return keys[x].second > keys[y].second;
-        return keys[x].first > keys[y].first;
+    struct Key {
+        int64_t cost;
+        int bin;
+        size_t i;
+    };
+    std::vector<Key> k(P.tasks.size());
+    for (size_t i = 0; i < k.size(); ++i) k[i] = {P.keys[i].first, P.keys[i].second, i};
+    std::sort(k.begin(), k.end(), [](const Key& x, const Key& y) {
+        if (x.bin != y.bin) return x.bin > y.bin;
+        if (x.cost != y.cost) return x.cost > y.cost;
+        return x.i < y.i;
     });
-    std::vector<SwTask> t2(idx.size());
-    std::vector<int> r2(idx.size());
-    for (size_t i = 0; i < idx.size(); ++i) { t2[i] = P.tasks[idx[i]]; r2[i] = P.task_R[idx[i]]; }
+    std::vector<SwTask> t2(k.size());
+    std::vector<int> r2(k.size());
+    for (size_t i = 0; i < k.size(); ++i) { t2[i] = P.tasks[k[i].i]; r2[i] = P.task_R[k[i].i]; }
     P.tasks.swap(t2);
     P.task_R.swap(r2);
 }
