@@ -15,12 +15,13 @@
 // the subject stream, so each packed DPX instruction advances two cells.
 //
 // Packed-int16 formulation.  Every stored value carries a bias beta >= o+e (stored = true +
-// beta), which keeps each half within [beta-o, 32767]: integer adds of packed constants then
-// never borrow across halves (they run on the IADD path, off the DPX pipe), and only the
-// maxima use DPX.  Per packed column: 4.5 ALU-pipe ops (3 viaddmax, 1 vimax3, 1/2 vimax3 for
-// the running maximum) and 2 IADDs.  If a stored best reaches 32767 - max(S), some cell may
-// have overflowed int16; that pair is marked and rescored on the int32 path, so every score
-// returned is exact.
+// beta), which keeps each half within [beta-o, 32767].  The DP keeps H - o, the value both gap
+// types open from, and the profile carries S + o, so the diagonal term reads H - o as well:
+// per packed column 3 viaddmax (E, F, diagonal), 1 vimax3 (H) and 1/2 vimax3 (running
+// maximum, every two columns) on the ALU pipe, plus one plain 32-bit subtract for H - o on
+// the IADD path (H >= beta > o in both halves, so it never borrows across them).  If a stored
+// best reaches 32767 - max(S), some cell may have overflowed int16; that pair is marked and
+// rescored on the int32 path, so every score returned is exact.
 #pragma once
 #include <algorithm>
 
