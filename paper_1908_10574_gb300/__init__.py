@@ -74,7 +74,16 @@ class Context:
 
     @staticmethod
     def _host(x, dtype, shape=None):
-        x = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+        a = np.asarray(x)
+        if (np.dtype(dtype).kind in "iu" and a.dtype != dtype and a.size and
+                a.dtype.kind in "iubf"):
+            # a narrowing cast would wrap (2^32 + 5 -> 5): values must fit the C type exactly
+            info = np.iinfo(dtype)
+            if a.dtype.kind == "f" and not np.array_equal(a, np.round(a)):
+                raise ValueError("non-integer values for a %s argument" % np.dtype(dtype).name)
+            if a.min() < info.min or a.max() > info.max:
+                raise ValueError("values outside the %s range" % np.dtype(dtype).name)
+        x = np.ascontiguousarray(a, dtype=dtype)
         if shape is not None:
             x = x.reshape(shape)
         return x
