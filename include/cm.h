@@ -20,9 +20,9 @@
  *     seqs[offsets[i] .. offsets[i+1]), offsets has n_seqs+1 non-decreasing int64 entries
  *     starting at 0.  Sequences may be empty (their scores are 0); one longer than 2^28
  *     residues is rejected with CM_ERR_ARG.  Device scratch grows with the longest sequence
- *     of a call (one boundary column per resident warp, about 80 KB per residue at 16 warps
- *     per CTA on 152 SMs: ~3 GB at 35,000 residues); a call whose scratch does not fit the
- *     device fails with CM_ERR_OOM before any output is written.
+ *     of a call (one boundary column per resident warp, 40-160 KB per residue on 152 SMs: a
+ *     few GB at 35,000 residues); a call whose scratch does not fit the device fails with
+ *     CM_ERR_OOM before any output is written.
  *   - Matrix: 400 int8 entries, row-major, matrix[x*20 + y] = score of residue x of the
  *     pair's FIRST sequence against residue y of its SECOND sequence.  Entries must lie in
  *     [-1000, 1000]; it need not be symmetric.
