@@ -208,10 +208,20 @@ cudaError_t launch_gather_stream(const uint8_t*, const int64_t*, const int32_t*,
     return cudaSuccess;
 }
 
+// first s in [lo, hi] with v[s] >= key; then the nearer of it and its predecessor (the
+// kernel's split of a task's rows over its warps' streams, at subject boundaries)
+int32_t nearest_boundary(const int64_t* v, int32_t lo, int32_t hi, int64_t key)
+{
+    const int32_t s = (int32_t)(std::lower_bound(v + lo, v + hi + 1, key) - v);
+    const int32_t t = s > hi ? hi : s;
+    return (t > lo && key - v[t - 1] < v[t] - key) ? t - 1 : t;
+}
+
 cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaStream_t)
 {
     if (grid < 1 || (W != 4 && W != 8 && W != 16)) return cudaErrorInvalidValue;
     if (*a.task_counter != 0) { contract_error(a, "task ticket not zeroed"); return cudaSuccess; }
+    const int spw = mode == kModePair ? 1 : mode == kModeTwo16 ? 4 : 2;
     for (int32_t i = 0; i < a.ntasks; ++i) {
         const SwTask& t = a.tasks[i];
         const SwBlock& B = a.blocks[t.block];
@@ -219,6 +229,23 @@ cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaS
         const TileChoice tc = choose_tile(len_of(qhi), t.hi_valid != 0);
         if (t.mode != mode || tc.mode != mode || tc.R != R || tc.npass != t.npass) {
             contract_error(a, "task outside its launch bin");
+            return cudaSuccess;
+        }
+        // every warp stream of a multi-pass task must fit the boundary buffer's stride
+        const int64_t* srow = a.srows + B.srow;
+        const int64_t R0 = srow[t.s0], R1 = srow[t.s1];
+        int64_t nmax = 0;
+        for (int w = 0; w < W; ++w) {
+            int32_t prev = -1;
+            for (int k = 0; k <= spw; ++k) {
+                const int32_t b = nearest_boundary(srow, t.s0, t.s1,
+                                                   R0 + (R1 - R0) * (w * spw + k) / (W * spw));
+                if (prev >= 0) nmax = std::max(nmax, srow[b] - srow[prev]);
+                prev = b;
+            }
+        }
+        if (t.npass > 1 && (tc.seg == 16 || nmax > a.bnd_stride)) {
+            contract_error(a, "warp stream longer than the boundary stride");
             return cudaSuccess;
         }
         for (int32_t q = t.k; q <= t.k + (t.hi_valid ? 1 : 0); ++q)
@@ -244,6 +271,7 @@ static cudaError_t rescore(const SwArgs& a, const PairRef* pr, int32_t n, int32_
     for (int32_t i = 0; i < n; ++i) {
         const bool lng = len_of(pr[i].q) >= kLongMinCols && len_of(pr[i].x) >= kLongMinRows;
         if (lng != want_long) { contract_error(a, "pair on the wrong rerun kernel"); return cudaSuccess; }
+        if (len_of(pr[i].x) > a.bnd_stride) { contract_error(a, "rerun subject longer than the stride"); return cudaSuccess; }
         a.out[pr[i].slot] = fake_score(first_of(pr[i].q, pr[i].x, pr[i].swap),
                                        second_of(pr[i].q, pr[i].x, pr[i].swap));
     }
