@@ -4,8 +4,10 @@
 // the launch bins, the int16 -> int32 rerun loop, the slot maps, compaction, the cells pipeline,
 // the bounded batches and the ClusterMerge driver do not depend on what the scores mean) and
 // check the launch contracts the real kernels rely on: a zeroed task ticket per launch, every
-// task in its launch's (tile, mode) bin, long pairs only on the whole-CTA kernels; after every
-// call the library's cell count must equal the cells the mock int16 kernel computed.  Device
+// task in its launch's (tile, mode) bin, each warp stream within the boundary stride, the row
+// stream holding the block's subjects where the kernel reads them, long pairs only on the
+// whole-CTA kernels; after every call the library's cell count must equal the cells the mock
+// int16 kernel computed.  Device
 // memory is host memory filled with garbage when allocated.
 //
 // fake score of the ordered pair (a, b): 0 if either is empty; else, with
@@ -200,11 +202,21 @@ cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, in
     return cudaSuccess;
 }
 
-cudaError_t launch_gather_stream(const uint8_t*, const int64_t*, const int32_t*, int32_t nb,
-                                 const int64_t* srow, uint8_t*, cudaStream_t)
+// subject s of the list occupies rows [srow[s], srow[s + 1]): its residues, then pad rows;
+// the first row flagged kFirst, the last residue's row (row 0 when empty) kLast
+cudaError_t launch_gather_stream(const uint8_t* db, const int64_t* off, const int32_t* ids,
+                                 int32_t nb, const int64_t* srow, uint8_t* stream, cudaStream_t)
 {
-    for (int32_t s = 0; s < nb; ++s)
+    for (int32_t s = 0; s < nb; ++s) {
         if (srow[s + 1] < srow[s]) return cudaErrorInvalidValue;
+        const int64_t b = off[ids[s]], len = off[ids[s] + 1] - b;
+        for (int64_t r = 0; r < srow[s + 1] - srow[s]; ++r) {
+            uint8_t v = r < len ? db[b + r] : (uint8_t)kPadCode;
+            if (r == 0) v |= kFirst;
+            if (r == (len > 0 ? len - 1 : 0)) v |= kLast;
+            stream[srow[s] + r] = v;
+        }
+    }
     return cudaSuccess;
 }
 
@@ -247,6 +259,20 @@ cudaError_t launch_sw16(int R, int W, int mode, int grid, const SwArgs& a, cudaS
         if (t.npass > 1 && (tc.seg == 16 || nmax > a.bnd_stride)) {
             contract_error(a, "warp stream longer than the boundary stride");
             return cudaSuccess;
+        }
+        // the rows the device kernel reads for subject s must be that subject's
+        for (int32_t s = t.s0; s < t.s1; ++s) {
+            const int32_t xid = a.ids[B.b_ids + s];
+            const uint8_t* row = a.streams + B.stream + srow[s];
+            const int64_t len = len_of(xid);
+            bool ok = srow[s + 1] - srow[s] == stream_rows(len) && (row[0] & kFirst) &&
+                      (row[len > 0 ? len - 1 : 0] & kLast);
+            for (int64_t r = 0; ok && r < srow[s + 1] - srow[s]; ++r)
+                ok = (row[r] & 31) == (r < len ? a.db[a.off[xid] + r] : (uint8_t)kPadCode);
+            if (!ok) {
+                contract_error(a, "row stream does not hold the block's subject");
+                return cudaSuccess;
+            }
         }
         for (int32_t q = t.k; q <= t.k + (t.hi_valid ? 1 : 0); ++q)
             for (int32_t s = t.s0; s < t.s1; ++s) {
