@@ -58,6 +58,32 @@ def test_batched_rep_wave_matches_oracle(case, limit):
     assert got["stats"]["comparisons_scored"] == one["stats"]["comparisons_scored"]
 
 
+@pytest.fixture(scope="module")
+def case2k():
+    """2,000 proteins of the 100k benchmark set (same recipe and stream): 200 whole families of
+    8 and 400 singletons, in the set's order."""
+    full = synth.proteome(100000, family_size=8, singleton_frac=0.2, stream=3)
+    fam, counts = np.unique(full.family, return_counts=True)
+    rng = np.random.default_rng(1908)
+    fams = rng.choice(fam[counts == 8], 200, replace=False)
+    singles = rng.choice(fam[counts == 1], 400, replace=False)
+    ids = np.flatnonzero(np.isin(full.family, np.concatenate([fams, singles])))
+    assert len(ids) == 2000
+    ss = full.subset(ids)
+    return ss, _oracle_cm(ss, 100, 138, 15)
+
+
+@pytest.mark.parametrize("limit", [0, 1 << 16])
+def test_2k_subset_of_the_100k_set_exact(case2k, limit):
+    """Clusters, similar pairs and comparison counts equal the oracle's on the 2k subset, with
+    whole rounds in one device batch and in batches of 65,536 slots."""
+    ss, want = case2k
+    ctx = cm.Context(0)
+    ctx.set_batch_limit(limit)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 100, 138, 15)
+    _check(got, want)
+
+
 def test_batch_limit_argument_checks():
     ctx = cm.Context(0)
     with pytest.raises(cm.CMError):
