@@ -507,13 +507,15 @@ int main()
         if (cmd == "limit") {
             long long s;
             std::cin >> s;
-            if (cm_set_batch_limit(ctx, s)) std::printf("error limit\n");
+            const int r = cm_set_batch_limit(ctx, s);
+            if (r) std::printf("error %d %s\n", r, cm_last_error(ctx));
             continue;
         }
         if (cmd == "tuning") {
             int w, r;
             std::cin >> w >> r;
-            if (cm_set_tuning(ctx, w, r)) std::printf("error tuning\n");
+            const int e = cm_set_tuning(ctx, w, r);
+            if (e) std::printf("error %d %s\n", e, cm_last_error(ctx));
             continue;
         }
         const int32_t n = (int32_t)g_off.size() - 1;

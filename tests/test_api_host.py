@@ -163,6 +163,25 @@ def test_score_batch_cells_and_rerun(exe):
     H.run()
 
 
+def test_argument_errors(exe):
+    """Invalid arguments come back as CM_ERR_ARG (-1) with nothing computed, and the context
+    stays usable."""
+    H = Harness(exe)
+    L = [40, 300, 0, 2500]
+    H.add("seqs 4 %s" % " ".join(map(str, L)), None)
+    H.add("sym 1", None)
+    H.add("allpairs 50 3 3 100", _expect_error(-1))             # part >= n_parts
+    H.add("allpairs 50 -1 3 100", _expect_error(-1))
+    H.add("cells 1 0 4", _expect_error(-1))                     # pair index out of range
+    H.add("score 0 1 -1 0", _expect_error(-1))
+    H.add("tuning 12 0", _expect_error(-1))                      # warps must be 4, 8 or 16
+    H.add("tuning 0 100", _expect_error(-1))                     # rows below 256
+    H.add("limit 1000", _expect_error(-1))                       # below 1,024 slots
+    H.add("score 0 2 0 1 3 1", _expect_values("score", [_score(0, 1, L, True),
+                                                         _score(3, 1, L, True)]))
+    H.run()
+
+
 def test_allpairs_parts(exe):
     rng = np.random.default_rng(12)
     H = Harness(exe)
