@@ -88,6 +88,14 @@ int cm_set_tuning(cm_ctx *ctx, int32_t warps_per_cta, int32_t rows_per_warp);
  * 0 restores the default of 2^32. */
 int cm_set_batch_limit(cm_ctx *ctx, int64_t max_slots);
 
+/* Bound on the one device wait of the library: a pass of the whole-CTA long-pair kernels
+ * (int32 rescoring and alignment cells of pairs of >= 2,048 x 512 residues) waits for the
+ * rows its predecessor pass has written.  Such a wait always ends in a correct run; after
+ * `polls` polls of ~100 ns each it gives up instead, the call returns CM_ERR_TIMEOUT with
+ * nothing written, and the context stays usable.  0 restores the default of 2^24 polls
+ * (~1.7 s).  A small value exists to exercise that error path. */
+int cm_set_wait_limit(cm_ctx *ctx, int32_t polls);
+
 /* Autotuner: scores the all-against-all of a length-stratified sample of `sample_seqs` of the
  * given sequences (0 = 3000) under every CTA width (4, 8, 16 warps) and warp-stream length
  * (4096 .. 32768 rows), keeps the fastest (CUDA-event time of the int16x2 kernel per cell) as
@@ -246,11 +254,14 @@ int cm_ranker_logits(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, i
  * It calls no cudaMalloc, cudaFree or other allocating routine: the per-pair DP rows use one
  * fixed 32 MiB array compiled into the library, which every GPU that loads the library keeps
  * until the process exits.  Limit: the second sequence of every pair must have at most 4095
- * residues; larger pairs are rejected with CM_ERR_ARG before anything is written.  The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  All calls share the array: calls whose work overlaps
- * on the GPU (other streams or threads) race and must be serialised by the caller.  The call
- * returns after the results are written. */
+ * residues; larger pairs are rejected with CM_ERR_ARG before anything is written.  Pair
+ * indices, offset order and residue codes are checked on the device before any output is
+ * written, but the length of the `seqs` allocation is not passed: offsets[n_seqs] must not
+ * exceed it (the caller's guarantee).  Every call looks up that array's device address on the
+ * current device (cudaGetSymbolAddress; the first lookup on a device may load the library's
+ * device code), so make the first call on a device before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (other streams or threads) race and
+ * must be serialised by the caller.  The call returns after the results are written. */
 int sw_cells_batch_noalloc(const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
                            const int32_t *pairs, int64_t n_pairs, const int8_t *matrix,
                            int32_t gap_open, int32_t gap_extend, int32_t *cells_out,

@@ -132,6 +132,11 @@ class Context:
         """Pair slots of one device batch of ClusterMerge's representative wave (0: default)."""
         _L.check(self._h, _L.lib().cm_set_batch_limit(self._h, int(max_slots)))
 
+    def set_wait_limit(self, polls=0):
+        """Polls (~100 ns each) before the long-pair pipeline wait gives up with
+        CM_ERR_TIMEOUT (0: the default of 2^24)."""
+        _L.check(self._h, _L.lib().cm_set_wait_limit(self._h, int(polls)))
+
     # ---- entry points ---------------------------------------------------------------------
     def sw_score_batch(self, seqs, offsets, pairs, matrix, gap_open, gap_extend, flags=0,
                        out=None):
@@ -340,11 +345,25 @@ def sw_allpairs(seqs, offsets, matrix, gap_open, gap_extend, T, part=0, n_parts=
 
 def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, cells_out,
                            flags=0):
-    """Allocation-free alignment cells (see include/cm.h): every array except `matrix` is a
-    torch CUDA tensor on the current device, `cells_out` is a caller-allocated (n, 5) int32
-    CUDA tensor, and the current torch stream is used.  Nothing is allocated by the call."""
+    """Allocation-free alignment cells (see include/cm.h): `seqs` (uint8), `offsets` (int64,
+    n+1), `pairs` (int32, (k, 2)) and `cells_out` (int32, (k, 5), caller-allocated) are
+    contiguous torch CUDA tensors on the current device; `matrix` is a host array of 400
+    int8-range values; the current torch stream is used.  Nothing is allocated by the call."""
     import torch
-    m = np.ascontiguousarray(np.asarray(matrix), dtype=np.int8).reshape(400)
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("seqs", seqs, torch.uint8), ("offsets", offsets, torch.int64),
+                        ("pairs", pairs, torch.int32), ("cells_out", cells_out, torch.int32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev):
+            raise TypeError("%s must be a CUDA tensor on the current device (cuda:%d)" % (name, dev))
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError("%s must be a contiguous %s tensor" % (name, dt))
+    if offsets.dim() != 1 or offsets.shape[0] < 1:
+        raise ValueError("offsets must have shape (n_seqs + 1,)")
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (k, 2)")
+    if tuple(cells_out.shape) != (pairs.shape[0], 5):
+        raise ValueError("cells_out must have shape (%d, 5)" % pairs.shape[0])
+    m = Context._host(matrix, np.int8, (400,))
     buf = ctypes.create_string_buffer(256)
     code = _L.lib().sw_cells_batch_noalloc(
         _ptr(seqs), _ptr(offsets), int(offsets.shape[0]) - 1, _ptr(pairs), int(pairs.shape[0]),

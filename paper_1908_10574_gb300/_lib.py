@@ -77,6 +77,7 @@ def lib():
         "cm_set_stream": (ctypes.c_int, [p, p]),
         "cm_set_tuning": (ctypes.c_int, [p, i32, i32]),
         "cm_set_batch_limit": (ctypes.c_int, [p, ctypes.c_int64]),
+        "cm_set_wait_limit": (ctypes.c_int, [p, i32]),
         "cm_get_stats": (ctypes.c_int, [p, ctypes.POINTER(cm_stats)]),
         "cm_autotune": (ctypes.c_int, [p, p, p, i32, p, i32, i32, i32, ctypes.c_char_p,
                                        ctypes.POINTER(i32), ctypes.POINTER(i32), u32]),

@@ -201,6 +201,7 @@ int run_plan(cm_ctx* c, const Prepared& P, Plan& plan, int32_t* out, const int64
     a.out = out;
     a.out_map = d_omap;
     a.err = d_flags + 1;
+    a.wait_limit = c->wait_limit;
     std::memcpy(a.mat, P.mat, sizeof(a.mat));
     a.gap_open = P.g1;
     a.gap_extend = P.ge;
@@ -538,6 +539,7 @@ int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, 
     a.bnd = d_bnd;
     a.bnd_stride = stride;
     a.err = d_flags + 1;
+    a.wait_limit = c->wait_limit;
     std::memcpy(a.mat, P.mat, sizeof(a.mat));
     a.gap_open = P.g1;
     a.gap_extend = P.ge;
@@ -747,6 +749,14 @@ int cm_set_batch_limit(cm_ctx* c, int64_t max_slots)
     if (max_slots != 0 && max_slots < 1024)
         return fail(c, CM_ERR_ARG, "max_slots must be 0 or >= 1024");
     c->max_batch_slots = max_slots ? max_slots : ((int64_t)1 << 32);
+    return CM_OK;
+}
+
+int cm_set_wait_limit(cm_ctx* c, int32_t polls)
+{
+    if (!c) return CM_ERR_ARG;
+    if (polls < 0) return fail(c, CM_ERR_ARG, "polls must be >= 0 (0 restores the default)");
+    c->wait_limit = polls ? polls : (1 << 24);
     return CM_OK;
 }
 

@@ -95,6 +95,7 @@ struct SwArgs {
     int32_t gap_extend;
     int32_t beta;               // int16 bias: stored = true + beta
     int32_t sat_thr;            // stored best >= sat_thr -> rerun in int32
+    int32_t wait_limit;         // polls of a bounded device wait before it gives up (long pairs)
 };
 
 constexpr int32_t kSat = INT32_MIN;   // output slot marker: saturated in int16, rerun pending

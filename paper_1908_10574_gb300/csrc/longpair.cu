@@ -7,9 +7,10 @@
 // publishes how many rows of its current pass are written in shared memory (tagged with the
 // pass), after a block fence.  Waits only point from pass p to pass p - 1 (never backwards),
 // and the warps of a CTA are co-resident, so the pipeline always advances; every wait is still
-// bounded and sets the error flag (2) when it gives up.  Slot p mod LW is rewritten by pass
-// p + LW, which trails its reader (pass p + 1) by at least 32 (LW - 1) rows through the chain
-// of waits, so a row is never overwritten before it has been read.
+// bounded (SwArgs::wait_limit polls of ~100 ns) and sets the error flag (2) when it gives up.
+// Slot p mod LW is rewritten by pass p + LW, which trails its reader (pass p + 1) by at least
+// 32 (LW - 1) rows through the chain of waits, so a row is never overwritten before it has
+// been read.
 #include "sw16_kernel.cuh"
 
 namespace cm {
@@ -17,7 +18,6 @@ namespace {
 
 constexpr int kLW = 8;                 // warps per CTA (passes in flight)
 constexpr int kLR = 8;                 // columns per lane: 256-column passes
-constexpr int kLongSpin = 1 << 24;     // bounded wait: iterations of ~100 ns each
 
 // the job in a form common to both uses: rows stream sequence `ra` (m residues), the columns
 // hold `cb` (n residues); either may be read back to front (cells reverse pass)
@@ -127,7 +127,7 @@ long_pair_kernel(const __grid_constant__ SwArgs a, const PairRef* __restrict__ p
                             for (;;) {
                                 const int32_t ps = s_pass[src];
                                 if (ps > pass - 1 || (ps == pass - 1 && s_prog[src] >= need)) break;
-                                if (++spins > kLongSpin) { ok = 0; break; }
+                                if (++spins > a.wait_limit) { ok = 0; break; }
                                 __nanosleep(100);
                             }
                             __threadfence_block();

@@ -8,16 +8,16 @@
 // this library instead of a context's grow-on-demand buffers.
 //
 // The scratch below is a file-scope __device__ array.  In host code its name is only a
-// host-side stand-in, never a device address, so the first call on each device looks up the
-// real address once with cudaGetSymbolAddress (with that device current) and passes that
-// pointer to the kernels.  Every GPU that loads the library holds the array until the process
-// exits.  All calls on a device share it, so two calls whose work overlaps on the GPU race;
-// the array keeps the last call's contents, and the status words at its end are cleared at the
-// start of every call.
+// host-side stand-in, never a device address, so every call looks up the real address with
+// cudaGetSymbolAddress (with the caller's device current) and passes that pointer to the
+// kernels.  The address is not cached: after a cudaDeviceReset the module is loaded again and
+// the array may move, and a lookup allocates nothing.  Every GPU that loads the library holds
+// the array until the process exits.  All calls on a device share it, so two calls whose work
+// overlaps on the GPU race; the array keeps the last call's contents, and the status words at
+// its end are cleared at the start of every call.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "cm_internal.h"
 
@@ -27,7 +27,6 @@ constexpr int kNaThreads = 1024;                 // pairs in flight (one thread 
 constexpr int kNaCols = 4096;                    // DP row length: second sequence <= 4095
 constexpr size_t kNaRowWords = 2ull * kNaThreads * kNaCols;   // H and F rows: 32 MiB
 constexpr size_t kNaStatusWords = 64;            // status words after the rows
-constexpr int kNaMaxDevices = 64;
 constexpr int32_t kNaNeg = -(1 << 28);
 
 static __device__ __align__(256) int32_t g_na_scratch[kNaRowWords + kNaStatusWords];
@@ -35,14 +34,6 @@ static __device__ __align__(256) int32_t g_na_scratch[kNaRowWords + kNaStatusWor
 struct NaMatrix {
     int16_t v[400];
 };
-
-struct NaDevice {
-    bool ready = false;
-    int32_t* ptr = nullptr;
-};
-
-std::mutex g_na_mu;
-NaDevice g_na_dev[kNaMaxDevices];
 
 void na_message(char* buf, int32_t len, const char* msg)
 {
@@ -166,32 +157,23 @@ extern "C" int sw_cells_batch_noalloc(const uint8_t* seqs, const int64_t* offset
     }
     if (n_pairs == 0) return CM_OK;
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
-        na_message(err_msg, err_len, "no usable current CUDA device");
-        return CM_ERR_CUDA;
-    }
+    // the array's device address on the current device, looked up on every call
     int32_t* scratch = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_dev[dev].ready) {
-            // once per device, with that device current: the device address of the array
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_na_scratch);
-            if (e != cudaSuccess || !p) {
-                na_message(err_msg, err_len, "cudaGetSymbolAddress of the scratch array failed");
-                return CM_ERR_CUDA;
-            }
-            g_na_dev[dev].ptr = static_cast<int32_t*>(p);
-            g_na_dev[dev].ready = true;
+        void* p = nullptr;
+        const cudaError_t le = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (le != cudaSuccess || !p) {
+            cudaGetLastError();
+            na_message(err_msg, err_len, "cudaGetSymbolAddress of the scratch array failed "
+                                         "(no usable current CUDA device?)");
+            return CM_ERR_CUDA;
         }
-        scratch = g_na_dev[dev].ptr;
+        scratch = static_cast<int32_t*>(p);
     }
     int32_t* status = scratch + kNaRowWords;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
 
-    e = cudaMemsetAsync(status, 0, kNaStatusWords * sizeof(int32_t), st);
+    cudaError_t e = cudaMemsetAsync(status, 0, kNaStatusWords * sizeof(int32_t), st);
     if (e == cudaSuccess) {
         const int64_t blocks = std::min<int64_t>((n_pairs + 255) / 256, 4096);
         na_check_kernel<<<(unsigned)blocks, 256, 0, st>>>(seqs, offsets, n_seqs, pairs, n_pairs,

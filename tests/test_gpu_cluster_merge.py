@@ -114,3 +114,17 @@ def test_empty_and_tiny_sequences_exact(ctx):
                                prune_logit=-1e30, ranker_min_pairs=0)
     assert ranked["clusters"] == want["clusters"]
     assert ranked["pairs"].tolist() == want["pairs"].tolist()
+
+
+def test_transitivity_handworked_cases(ctx):
+    """The hand-worked transitivity cases (Sec. 4, tests/golden/transitivity_handworked.tsv):
+    the GPU merge takes the same full-merge branch as the hand derivation and the oracle, on
+    the cells its own alignment-cells pass computes."""
+    import test_oracle_transitivity as tt
+    for case in tt.CASES:
+        ss = synth.SeqSet.from_list([synth.encode(case["a"]), synth.encode(case["b"])])
+        got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, tt.T, case["mT"], case["mU"])
+        assert got["clusters"] == case["clusters"], case["why"]
+        _check(got, _oracle_cm(ss, tt.T, case["mT"], case["mU"]))
+        cells = ctx.sw_cells_batch(ss.seqs, ss.offsets, np.array([[0, 1]], np.int32), S62, 11, 1)
+        assert tuple(cells[0]) == (case["score"],) + case["cells"], case["why"]

@@ -294,3 +294,54 @@ def test_full_size_allpairs_sampled_exact(ctx):
     pick = np.concatenate([np.flatnonzero(vals >= 32767 - 11),
                            rng.choice(len(keys), 5000, replace=False)])
     assert np.array_equal(oracle.sw_batch(ss.seqs, ss.offsets, keys[pick], S62, 11, 1), vals[pick])
+
+
+def test_full_size_single_query_modes_sampled_exact(ctx):
+    """sw_score_batch's single-query launch modes at full size.  A generic pair list becomes
+    one block per distinct first sequence, a lone query that runs with two or four subject
+    streams per warp (the modes that score a ranked merge's per-representative subject
+    lists).  64 queries of the 20,000-protein set, spread over its length range (short ones
+    in 16-lane segments, long ones in 512-column passes), each against every protein: 1.28M
+    pairs, checked on a 100,000-pair sample and on every pair the oracle scores above T."""
+    ss = synth.proteome(20000, 10)
+    n = len(ss)
+    order = np.argsort(ss.lengths, kind="stable")
+    queries = order[np.linspace(0, n - 1, 64).astype(np.int64)]
+    assert ss.lengths[queries].min() <= 256 and ss.lengths[queries].max() > 1024
+    pairs = np.stack([np.repeat(queries, n), np.tile(np.arange(n), len(queries))], 1)
+    pairs = pairs[pairs[:, 0] != pairs[:, 1]].astype(np.int32)
+    got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    rng = np.random.default_rng(2021)
+    pick = rng.choice(len(pairs), 100000, replace=False)
+    want = oracle.sw_batch(ss.seqs, ss.offsets, pairs[pick], S62, 11, 1)
+    assert np.array_equal(got[pick], want)
+    # every planted relative of a query (same family) plus every pair the GPU puts above T
+    fam = ss.family
+    rel = np.flatnonzero((fam[pairs[:, 0]] == fam[pairs[:, 1]]) & (fam[pairs[:, 0]] >= 0))
+    hi = np.union1d(rel, np.flatnonzero(got > 100))
+    assert len(hi) > 64
+    assert np.array_equal(got[hi], oracle.sw_batch(ss.seqs, ss.offsets, pairs[hi], S62, 11, 1))
+
+
+def test_long_pair_wait_limit_times_out_then_recovers(ctx):
+    """The whole-CTA long-pair kernel's one device wait (a column pass waiting for the rows
+    of the pass before it) is bounded.  With a limit of one poll the later passes cannot see
+    their predecessor's first 32 rows in time, so the call must return CM_ERR_TIMEOUT with
+    nothing written; with the default limit restored the same context gives the oracle's
+    cells."""
+    base = synth.proteome(4, family_size=2, stream=31)
+    ss = synth.long_tail(base, 2, 1, stream=31, lo=6000, hi=7000)
+    x, y = len(ss) - 2, len(ss) - 1
+    pairs = np.array([(x, y)], dtype=np.int32)
+    out = np.full((1, 5), -7, dtype=np.int32)
+    ctx.set_wait_limit(1)
+    try:
+        with pytest.raises(cm.CMError) as ei:
+            ctx.sw_cells_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1, out=out)
+        assert ei.value.code == -5
+        assert out.tolist() == [[-7] * 5]
+    finally:
+        ctx.set_wait_limit(0)
+    cells = ctx.sw_cells_batch(ss.seqs, ss.offsets, pairs, S62, 11, 1)
+    assert tuple(cells[0]) == oracle.sw_cells(ss[x], ss[y], S62, 11, 1)
+    assert cells[0][0] > 10000

@@ -4,7 +4,9 @@ It serves callers that cannot allocate device memory when they call (memory rese
 by another framework's allocator, or loops that must avoid cudaMalloc's synchronisation).  The
 test calls it through the C ABI (ctypes) twice in a row on the same inputs and requires both
 results to equal those of the ordinary entry point sw_cells_batch exactly (the tolerance of all
-integer tests here).  It also checks the size limit is rejected cleanly.  This file is named so
+integer tests here), and, since its one-thread-per-pair kernel shares no code with
+sw_cells_batch's, also the oracle's cells pair by pair.  It also checks the size limit and the
+binding's argument checks are rejected cleanly.  This file is named so
 pytest collects it last; it builds all of its own inputs, so it also passes alone in a fresh
 process.
 """
@@ -12,6 +14,8 @@ import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +43,7 @@ def test_noalloc_cells_match_sw_cells_batch_twice():
     ss, pairs, S = _inputs()
     ctx = cm.Context(0)
     want = ctx.sw_cells_batch(ss.seqs, ss.offsets, pairs, S, 11, 1)
+    ref = np.array([oracle.sw_cells(ss[x], ss[y], S, 11, 1) for x, y in pairs], dtype=np.int64)
 
     torch.cuda.set_device(0)
     dseqs = torch.from_numpy(ss.seqs).cuda()
@@ -56,6 +61,7 @@ def test_noalloc_cells_match_sw_cells_batch_twice():
             11, 1, ctypes.c_void_p(out.data_ptr()), stream, 0, err, 256)
         assert code == 0, err.value
         assert np.array_equal(out.cpu().numpy(), want), "call %d differs" % call
+        assert np.array_equal(out.cpu().numpy(), ref), "call %d differs from the oracle" % call
 
     # the binding wrapper gives the same result
     out = torch.empty((len(pairs), 5), dtype=torch.int32, device="cuda")
@@ -84,3 +90,34 @@ def test_noalloc_rejects_sequences_beyond_the_limit():
     want = cm.Context(0).sw_cells_batch(ss.seqs, ss.offsets, np.array([[1, 0]], np.int32),
                                         synth.BLOSUM62, 11, 1)
     assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_noalloc_binding_rejects_bad_arguments():
+    import torch
+    import paper_1908_10574_gb300 as cm
+    from paper_1908_10574_gb300 import synth
+
+    ss, pairs, S = _inputs()
+    dseqs = torch.from_numpy(ss.seqs).cuda()
+    doff = torch.from_numpy(ss.offsets).cuda()
+    dpairs = torch.from_numpy(pairs).cuda()
+    out = torch.full((len(pairs), 5), -7, dtype=torch.int32, device="cuda")
+    bad = [
+        dict(pairs=dpairs.long()),                                   # int64 pairs
+        dict(offsets=doff.int()),                                    # int32 offsets
+        dict(cells_out=out[:-1]),                                    # too few rows
+        dict(cells_out=torch.zeros((len(pairs), 10), dtype=torch.int32,
+                                   device="cuda")[:, ::2]),          # non-contiguous
+        dict(seqs=torch.from_numpy(ss.seqs)),                        # host tensor
+    ]
+    for kw in bad:
+        args = dict(seqs=dseqs, offsets=doff, pairs=dpairs, cells_out=out)
+        args.update(kw)
+        with pytest.raises((TypeError, ValueError)):
+            cm.sw_cells_batch_noalloc(args["seqs"], args["offsets"], args["pairs"], S, 11, 1,
+                                      args["cells_out"])
+    big = S.astype(np.int64).copy()
+    big[0, 0] = 300                                                  # does not fit int8
+    with pytest.raises(ValueError):
+        cm.sw_cells_batch_noalloc(dseqs, doff, dpairs, big, 11, 1, out)
+    assert (out == -7).all()
