@@ -302,7 +302,8 @@ def run_cluster_merge(args):
     ranker = None
     if args.ranker:
         ranker = train_ranker(ctx, args.train_seqs, args.train_pairs, args.epochs, args.keep,
-                              lr=args.lr, train_set=ss if args.transductive else None)
+                              lr=args.lr, train_set=ss if args.transductive else None,
+                              group=args.train_group)
         progress("ranker training", ranker)
     elif args.ranker_untrained is not None:
         # profiling the ranked path without training: standardised random weights, pruning at
@@ -395,33 +396,166 @@ def run_cluster_merge(args):
     print(json.dumps(out), flush=True)
 
 
-def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, train_set=None):
+# the learned-ranker recipe of the ClusterMerge comparison (training pairs drawn inside groups
+# of this many proteins, epochs, Adam learning rate, held-out positives kept by the pruning)
+CM_RECIPE = {"group": 128, "epochs": 40, "lr": 3e-4, "keep": 0.9995}
+
+
+def cm_comparison(ctx, n_seqs=100000, recipes=(CM_RECIPE,), clocks_dir=None, device=0):
+    """ClusterMerge of a proteome-shaped set (80 % in families of 8, 20 % singletons, lognormal
+    lengths): the plain merge, then for each learned-ranker recipe the whole learned path --
+    labelling 1M training pairs with the GPU SW path, training on the set itself, calibrating
+    the pruning threshold on held-out pairs, and the ranked merge -- each timed end to end;
+    recall of both against the GPU all-against-all of the set (Sec. 6.1), plus recall over the
+    planted within-family pairs.  Returns a dict with its own SM-clock record."""
+    ss = synth.proteome(n_seqs, family_size=8, singleton_frac=0.2, stream=3)
+    n = len(ss)
+    T, mT, mU = T_SIG, M_T, M_U
+    clk = ClockSampler(device, clocks_dir or tempfile.gettempdir())
+    clk.path = clk.path.replace(".csv", "_cm.csv")
+    clk.start()
+    t0 = time.perf_counter()
+    plain = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT, mU)
+    t_plain = time.perf_counter() - t0
+    progress("plain merge", {"seconds": t_plain})
+    learned = []
+    for rc in recipes:
+        t0 = time.perf_counter()
+        info = train_ranker(ctx, n, 1000000, rc["epochs"], rc["keep"], lr=rc["lr"], train_set=ss,
+                            group=rc["group"])
+        t_train = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ranked = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT,
+                                   mU, use_ranker=True, prune_logit=info["prune_logit"],
+                                   ranker_min_pairs=100000)
+        t_merge = time.perf_counter() - t0
+        learned.append((rc, info, t_train, t_merge, ranked))
+        progress("learned path", {"recipe": rc, "train_seconds": t_train, "merge_seconds": t_merge})
+    t0 = time.perf_counter()
+    truth = set()
+    parts = max(1, int(total_cells(ss) / 2e12))
+    for part in range(parts):
+        p, _ = ctx.sw_allpairs(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, part,
+                               parts, capacity=1 << 22)
+        truth.update(zip(p[:, 0].tolist(), p[:, 1].tolist()))
+    t_truth = time.perf_counter() - t0
+    clocks = clk.stop()
+    fp = family_pairs(ss.family)
+    sc = ctx.sw_score_batch(ss.seqs, ss.offsets, fp, synth.BLOSUM62, GAP_OPEN, GAP_EXT)
+    truth_f = fp[sc > T]
+
+    def recall(res):
+        found = set(zip(res["pairs"][:, 0].tolist(), res["pairs"][:, 1].tolist()))
+        return len(found & truth) / max(len(truth), 1)
+
+    def merge_stats(res):
+        st = res["stats"]
+        return {k: st[k] for k in ("rep_comparisons", "exchange_comparisons", "intra_comparisons",
+                                   "comparisons_scored", "full_merges", "exchanges", "rounds")}
+
+    out = {"workload": "ClusterMerge of %d synthetic proteins (80%% in 10,000 families of 8, 20%% "
+                       "singletons; lognormal lengths median 350 sigma 0.6 clipped 30-5000), "
+                       "BLOSUM62 11/1, T=%d, mT=%d, mU=%d" % (n, T, mT, mU),
+           "truth_pairs": len(truth), "all_pairs_seconds": t_truth,
+           "plain": {"seconds": t_plain, "recall": recall(plain),
+                     "family_recall": stratum_recall(plain["pairs"][:, :2], truth_f, n),
+                     "similar_pairs": len(plain["pairs"]), "clusters": len(plain["clusters"]),
+                     **merge_stats(plain)},
+           "learned": [], "clocks": clocks}
+    for rc, info, t_train, t_merge, ranked in learned:
+        out["learned"].append({
+            "recipe": rc, "seconds_total": t_train + t_merge, "seconds_merge": t_merge,
+            "seconds_training_path": t_train, "label_seconds": info["label_seconds"],
+            "train_seconds": info["train_seconds"], "heldout_auc": info["heldout_auc"],
+            "heldout_negatives_kept": info["heldout_negatives_kept"],
+            "recall": recall(ranked),
+            "family_recall": stratum_recall(ranked["pairs"][:, :2], truth_f, n),
+            "ranker_selected": ranked["stats"]["ranker_selected"],
+            "vs_plain_end_to_end": t_plain / (t_train + t_merge),
+            "vs_plain_merge_only": t_plain / t_merge, **merge_stats(ranked)})
+    return out
+
+
+def grouped_training_pairs(family, n_pairs, group, rng):
+    """Training pairs drawn inside groups of about `group` proteins: the planted families
+    (singletons count as families of one) are dealt whole, in random order, into consecutive
+    groups; each group gets a share of the pairs proportional to its size, half of them two
+    distinct members of one of its families (within-family), half two distinct proteins of
+    the group drawn uniformly (random).  Returns (pairs (n, 2) int32, group id per pair)."""
+    family = np.asarray(family)
+    order = np.argsort(family, kind="stable")
+    bounds = np.flatnonzero(np.diff(family[order])) + 1
+    fams = np.split(order, bounds)
+    fams = [fams[i] for i in rng.permutation(len(fams))]
+    groups, cur = [], []
+    for f in fams:
+        cur.append(f)
+        if sum(len(x) for x in cur) >= group:
+            groups.append(cur)
+            cur = []
+    if cur:
+        groups.append(cur)
+    n = len(family)
+    out, gid = [], []
+    for g, fl in enumerate(groups):
+        members = np.concatenate(fl)
+        k = max(2, int(round(n_pairs * len(members) / n)))
+        multi = [f for f in fl if len(f) > 1]
+        kpos = k // 2 if multi else 0
+        if kpos:
+            fi = rng.integers(0, len(multi), size=kpos)
+            pos = np.array([rng.choice(multi[i], 2, replace=False) for i in fi])
+        else:
+            pos = np.zeros((0, 2), np.int64)
+        a = rng.integers(0, len(members), size=k - kpos)
+        b = rng.integers(0, len(members) - 1, size=k - kpos)
+        b = np.where(b >= a, b + 1, b)
+        neg = np.stack([members[a], members[b]], 1)
+        out.append(np.concatenate([pos, neg]))
+        gid.append(np.full(k, g))
+    pairs = np.concatenate(out).astype(np.int32)
+    gid = np.concatenate(gid)
+    perm = rng.permutation(len(pairs))[:n_pairs]
+    return pairs[perm], gid[perm]
+
+
+def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, train_set=None,
+                 group=512):
     """Train the ranker on a synthetic proteome (an independent one, or `train_set` itself):
-    half within-family pairs, half random pairs, labelled [SW score > T] by the GPU path; 10 %
-    held out to calibrate the pruning threshold so that a fraction `keep` of held-out
-    positives survives."""
+    pairs drawn inside groups of about `group` proteins, half within-family and half random
+    (grouped_training_pairs), labelled [SW score > T] by the GPU path; 10 % held out to
+    calibrate the pruning threshold so that a fraction `keep` of held-out positives survives.
+    Each training step takes one group with all of its pairs (CM_TRAIN_COMPONENTS: the library
+    batches whole components of the pair graph), so every protein is embedded once per epoch."""
+    import paper_1908_10574_gb300 as cm
     tr = train_set if train_set is not None else \
         synth.proteome(n_train_seqs, family_size=8, singleton_frac=0.2, stream=seed)
     rng = np.random.default_rng(seed)
-    fam = tr.family
-    order = np.argsort(fam, kind="stable")
-    bounds = np.flatnonzero(np.diff(fam[order])) + 1
-    groups = [g for g in np.split(order, bounds) if len(g) > 1]
-    gi = rng.integers(0, len(groups), size=n_pairs // 2)
-    pos = np.array([rng.choice(groups[g], 2, replace=False) for g in gi])
-    neg = rng.integers(0, len(tr), size=(n_pairs - len(pos), 2))
-    pairs = np.concatenate([pos, neg]).astype(np.int32)
-    pairs = pairs[rng.permutation(len(pairs))]
+    if group > 0:
+        pairs, _ = grouped_training_pairs(tr.family, n_pairs, group, rng)
+    else:
+        # pairs over the whole set: half within-family, half uniformly random
+        fam = tr.family
+        order = np.argsort(fam, kind="stable")
+        bounds = np.flatnonzero(np.diff(fam[order])) + 1
+        groups = [g for g in np.split(order, bounds) if len(g) > 1]
+        gi = rng.integers(0, len(groups), size=n_pairs // 2)
+        pos = np.array([rng.choice(groups[g], 2, replace=False) for g in gi])
+        neg = rng.integers(0, len(tr), size=(n_pairs - len(pos), 2))
+        pairs = np.concatenate([pos, neg]).astype(np.int32)
+        pairs = pairs[rng.permutation(len(pairs))]
     t0 = time.perf_counter()
     sc = ctx.sw_score_batch(tr.seqs, tr.offsets, pairs, synth.BLOSUM62, GAP_OPEN, GAP_EXT)
     t_label = time.perf_counter() - t0
     y = (sc > T_SIG).astype(np.float32)
     cut = int(0.9 * len(pairs))
+    batch_pairs = int(1.5 * n_pairs * group / max(len(tr), 1)) + 64 if group > 0 else 256
     t0 = time.perf_counter()
     ctx.ranker_init(seed)
     ctx.ranker_standardize(tr.seqs, tr.offsets, max_sample=2048)
     loss = ctx.ranker_train(tr.seqs, tr.offsets, pairs[:cut], y[:cut], epochs=epochs,
-                            batch_pairs=256, lr=lr, seed=seed)
+                            batch_pairs=batch_pairs, lr=lr, seed=seed,
+                            flags=cm.CM_TRAIN_COMPONENTS if group > 0 else 0)
     t_train = time.perf_counter() - t0
     z = ctx.ranker_logits(tr.seqs, tr.offsets, pairs[cut:])
     yh = y[cut:]
@@ -431,8 +565,10 @@ def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, tra
     ranks[zo] = np.arange(1, len(z) + 1)
     npos = yh.sum()
     auc = float((ranks[yh == 1].sum() - npos * (npos + 1) / 2) / (npos * (len(yh) - npos)))
-    return {"train_seqs": len(tr), "transductive": train_set is not None, "train_pairs": int(cut), "heldout_pairs": int(len(pairs) - cut),
-            "positives": float(y.mean()), "epochs": epochs, "last_batch_loss": loss,
+    return {"train_seqs": len(tr), "transductive": train_set is not None,
+            "train_pairs": int(cut), "heldout_pairs": int(len(pairs) - cut),
+            "group": group, "batch_pairs": batch_pairs,
+            "positives": float(y.mean()), "epochs": epochs, "lr": lr, "last_batch_loss": loss,
             "label_seconds": t_label, "train_seconds": t_train, "heldout_auc": auc,
             "prune_logit": thr, "keep_heldout_positives": keep,
             "heldout_negatives_kept": float((z[yh == 0] >= thr).mean())}
@@ -471,6 +607,9 @@ def main():
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--keep", type=float, default=0.9995)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--train-group", type=int, default=512,
+                    help="cm: training pairs are drawn inside groups of this many proteins "
+                         "(0: over the whole set, trained in shuffled batches of 256 pairs)")
     ap.add_argument("--transductive", action="store_true",
                     help="cm: train the ranker on the set being clustered (as the 100k setup)")
     ap.add_argument("--min-pairs", type=int, default=100000,

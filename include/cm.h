@@ -60,6 +60,7 @@ extern "C" {
 #define CM_ASCII          0x2u  /* seqs holds ASCII letters (upper or lower case) */
 #define CM_GAP_BLAST      0x4u  /* gap of k residues costs open + k*extend */
 #define CM_FORCE_INT32    0x8u  /* score every pair on the int32 path (no int16x2 first pass) */
+#define CM_TRAIN_COMPONENTS 0x10u /* cm_ranker_train: batches hold whole components of the pair graph */
 
 typedef struct cm_ctx cm_ctx;
 
@@ -156,6 +157,29 @@ int sw_allpairs(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_
                 int64_t part, int64_t n_parts, int32_t *pairs_out, int32_t *scores_out,
                 int64_t capacity, int64_t *n_found, uint32_t flags);
 
+/* sw_align_batch -- one optimal local alignment per pair, for re-aligning the similar pairs a
+ * clustering reports (Sec. 6.1), as run-length operations.
+ *   cells_out:   5*n_pairs int32 as sw_cells_batch (score, i_start, i_end, j_start, j_end).
+ *   ops_offsets: n_pairs+1 int64; the runs of pair k are ops_out[ops_offsets[k] ..
+ *                ops_offsets[k+1]), none when its score is 0.
+ *   ops_out:     ops_capacity int32 runs, each (length << 2) | op from the alignment's start to
+ *                its end: op 0 = M (a residue of the first sequence aligned with one of the
+ *                second), 1 = I (a residue of the first sequence against a gap), 2 = D (a
+ *                residue of the second sequence against a gap).
+ *   n_ops:       total runs (host pointer, always host).
+ * The alignment spans exactly the cells: a[i_start..i_end] against b[j_start..j_end].  Inside
+ * that span it is the global affine alignment of the two substrings (same gap costs), which
+ * scores the local optimum; among equal-scoring ones the traceback from the end takes an
+ * aligned pair first, then I, then D, and a gap's opening before its extension.  If
+ * *n_ops > ops_capacity nothing is written and CM_ERR_CAPACITY is returned.  One GPU thread
+ * aligns one pair (a p x q byte matrix of choices per pair in device scratch): meant for the
+ * similar pairs of a clustering, not for all-against-all. */
+int sw_align_batch(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                   const int32_t *pairs, int64_t n_pairs, const int8_t *matrix,
+                   int32_t gap_open, int32_t gap_extend, int32_t *cells_out,
+                   int64_t *ops_offsets, int32_t *ops_out, int64_t ops_capacity,
+                   int64_t *n_ops, uint32_t flags);
+
 /* ---- ClusterMerge (Algorithm 1 Merge, Algorithm 2 BottomUpMerge, Sec. 4 transitivity) ---- */
 typedef struct {
     int32_t T;      /* significance: a pair is similar when its score > T (Sec. 3) */
@@ -230,7 +254,14 @@ int cm_ranker_load(cm_ctx *ctx, const char *path);
 int cm_ranker_loss_grad(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
                         const int32_t *pairs, const float *labels, int64_t n_pairs,
                         float *loss, float *grad, uint32_t flags);
-/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) over shuffled mini-batches of batch_pairs pairs */
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) over mini-batches of at most batch_pairs pairs,
+ * reshuffled every epoch (seeded by `seed`); the loss of a step is the mean BCE over its pairs.
+ * Each step embeds every distinct sequence of its batch once.  By default a batch is a chunk
+ * of the shuffled pair list.  With CM_TRAIN_COMPONENTS in flags a batch holds whole connected
+ * components of the pair graph (sequences as nodes, pairs as edges), as many as fit, and a
+ * component with more pairs is cut into chunks of batch_pairs: pairs drawn within groups of
+ * sequences then train one group per step with all of its pairs, each sequence embedded once
+ * per epoch.  The component order and the pairs inside each component are shuffled. */
 int cm_ranker_train(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
                     const int32_t *pairs, const float *labels, int64_t n_pairs, int32_t epochs,
                     int32_t batch_pairs, float lr, uint64_t seed, float *last_loss,

@@ -50,6 +50,8 @@ def _lib():
         lib.cm_oracle_sw.argtypes = [p, i64, p, i64, p, i64, i64, ctypes.c_int]
         lib.cm_oracle_sw_cells.restype = None
         lib.cm_oracle_sw_cells.argtypes = [p, i64, p, i64, p, i64, i64, ctypes.c_int, p]
+        lib.cm_oracle_sw_align.restype = i64
+        lib.cm_oracle_sw_align.argtypes = [p, i64, p, i64, p, i64, i64, ctypes.c_int, p, p, i64]
         lib.cm_oracle_sw_batch.restype = ctypes.c_int
         lib.cm_oracle_sw_batch.argtypes = [p, p, p, i64, p, i64, i64, ctypes.c_int, p,
                                            ctypes.c_int]
@@ -83,6 +85,31 @@ def sw_cells(a, b, S, gap_open, gap_extend, gap_mode=0):
     _lib().cm_oracle_sw_cells(a.ctypes.data, len(a), b.ctypes.data, len(b), S.ctypes.data,
                               int(gap_open), int(gap_extend), int(gap_mode), out.ctypes.data)
     return tuple(int(v) for v in out)
+
+
+OPS = "MID"
+
+
+def sw_align(a, b, S, gap_open, gap_extend, gap_mode=0):
+    """One optimal local alignment: (cells, ops) with cells as sw_cells and ops a list of
+    (run length, op) from start to end, op 'M' (a_i with b_j), 'I' (a_i against a gap) or 'D'
+    (b_j against a gap).  The span is sw_cells'; inside it the global affine alignment of the
+    two substrings, traced back from the end preferring M, then I, then D, and a gap's
+    opening over its extension."""
+    a, b, S = _codes(a), _codes(b), _matrix(S)
+    cells = np.zeros(5, dtype=np.int64)
+    cap = len(a) + len(b) + 1
+    ops = np.zeros(cap, dtype=np.int32)
+    k = _lib().cm_oracle_sw_align(a.ctypes.data, len(a), b.ctypes.data, len(b), S.ctypes.data,
+                                  int(gap_open), int(gap_extend), int(gap_mode),
+                                  cells.ctypes.data, ops.ctypes.data, cap)
+    assert k >= 0
+    return tuple(int(v) for v in cells), [(int(x) >> 2, OPS[int(x) & 3]) for x in ops[:k]]
+
+
+def cigar(ops):
+    """CIGAR text of run-length ops, e.g. [(3, 'M'), (1, 'I')] -> '3M1I'."""
+    return "".join("%d%s" % (n, op) for n, op in ops)
 
 
 def uncovered(a_len, b_len, cells):

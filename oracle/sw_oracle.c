@@ -88,6 +88,85 @@ void cm_oracle_sw_cells(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     out[4] = je;
 }
 
+/* One optimal local alignment as run-length operations (the alignment biologists re-inspect
+ * for the similar pairs, Sec. 6.1).  The alignment spans exactly the cells of
+ * cm_oracle_sw_cells: a[i_s..i_e] against b[j_s..j_e].  Inside that rectangle it is a global
+ * affine alignment of the two substrings (Gotoh recurrences; it scores the local optimum,
+ * since a global alignment of the span is a local alignment and the optimal local alignment
+ * is a global alignment of its span):
+ *   H(0,0) = 0;  H(0,j) = E(0,j) = -(g1 + (j-1)e);  H(i,0) = F(i,0) = -(g1 + (i-1)e)
+ *   E(i,j) = max(H(i,j-1) - g1, E(i,j-1) - e)    gap in a: b_j against '-'   (op D)
+ *   F(i,j) = max(H(i-1,j) - g1, F(i-1,j) - e)    gap in b: a_i against '-'   (op I)
+ *   H(i,j) = max(H(i-1,j-1) + S(a_i, b_j), F(i,j), E(i,j))                 (op M)
+ * Traceback from (p, q) in H.  Ties: H takes the aligned pair first, then F, then E; F and E
+ * take opening (from H) before extending.  Output: ops[k] = (run length << 2) | op, op 0 = M,
+ * 1 = I, 2 = D, from the start of the alignment to its end.  Returns the number of runs
+ * (0 when the score is 0), or -1 if max_ops is too small.  cells as cm_oracle_sw_cells. */
+int64_t cm_oracle_sw_align(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                           const int32_t *S, int64_t o, int64_t e, int gap_mode,
+                           int64_t *cells, int32_t *ops, int64_t max_ops)
+{
+    (void)m; (void)n;
+    cm_oracle_sw_cells(a, m, b, n, S, o, e, gap_mode, cells);
+    if (cells[0] == 0) return 0;
+    const int64_t g1 = (gap_mode == 0) ? o : o + e;
+    const uint8_t *A = a + cells[1] - 1, *B = b + cells[3] - 1;
+    const int64_t p = cells[2] - cells[1] + 1, q = cells[4] - cells[3] + 1;
+    const size_t W = (size_t)(q + 1), cnt = (size_t)(p + 1) * W;
+    int64_t *H = (int64_t *)malloc(sizeof(int64_t) * cnt);
+    int64_t *E = (int64_t *)malloc(sizeof(int64_t) * cnt);
+    int64_t *F = (int64_t *)malloc(sizeof(int64_t) * cnt);
+    H[0] = 0; E[0] = F[0] = NEG_INF;
+    for (int64_t j = 1; j <= q; j++) { H[j] = E[j] = -(g1 + (j - 1) * e); F[j] = NEG_INF; }
+    for (int64_t i = 1; i <= p; i++) {
+        H[i * W] = F[i * W] = -(g1 + (i - 1) * e);
+        E[i * W] = NEG_INF;
+        for (int64_t j = 1; j <= q; j++) {
+            E[i * W + j] = max64(H[i * W + j - 1] - g1, E[i * W + j - 1] - e);
+            F[i * W + j] = max64(H[(i - 1) * W + j] - g1, F[(i - 1) * W + j] - e);
+            int64_t h = H[(i - 1) * W + j - 1] + (int64_t)S[A[i - 1] * 20 + B[j - 1]];
+            h = max64(h, F[i * W + j]);
+            h = max64(h, E[i * W + j]);
+            H[i * W + j] = h;
+        }
+    }
+    /* reversed op sequence, one op per column of the alignment */
+    int8_t *rev = (int8_t *)malloc((size_t)(p + q));
+    int64_t len = 0, i = p, j = q;
+    int state = 0;                      /* 0 = H, 1 = F, 2 = E */
+    while (i > 0 || j > 0) {
+        if (i == 0) { rev[len++] = 2; j--; continue; }
+        if (j == 0) { rev[len++] = 1; i--; continue; }
+        if (state == 0) {
+            if (H[i * W + j] == H[(i - 1) * W + j - 1] + (int64_t)S[A[i - 1] * 20 + B[j - 1]]) {
+                rev[len++] = 0; i--; j--;
+            } else if (H[i * W + j] == F[i * W + j]) {
+                state = 1;
+            } else {
+                state = 2;
+            }
+        } else if (state == 1) {
+            rev[len++] = 1;
+            state = (F[i * W + j] == H[(i - 1) * W + j] - g1) ? 0 : 1;
+            i--;
+        } else {
+            rev[len++] = 2;
+            state = (E[i * W + j] == H[i * W + j - 1] - g1) ? 0 : 2;
+            j--;
+        }
+    }
+    int64_t nruns = 0;
+    for (int64_t k = len - 1; k >= 0; ) {
+        int64_t r = 1;
+        while (k - r >= 0 && rev[k - r] == rev[k]) r++;
+        if (nruns >= max_ops) { nruns = -1; break; }
+        ops[nruns++] = (int32_t)((r << 2) | rev[k]);
+        k -= r;
+    }
+    free(H); free(E); free(F); free(rev);
+    return nruns;
+}
+
 typedef struct {
     const uint8_t *seqs; const int64_t *off; const int32_t *pairs; int64_t npairs;
     const int32_t *S; int64_t o, e; int gap_mode; int64_t *out; int tid, nthreads;

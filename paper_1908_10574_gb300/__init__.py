@@ -14,10 +14,11 @@ import os
 import numpy as np
 
 from . import _lib as _L
-from ._lib import CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS  # noqa: F401
+from ._lib import (CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS,  # noqa: F401
+                   CM_TRAIN_COMPONENTS)
 
 __all__ = ["Context", "sw_score_batch", "sw_cells_batch", "sw_allpairs", "CMError",
-           "default_context", "sw_cells_batch_noalloc", "cluster_merge"]
+           "default_context", "sw_cells_batch_noalloc", "cluster_merge", "ops_to_cigar"]
 
 
 def _is_torch_cuda(x):
@@ -173,6 +174,34 @@ class Context:
                                                   int(gap_open), int(gap_extend), _ptr(out),
                                                   flags))
         return out
+
+    def sw_align_batch(self, seqs, offsets, pairs, matrix, gap_open, gap_extend, flags=0):
+        """One optimal local alignment per pair (see sw_align_batch in cm.h).  Host arrays
+        only.  Returns (cells (n, 5) int32, offsets (n + 1,) int64, runs int32); the runs of
+        pair k are runs[offsets[k]:offsets[k + 1]], each (length << 2) | op with op 0 = M,
+        1 = I, 2 = D (see ops_to_cigar)."""
+        seqs, offsets, matrix, pairs = self._inputs(seqs, offsets, matrix, pairs)
+        flags |= self._prep([seqs, offsets, matrix, pairs])
+        if flags & CM_DEVICE_PTRS:
+            raise TypeError("sw_align_batch takes host arrays")
+        n = int(offsets.shape[0]) - 1
+        npairs = int(pairs.shape[0])
+        cells = np.empty((npairs, 5), dtype=np.int32)
+        offs = np.empty(npairs + 1, dtype=np.int64)
+        total = ctypes.c_int64(0)
+        cap = 0
+        for _attempt in range(2):
+            runs = np.empty(max(cap, 1), dtype=np.int32)
+            code = _L.lib().sw_align_batch(self._h, _ptr(seqs), _ptr(offsets), n, _ptr(pairs),
+                                           npairs, _ptr(matrix), int(gap_open), int(gap_extend),
+                                           _ptr(cells), _ptr(offs), _ptr(runs), cap,
+                                           ctypes.byref(total), flags)
+            if code == _L.CM_ERR_CAPACITY:
+                cap = int(total.value)
+                continue
+            _L.check(self._h, code)
+            return cells, offs, runs[:int(total.value)]
+        raise CMError(_L.CM_ERR_CAPACITY, "capacity retry failed")
 
     def sw_allpairs(self, seqs, offsets, matrix, gap_open, gap_extend, T, part=0, n_parts=1,
                     flags=0, capacity=None, pairs_out=None, scores_out=None):
@@ -341,6 +370,11 @@ def sw_allpairs(seqs, offsets, matrix, gap_open, gap_extend, T, part=0, n_parts=
                 capacity=None):
     return default_context().sw_allpairs(seqs, offsets, matrix, gap_open, gap_extend, T, part,
                                          n_parts, flags, capacity)
+
+
+def ops_to_cigar(runs):
+    """CIGAR text of run-length alignment ops ((length << 2) | op, op 0 = M, 1 = I, 2 = D)."""
+    return "".join("%d%s" % (int(x) >> 2, "MID"[int(x) & 3]) for x in runs)
 
 
 def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, cells_out,

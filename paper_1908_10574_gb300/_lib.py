@@ -15,6 +15,7 @@ CM_DEVICE_PTRS = 0x1
 CM_ASCII = 0x2
 CM_GAP_BLAST = 0x4
 CM_FORCE_INT32 = 0x8
+CM_TRAIN_COMPONENTS = 0x10
 
 _ERRNAMES = {-1: "CM_ERR_ARG", -2: "CM_ERR_RESIDUE", -3: "CM_ERR_OOM", -4: "CM_ERR_CUDA",
              -5: "CM_ERR_TIMEOUT", -6: "CM_ERR_CAPACITY", -7: "CM_ERR_INTERNAL"}
@@ -84,6 +85,8 @@ def lib():
         "cm_reset_stats": (ctypes.c_int, [p]),
         "sw_score_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
         "sw_cells_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
+        "sw_align_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, p, p, i64,
+                                          ctypes.POINTER(i64), u32]),
         "sw_allpairs": (ctypes.c_int, [p, p, p, i32, p, i32, i32, i32, i64, i64, p, p, i64,
                                        ctypes.POINTER(i64), u32]),
         "cluster_merge": (ctypes.c_int, [p, p, p, i32, p, i32, i32, ctypes.POINTER(cm_params),

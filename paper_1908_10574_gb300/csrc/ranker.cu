@@ -15,8 +15,8 @@
 // conv9 is a width-9 "same" convolution.  A batch concatenates its sequences with kGap = 4
 // zero rows before, between and after them, so no output row ever reads another sequence.
 //
-// The convolutions run as implicit GEMMs on BF16 tensor cores with FP32 accumulation
-// (mma.sync m16n8k16, operands staged by cp.async double buffering and read with ldmatrix):
+// The convolutions run as implicit GEMMs on the 5th-generation tensor cores (tcgen05.mma,
+// BF16 operands staged by TMA, FP32 accumulators in tensor memory; csrc/ranker_tc.cuh):
 //   forward      C[r, n]        = sum_k sum_c X[r+k-4, c] * W[k][c][n]
 //   backward dX  C[r, c]        = sum_k sum_n dY[r+k-4, n] * W[8-k][c][n]   (flipped weights)
 //   backward dW  C[(k, c), n]   = sum_r X[r+k-4, c] * dY[r, n]             (split over rows)
@@ -30,6 +30,8 @@
 #include <cuda_bf16.h>
 
 #include "ctx.h"
+#include "ranker_tc.cuh"
+#include "train_batches.h"
 
 namespace cm {
 
@@ -87,208 +89,6 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// ---------------------------------------------------------------------------------------
-// Row-convolution GEMM (forward and backward-data).  One CTA = 128 rows x BN channels.
-enum Epi : int { kEpiRelu = 0, kEpiLinear = 1, kEpiGate = 2, kEpiF32 = 3 };
-
-constexpr int kBM = 128, kBK = 32, kAStr = kBK + 8;   // A tile row stride (halves)
-
-template <int CIN, int BN, int EPI>
-__global__ void __launch_bounds__(256) conv_rows_kernel(const bf16* __restrict__ X, int64_t R,
-                                                        const bf16* __restrict__ Wt,
-                                                        const float* __restrict__ bias,
-                                                        const int32_t* __restrict__ rowseq,
-                                                        const bf16* __restrict__ gate,
-                                                        bf16* __restrict__ out,
-                                                        float* __restrict__ out32)
-{
-    constexpr int WM = (BN == 128) ? 4 : 8, WN = 8 / WM;
-    constexpr int TM = kBM / WM, TN = BN / WN;          // warp tile
-    constexpr int MT = TM / 16, NT = TN / 8;
-    constexpr int BStr = BN + 8;
-    constexpr int KSTEPS = kTaps * (CIN / kBK);
-    __shared__ __align__(16) bf16 sA[2][kBM * kAStr];
-    __shared__ __align__(16) bf16 sB[2][kBK * BStr];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm0 = (warp % WM) * TM, wn0 = (warp / WM) * TN;
-    const int64_t row0 = (int64_t)blockIdx.x * kBM;
-
-    auto load = [&](int st, int s) {
-        const int k = s / (CIN / kBK), cb = (s % (CIN / kBK)) * kBK;
-        for (int id = tid; id < kBM * 4; id += 256) {
-            const int i = id >> 2, part = id & 3;
-            const int64_t src = row0 + i + k - 4;
-            const bool ok = src >= 0 && src < R;
-            const bf16* g = X + (ok ? src : 0) * CIN + cb + part * 8;
-            cp_async16(&sA[st][i * kAStr + part * 8], g, ok);
-        }
-        constexpr int CPR = BN / 8;                      // 16-byte chunks per B row
-        for (int id = tid; id < kBK * CPR; id += 256) {
-            const int kk = id / CPR, part = id % CPR;
-            const bf16* g = Wt + ((int64_t)(k * CIN + cb + kk)) * BN + part * 8;
-            cp_async16(&sB[st][kk * BStr + part * 8], g, true);
-        }
-        cp_commit();
-    };
-
-    float acc[MT][NT][4];
-#pragma unroll
-    for (int a = 0; a < MT; ++a)
-#pragma unroll
-        for (int b = 0; b < NT; ++b)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
-
-    load(0, 0);
-    for (int s = 0; s < KSTEPS; ++s) {
-        const int st = s & 1;
-        if (s + 1 < KSTEPS) { load(st ^ 1, s + 1); cp_wait1(); } else { cp_wait0(); }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < kBK; ks += 16) {
-            uint32_t af[MT][4];
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const bf16* p = &sA[st][(wm0 + mt * 16 + (lane & 15)) * kAStr + ks + (lane >> 4) * 8];
-                ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], p);
-            }
-#pragma unroll
-            for (int np = 0; np < NT / 2; ++np) {
-                uint32_t b0, b1, b2, b3;
-                const bf16* p = &sB[st][(ks + (lane & 7) + ((lane >> 3) & 1) * 8) * BStr +
-                                        wn0 + np * 16 + (lane >> 4) * 8];
-                ldsm_x4_t(b0, b1, b2, b3, p);
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    mma_bf16(acc[mt][2 * np], af[mt], b0, b1);
-                    mma_bf16(acc[mt][2 * np + 1], af[mt], b2, b3);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // epilogue
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int64_t r = row0 + wm0 + mt * 16 + g + hh * 8;
-            if (r >= R) continue;
-            const bool real = rowseq[r] >= 0;
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int n = wn0 + nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * hh], v1 = acc[mt][nt][2 * hh + 1];
-                if (EPI == kEpiRelu || EPI == kEpiLinear) {
-                    v0 += bias[n];
-                    v1 += bias[n + 1];
-                    if (EPI == kEpiRelu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
-                } else if (EPI == kEpiGate) {
-                    const __nv_bfloat162 gz = *reinterpret_cast<const __nv_bfloat162*>(gate + r * BN + n);
-                    if (!(__bfloat162float(gz.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(gz.y) > 0.f)) v1 = 0.f;
-                }
-                if (!real) { v0 = 0.f; v1 = 0.f; }
-                if (EPI == kEpiF32) {
-                    *reinterpret_cast<float2*>(out32 + r * BN + n) = make_float2(v0, v1);
-                } else {
-                    *reinterpret_cast<__nv_bfloat162*>(out + r * BN + n) = __floats2bfloat162_rn(v0, v1);
-                }
-            }
-        }
-}
-
-// Weight gradient: part[chunk][(k, c)][n] = sum over the chunk's rows r of X[r+k-4, c] * dY[r, n].
-// One CTA = a 128-wide slice of the (k, c) axis x all 128 n, over `rows_per_chunk` rows.
-template <int CIN>
-__global__ void __launch_bounds__(256) conv_wgrad_kernel(const bf16* __restrict__ X,
-                                                         const bf16* __restrict__ dY, int64_t R,
-                                                         int64_t rows_per_chunk,
-                                                         float* __restrict__ part, int MPAD)
-{
-    constexpr int Str = 128 + 8;
-    __shared__ __align__(16) bf16 sA[2][kBK * Str];     // [rows][m]
-    __shared__ __align__(16) bf16 sB[2][kBK * Str];     // [rows][n]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm0 = (warp % 4) * 32, wn0 = (warp / 4) * 64;
-    const int mtile = blockIdx.x;
-    const int64_t chunk = blockIdx.y;
-    const int64_t rbeg = chunk * rows_per_chunk;
-    const int64_t rend = min(R, rbeg + rows_per_chunk);
-    const int nsteps = (int)((rend - rbeg + kBK - 1) / kBK);
-
-    auto load = [&](int st, int s) {
-        const int64_t r0 = rbeg + (int64_t)s * kBK;
-        for (int id = tid; id < kBK * 16; id += 256) {
-            const int i = id >> 4, part16 = id & 15;
-            // A: column m = mtile*128 + part16*8 .. +8 -> tap k, channel c
-            const int m = mtile * 128 + part16 * 8;
-            const int k = m / CIN, c = m % CIN;
-            const int64_t rr = r0 + i;
-            const int64_t src = rr + k - 4;
-            const bool okA = k < kTaps && rr < rend && src >= 0 && src < R;
-            cp_async16(&sA[st][i * Str + part16 * 8], X + (okA ? src : 0) * CIN + (okA ? c : 0), okA);
-            const bool okB = rr < rend;
-            cp_async16(&sB[st][i * Str + part16 * 8], dY + (okB ? rr : 0) * kCh + part16 * 8, okB);
-        }
-        cp_commit();
-    };
-
-    float acc[2][8][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
-
-    if (nsteps > 0) load(0, 0);
-    for (int s = 0; s < nsteps; ++s) {
-        const int st = s & 1;
-        if (s + 1 < nsteps) { load(st ^ 1, s + 1); cp_wait1(); } else { cp_wait0(); }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < kBK; ks += 16) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const bf16* p = &sA[st][(ks + (lane & 7) + (lane >> 4) * 8) * Str + wm0 + mt * 16 +
-                                        ((lane >> 3) & 1) * 8];
-                ldsm_x4_t(af[mt][0], af[mt][1], af[mt][2], af[mt][3], p);
-            }
-#pragma unroll
-            for (int np = 0; np < 4; ++np) {
-                uint32_t b0, b1, b2, b3;
-                const bf16* p = &sB[st][(ks + (lane & 7) + ((lane >> 3) & 1) * 8) * Str + wn0 +
-                                        np * 16 + (lane >> 4) * 8];
-                ldsm_x4_t(b0, b1, b2, b3, p);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    mma_bf16(acc[mt][2 * np], af[mt], b0, b1);
-                    mma_bf16(acc[mt][2 * np + 1], af[mt], b2, b3);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    const int g = lane >> 2, t = lane & 3;
-    float* dst = part + chunk * (int64_t)MPAD * kCh;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int m = mtile * 128 + wm0 + mt * 16 + g + hh * 8;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int n = wn0 + nt * 8 + 2 * t;
-                *reinterpret_cast<float2*>(dst + (int64_t)m * kCh + n) =
-                    make_float2(acc[mt][nt][2 * hh], acc[mt][nt][2 * hh + 1]);
-            }
-        }
-}
-
 // sum the per-chunk partials into the gradient vector (first M rows of the padded tile)
 __global__ void reduce_parts_kernel(const float* __restrict__ part, int64_t nchunks, int MPAD,
                                     int M, float* __restrict__ grad)
@@ -298,15 +98,6 @@ __global__ void reduce_parts_kernel(const float* __restrict__ part, int64_t nchu
     float s = 0.f;
     for (int64_t c = 0; c < nchunks; ++c) s += part[c * (int64_t)MPAD * kCh + i];
     grad[i] += s;
-}
-
-// column sums of dY over rows (bias gradient); rows of padding are zero already
-__global__ void bias_grad_kernel(const bf16* __restrict__ dY, int64_t R, float* __restrict__ db)
-{
-    const int n = threadIdx.x;
-    float s = 0.f;
-    for (int64_t r = blockIdx.x; r < R; r += gridDim.x) s += __bfloat162float(dY[r * kCh + n]);
-    atomicAdd(&db[n], s);
 }
 
 __global__ void embed_fwd_kernel(const uint8_t* __restrict__ codes, int64_t R,
@@ -320,41 +111,40 @@ __global__ void embed_fwd_kernel(const uint8_t* __restrict__ codes, int64_t R,
     X0[i] = (code < 20) ? E[code * kEmb + c] : __float2bfloat16(0.f);
 }
 
-__global__ void embed_bwd_kernel(const uint8_t* __restrict__ codes, int64_t R,
-                                 const float* __restrict__ dX0, float* __restrict__ dE)
-{
-    __shared__ float h[20 * kEmb];
-    for (int i = threadIdx.x; i < 20 * kEmb; i += blockDim.x) h[i] = 0.f;
-    __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R * kEmb;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint8_t code = codes[i / kEmb];
-        if (code < 20) atomicAdd(&h[code * kEmb + (int)(i % kEmb)], dX0[i]);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 20 * kEmb; i += blockDim.x) atomicAdd(&dE[i], h[i]);
-}
-
-// v[s][n] = mean over the sequence's rows of Z3
-__global__ void pool_fwd_kernel(const bf16* __restrict__ Z3, const int64_t* __restrict__ srow,
-                                const int32_t* __restrict__ slen, float* __restrict__ v)
-{
-    const int s = blockIdx.x, n = threadIdx.x;
-    const int64_t r0 = srow[s];
-    const int L = slen[s];
-    float acc = 0.f;
-    for (int i = 0; i < L; ++i) acc += __bfloat162float(Z3[(r0 + i) * kCh + n]);
-    v[(int64_t)s * kCh + n] = L > 0 ? acc / (float)L : 0.f;
-}
-
+// dY3[r] = dv[s] / len(s) for the real rows r of sequence s, 0 for gap rows (the gradient of
+// the mean pooling); one thread per 8 channels of a row
 __global__ void pool_bwd_kernel(const float* __restrict__ dv, const int32_t* __restrict__ rowseq,
                                 const int32_t* __restrict__ slen, int64_t R, bf16* __restrict__ dZ)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= R * kCh) return;
-    const int32_t s = rowseq[i / kCh];
-    const int n = (int)(i % kCh);
-    dZ[i] = __float2bfloat16(s >= 0 ? dv[(int64_t)s * kCh + n] / (float)slen[s] : 0.f);
+    if (i >= R * (kCh / 8)) return;
+    const int64_t r = i / (kCh / 8);
+    const int c0 = (int)(i % (kCh / 8)) * 8;
+    const int32_t s = rowseq[r];
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (s >= 0) {
+        const float inv = 1.f / (float)slen[s];
+        const float4 a = *reinterpret_cast<const float4*>(dv + (int64_t)s * kCh + c0);
+        const float4 b = *reinterpret_cast<const float4*>(dv + (int64_t)s * kCh + c0 + 4);
+        const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const __nv_bfloat162 p = __floats2bfloat162_rn(f[2 * h] * inv, f[2 * h + 1] * inv);
+            w[h] = *reinterpret_cast<const uint32_t*>(&p);
+        }
+    }
+    *reinterpret_cast<uint4*>(dZ + r * kCh + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// db3[n] += sum over the batch's non-empty sequences of dv[s][n]
+__global__ void dv_sum_kernel(const float* __restrict__ dv, const int32_t* __restrict__ slen,
+                              int64_t ns, float* __restrict__ db)
+{
+    const int n = threadIdx.x;
+    float t = 0.f;
+    for (int64_t s = 0; s < ns; ++s)
+        if (slen[s] > 0) t += dv[s * kCh + n];
+    db[n] += t;
 }
 
 // one warp per pair: logit = alpha * cos(v_a, v_b) + beta, the loss and the gradients of v,
@@ -422,9 +212,26 @@ __global__ void gather_rows_kernel(const uint8_t* __restrict__ db, const int64_t
     }
 }
 
+// bf16 copies of one conv layer's weight W[k][c][n] (cin inputs) as the two K-major GEMM
+// operands: forward WF[n][k*cin + c] = W[k][c][n]; backward-data WB[c][k*128 + n] = W[8-k][c][n]
+__device__ __forceinline__ void store_weight_operands(int64_t i, int cin, bf16 b, bf16* WF,
+                                                      bf16* WB)
+{
+    const int k = (int)(i / ((int64_t)cin * kCh));
+    const int c = (int)((i / kCh) % cin);
+    const int n = (int)(i % kCh);
+    WF[(int64_t)n * kTaps * cin + k * cin + c] = b;
+    WB[(int64_t)c * kTaps * kCh + (kTaps - 1 - k) * kCh + n] = b;
+}
+
+struct Bf16Copies {
+    bf16 *E, *W1, *W1T, *W2, *W2T, *W3, *W3T;
+};
+
+// Adam step on every parameter, then the bf16 operand copies of the embedding and conv weights
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
                             float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
-                            float b1, float b2, float eps, float bc1, float bc2)
+                            float b1, float b2, float eps, float bc1, float bc2, Bf16Copies out)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -433,22 +240,21 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    w[i] = wi;
+    const bf16 b = __float2bfloat16(wi);
+    if (i < kOffW1) out.E[i - kOffE] = b;
+    else if (i < kOffB1) store_weight_operands(i - kOffW1, kEmb, b, out.W1, out.W1T);
+    else if (i >= kOffW2 && i < kOffB2) store_weight_operands(i - kOffW2, kCh, b, out.W2, out.W2T);
+    else if (i >= kOffW3 && i < kOffB3) store_weight_operands(i - kOffW3, kCh, b, out.W3, out.W3T);
 }
 
-// bf16 operand copies: W[k][c][n] as stored, and flipped-transposed WTF[k][n][c] = W[8-k][c][n]
-__global__ void cast_weights_kernel(const float* __restrict__ W, int cin, bf16* __restrict__ Wb,
-                                    bf16* __restrict__ WTF)
+// bf16 GEMM operands of a conv layer's W[k][c][n] (see store_weight_operands)
+__global__ void cast_weights_kernel(const float* __restrict__ W, int cin, bf16* __restrict__ WF,
+                                    bf16* __restrict__ WB)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)kTaps * cin * kCh;
-    if (i >= total) return;
-    const int k = (int)(i / ((int64_t)cin * kCh));
-    const int c = (int)((i / kCh) % cin);
-    const int n = (int)(i % kCh);
-    const bf16 b = __float2bfloat16(W[i]);
-    Wb[i] = b;
-    WTF[((int64_t)(kTaps - 1 - k) * kCh + n) * cin + c] = b;
+    if (i < (int64_t)kTaps * cin * kCh) store_weight_operands(i, cin, __float2bfloat16(W[i]), WF, WB);
 }
 
 __global__ void cast_kernel(const float* __restrict__ x, bf16* __restrict__ y, int64_t n)
@@ -551,17 +357,18 @@ struct Ranker {
     float* m = nullptr;
     float* v = nullptr;
     bf16* E = nullptr;
-    bf16* W1 = nullptr; bf16* W1T = nullptr;
+    bf16* W1 = nullptr; bf16* W1T = nullptr;   // forward / backward-data GEMM operands
     bf16* W2 = nullptr; bf16* W2T = nullptr;
     bf16* W3 = nullptr; bf16* W3T = nullptr;
+    int32_t* tc_err = nullptr;                  // error word of the tensor-core kernels
     int64_t step = 0;
     bool ready = false;
     // activation buffers (grown on demand)
-    DevBuf act[16];
+    DevBuf act[24];
 };
 
-enum ActId { A_CODES, A_ROWSEQ, A_X0, A_Z1, A_Z2, A_Z3, A_DZ, A_DY2, A_DX0, A_PART, A_V, A_DV,
-             A_SEQ, A_PIDX, A_Y, A_LOGIT };
+enum ActId { A_CODES, A_ROWSEQ, A_X0, A_Z1, A_Z2, A_DZ, A_DY2, A_PART, A_V, A_DV,
+             A_SEQ, A_PIDX, A_Y, A_LOGIT, A_EP_SID, A_EP_SROW, A_EP_SLEN, A_EP_PIDX, A_EP_Y };
 
 namespace {
 
@@ -599,7 +406,7 @@ void ranker_free(void* p)
     if (!K) return;
     cudaFree(K->params); cudaFree(K->grad); cudaFree(K->m); cudaFree(K->v);
     cudaFree(K->E); cudaFree(K->W1); cudaFree(K->W1T); cudaFree(K->W2); cudaFree(K->W2T);
-    cudaFree(K->W3); cudaFree(K->W3T);
+    cudaFree(K->W3); cudaFree(K->W3T); cudaFree(K->tc_err);
     for (auto& b : K->act) if (b.p) cudaFree(b.p);
     delete K;
 }
@@ -616,7 +423,8 @@ int get_ranker(cm_ctx* c, Ranker** out)
             {(void**)&K->params, nb}, {(void**)&K->grad, nb}, {(void**)&K->m, nb},
             {(void**)&K->v, nb}, {(void**)&K->E, 20 * kEmb * sizeof(bf16)},
             {(void**)&K->W1, w1}, {(void**)&K->W1T, w1}, {(void**)&K->W2, w2},
-            {(void**)&K->W2T, w2}, {(void**)&K->W3, w2}, {(void**)&K->W3T, w2}};
+            {(void**)&K->W2T, w2}, {(void**)&K->W3, w2}, {(void**)&K->W3T, w2},
+            {(void**)&K->tc_err, 256}};
         cudaError_t e = cudaSuccess;
         for (const auto& b : bufs)
             if (e == cudaSuccess) e = cudaMalloc(b.first, b.second);
@@ -626,6 +434,11 @@ int get_ranker(cm_ctx* c, Ranker** out)
             ranker_free(K);
             return fail(c, CM_ERR_OOM, std::string("device allocation of the ranker failed: ") +
                                            cudaGetErrorString(e));
+        }
+        e = cudaMemset(K->tc_err, 0, 256);
+        if (e != cudaSuccess) {
+            ranker_free(K);
+            return fail(c, CM_ERR_CUDA, std::string("cudaMemset failed: ") + cudaGetErrorString(e));
         }
         c->ranker = K;
         c->ranker_free = ranker_free;
@@ -671,20 +484,81 @@ void layout(const Prepared& P, const int32_t* ids, int64_t n, Batch& B)
     B.R = r;
 }
 
-// forward over a batch; leaves X0, Z1, Z2, Z3 and the pooled vectors V on the device
-int forward(cm_ctx* c, const Prepared& P, Ranker* K, const Batch& B, float** V_out)
+// One tensor-core convolution launch (csrc/ranker_tc.cuh): X is R x CIN bf16, Wk the layer's
+// NOUT x 9*CIN K-major operand; tensor maps are encoded on the host for these buffers.
+template <int CIN, int NOUT, int EPI>
+int conv_tc(cm_ctx* c, Ranker* K, const bf16* X, int64_t R, const bf16* Wk, const ConvEpi& ep)
+{
+    using C = tc::ConvCfg<CIN, NOUT>;
+    CUtensorMap ta, tb;
+    CUDA_TRY(tc::make_tmap_bf16(&ta, X, CIN, (uint64_t)R, C::BK, tc::kTcRows));
+    CUDA_TRY(tc::make_tmap_bf16(&tb, Wk, kTaps * CIN, NOUT, C::BK, NOUT));
+    auto kern = tc::conv_tc_kernel<CIN, NOUT, EPI>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    kern<<<blocks_for(R, tc::kTcRows), 128, C::SMEM, c->stream>>>(ta, tb, R, ep, K->tc_err);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 1;
+    return CM_OK;
+}
+
+// the tensor-core kernels' error word (a bounded wait gave up): reported and cleared
+int check_tc(cm_ctx* c, Ranker* K)
+{
+    int32_t e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, K->tc_err, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (e) {
+        CUDA_TRY(cudaMemsetAsync(K->tc_err, 0, 4, c->stream));
+        return fail(c, CM_ERR_TIMEOUT, "a tensor-core GEMM's bounded wait gave up");
+    }
+    return CM_OK;
+}
+
+// forward over a batch whose layout (sequence ids, first rows, lengths; R rows) is on the
+// device; leaves X0, Z1, Z2, Z3 and the pooled vectors V on the device
+int forward_dev(cm_ctx* c, const Prepared& P, Ranker* K, const int32_t* d_sid,
+                const int64_t* d_srow, const int32_t* d_slen, int64_t ns, int64_t R, float** V_out)
 {
     const cudaStream_t st = c->stream;
-    const int64_t R = B.R, ns = (int64_t)B.sid.size();
-    uint8_t* codes; int32_t* rowseq; bf16 *X0, *Z1, *Z2, *Z3; float* V;
-    int32_t* seqinfo;
+    uint8_t* codes; int32_t* rowseq; bf16 *X0, *Z1, *Z2; float* V;
     AENSURE(A_CODES, R, codes);
     AENSURE(A_ROWSEQ, R * 4, rowseq);
     AENSURE(A_X0, R * kEmb * 2, X0);
     AENSURE(A_Z1, R * kCh * 2, Z1);
     AENSURE(A_Z2, R * kCh * 2, Z2);
-    AENSURE(A_Z3, R * kCh * 2, Z3);
     AENSURE(A_V, ns * kCh * 4, V);
+    int r;
+    CUDA_TRY(cudaMemsetAsync(codes, 0xff, R, st));
+    CUDA_TRY(cudaMemsetAsync(rowseq, 0xff, R * 4, st));
+    CUDA_TRY(cudaMemsetAsync(V, 0, ns * kCh * 4, st));
+    gather_rows_kernel<<<(unsigned)ns, 128, 0, st>>>(P.db, P.off, d_sid, d_srow, d_slen, (int32_t)ns,
+                                                     codes, rowseq);
+    embed_fwd_kernel<<<blocks_for(R * kEmb, 256), 256, 0, st>>>(codes, R, K->E, X0);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 2;
+    ConvEpi ep{};
+    ep.rowseq = rowseq;
+    ep.bias = K->params + kOffB1;
+    ep.out = Z1;
+    if ((r = conv_tc<kEmb, kCh, kEpiRelu>(c, K, X0, R, K->W1, ep))) return r;
+    ep.bias = K->params + kOffB2;
+    ep.out = Z2;
+    if ((r = conv_tc<kCh, kCh, kEpiRelu>(c, K, Z1, R, K->W2, ep))) return r;
+    // layer 3 is pooled in its epilogue: v = mean over a sequence's rows of conv(Z2) + b3
+    ep.bias = K->params + kOffB3;
+    ep.out = nullptr;
+    ep.slen = d_slen;
+    ep.acc = V;
+    if ((r = conv_tc<kCh, kCh, kEpiPool>(c, K, Z2, R, K->W3, ep))) return r;
+    *V_out = V;
+    return CM_OK;
+}
+
+// forward over a batch laid out on the host
+int forward(cm_ctx* c, const Prepared& P, Ranker* K, const Batch& B, float** V_out)
+{
+    const int64_t ns = (int64_t)B.sid.size();
+    int32_t* seqinfo;
     AENSURE(A_SEQ, ns * 16 + 64, seqinfo);
     int32_t* d_sid = seqinfo;
     int64_t* d_srow = reinterpret_cast<int64_t*>(seqinfo + ((ns + 1) & ~1LL));
@@ -693,68 +567,119 @@ int forward(cm_ctx* c, const Prepared& P, Ranker* K, const Batch& B, float** V_o
     if ((r = copy_in(c, d_sid, B.sid.data(), ns * 4, false))) return r;
     if ((r = copy_in(c, d_srow, B.srow.data(), ns * 8, false))) return r;
     if ((r = copy_in(c, d_slen, B.slen.data(), ns * 4, false))) return r;
-    CUDA_TRY(cudaMemsetAsync(codes, 0xff, R, st));
-    CUDA_TRY(cudaMemsetAsync(rowseq, 0xff, R * 4, st));
-    gather_rows_kernel<<<(unsigned)ns, 128, 0, st>>>(P.db, P.off, d_sid, d_srow, d_slen, (int32_t)ns,
-                                                     codes, rowseq);
-    embed_fwd_kernel<<<blocks_for(R * kEmb, 256), 256, 0, st>>>(codes, R, K->E, X0);
-    const unsigned g = blocks_for(R, kBM);
-    conv_rows_kernel<kEmb, kCh, kEpiRelu><<<g, 256, 0, st>>>(X0, R, K->W1, K->params + kOffB1,
-                                                             rowseq, nullptr, Z1, nullptr);
-    conv_rows_kernel<kCh, kCh, kEpiRelu><<<g, 256, 0, st>>>(Z1, R, K->W2, K->params + kOffB2,
-                                                            rowseq, nullptr, Z2, nullptr);
-    conv_rows_kernel<kCh, kCh, kEpiLinear><<<g, 256, 0, st>>>(Z2, R, K->W3, K->params + kOffB3,
-                                                              rowseq, nullptr, Z3, nullptr);
-    pool_fwd_kernel<<<(unsigned)ns, kCh, 0, st>>>(Z3, d_srow, d_slen, V);
-    CUDA_TRY(cudaGetLastError());
-    c->stats.launches += 6;
-    *V_out = V;
-    return CM_OK;
+    return forward_dev(c, P, K, d_sid, d_srow, d_slen, ns, B.R, V_out);
 }
 
+// weight gradient of a conv layer on the tensor cores: the rows are cut into chunks so that
+// the grid (m-tiles x chunks) fills about two CTAs per SM; the chunks' partial tiles are
+// summed in a second kernel (deterministic)
 template <int CIN>
 int wgrad(cm_ctx* c, Ranker* K, const bf16* X, const bf16* dY, int64_t R, float* dW)
 {
+    using C = tc::WgradCfg<CIN>;
     const int M = kTaps * CIN;
-    const int mtiles = (M + 127) / 128, MPAD = mtiles * 128;
-    const int64_t rpc = 4096;
-    const int64_t nch = std::max<int64_t>(1, (R + rpc - 1) / rpc);
+    const int mtiles = C::MTILES, MPAD = mtiles * 128;
+    const int64_t want = std::max<int64_t>(1, (2 * (int64_t)c->num_sms + mtiles - 1) / mtiles);
+    const int64_t steps = (R + C::BKR - 1) / C::BKR;
+    const int64_t rpc = ((steps + want - 1) / want) * C::BKR;
+    const int64_t nch = (R + rpc - 1) / rpc;
     float* part;
     AENSURE(A_PART, nch * MPAD * kCh * 4, part);
-    dim3 grid(mtiles, (unsigned)nch);
-    conv_wgrad_kernel<CIN><<<grid, 256, 0, c->stream>>>(X, dY, R, rpc, part, MPAD);
+    CUtensorMap tx, td;
+    CUDA_TRY(tc::make_tmap_bf16(&tx, X, CIN, (uint64_t)R, C::CW, C::BKR));
+    CUDA_TRY(tc::make_tmap_bf16(&td, dY, kCh, (uint64_t)R, 64, C::BKR));
+    auto kern = tc::wgrad_tc_kernel<CIN>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    kern<<<dim3(mtiles, (unsigned)nch), 128, C::SMEM, c->stream>>>(tx, td, rpc, part, MPAD,
+                                                                   K->tc_err);
     reduce_parts_kernel<<<blocks_for((int64_t)M * kCh, 256), 256, 0, c->stream>>>(part, nch, MPAD, M, dW);
     CUDA_TRY(cudaGetLastError());
     c->stats.launches += 2;
     return CM_OK;
 }
 
-// loss and gradient (accumulated into K->grad, which the caller zeroes) of a batch of pairs
-int loss_grad(cm_ctx* c, const Prepared& P, Ranker* K, const int32_t* pairs, const float* labels,
-              int64_t npairs, float* loss_out)
+// Training batches packed for the device: per batch its distinct sequences (in order of first
+// appearance) with their first rows and lengths (rows relative to the batch, kGap zero rows
+// around each), the pairs as indices into that list, and the labels.
+struct Packed {
+    std::vector<int32_t> sid, slen, pidx;
+    std::vector<int64_t> srow;
+    std::vector<float> y;
+    std::vector<int64_t> seq_off{0}, pair_off{0}, rows;
+    std::vector<int32_t> stamp, local;   // per sequence: last batch that listed it, its index
+};
+
+void pack_batch(const Prepared& P, int32_t n_seqs, const int32_t* pairs, const float* labels,
+                const int64_t* idx, int64_t n, Packed& B)
+{
+    if ((int64_t)B.stamp.size() != n_seqs) {
+        B.stamp.assign((size_t)n_seqs, -1);
+        B.local.assign((size_t)n_seqs, 0);
+    }
+    const int32_t bid = (int32_t)B.rows.size();
+    const size_t s0 = B.sid.size();
+    int64_t r = kGap;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t k = idx ? idx[i] : i;
+        for (int h = 0; h < 2; ++h) {
+            const int32_t q = pairs[2 * k + h];
+            if (B.stamp[q] != bid) {
+                B.stamp[q] = bid;
+                B.local[q] = (int32_t)(B.sid.size() - s0);
+                B.sid.push_back(q);
+                B.srow.push_back(r);
+                B.slen.push_back((int32_t)P.len(q));
+                r += P.len(q) + kGap;
+            }
+            B.pidx.push_back(B.local[q]);
+        }
+        B.y.push_back(labels[k]);
+    }
+    B.rows.push_back(r);
+    B.seq_off.push_back((int64_t)B.sid.size());
+    B.pair_off.push_back((int64_t)B.y.size());
+}
+
+// upload every packed batch's arrays (one copy each)
+struct PackedDev {
+    int32_t *sid, *slen, *pidx;
+    int64_t* srow;
+    float* y;
+};
+
+int upload_packed(cm_ctx* c, Ranker* K, const Packed& B, PackedDev& D)
+{
+    const int64_t ns = (int64_t)B.sid.size(), np = (int64_t)B.y.size();
+    AENSURE(A_EP_SID, ns * 4, D.sid);
+    AENSURE(A_EP_SLEN, ns * 4, D.slen);
+    AENSURE(A_EP_SROW, ns * 8, D.srow);
+    AENSURE(A_EP_PIDX, np * 8, D.pidx);
+    AENSURE(A_EP_Y, np * 4 + 64, D.y);
+    int r;
+    if ((r = copy_in(c, D.sid, B.sid.data(), ns * 4, false))) return r;
+    if ((r = copy_in(c, D.slen, B.slen.data(), ns * 4, false))) return r;
+    if ((r = copy_in(c, D.srow, B.srow.data(), ns * 8, false))) return r;
+    if ((r = copy_in(c, D.pidx, B.pidx.data(), np * 8, false))) return r;
+    return copy_in(c, D.y, B.y.data(), np * 4, false);
+}
+
+// loss and gradient (accumulated into K->grad, which the caller zeroes) of packed batch b
+int loss_grad_packed(cm_ctx* c, const Prepared& P, Ranker* K, const Packed& B, const PackedDev& D,
+                     size_t b, float* loss_out)
 {
     const cudaStream_t st = c->stream;
-    // distinct sequences of the batch
-    std::vector<int32_t> ids(pairs, pairs + 2 * npairs);
-    std::vector<int32_t> uniq = ids;
-    std::sort(uniq.begin(), uniq.end());
-    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
-    std::vector<int32_t> pidx((size_t)npairs * 2);
-    for (int64_t i = 0; i < 2 * npairs; ++i)
-        pidx[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), ids[i]) - uniq.begin());
-    Batch B;
-    layout(P, uniq.data(), (int64_t)uniq.size(), B);
+    const int64_t so = B.seq_off[b], ns = B.seq_off[b + 1] - so;
+    const int64_t po = B.pair_off[b], npairs = B.pair_off[b + 1] - po;
+    const int64_t R = B.rows[b];
+    const int32_t* d_slen = D.slen + so;
     float* V;
-    int r = forward(c, P, K, B, &V);
+    int r = forward_dev(c, P, K, D.sid + so, D.srow + so, d_slen, ns, R, &V);
     if (r) return r;
-    const int64_t R = B.R, ns = (int64_t)uniq.size();
-    int32_t* d_pidx; float *d_y, *dv, *d_loss;
-    AENSURE(A_PIDX, npairs * 8, d_pidx);
-    AENSURE(A_Y, npairs * 4 + 64, d_y);
+    const int32_t* d_pidx = D.pidx + 2 * po;
+    const float* d_y = D.y + po;
+    float *dv, *d_loss;
     AENSURE(A_DV, ns * kCh * 4, dv);
-    d_loss = d_y + ((npairs + 15) & ~15LL);
-    if ((r = copy_in(c, d_pidx, pidx.data(), npairs * 8, false))) return r;
-    if ((r = copy_in(c, d_y, labels, npairs * 4, false))) return r;
+    AENSURE(A_LOGIT, 64, d_loss);
     CUDA_TRY(cudaMemsetAsync(dv, 0, ns * kCh * 4, st));
     CUDA_TRY(cudaMemsetAsync(d_loss, 0, 4, st));
     head_kernel<<<blocks_for(npairs * 32, 256), 256, 0, st>>>(V, d_pidx, d_y, (int32_t)npairs,
@@ -765,37 +690,38 @@ int loss_grad(cm_ctx* c, const Prepared& P, Ranker* K, const int32_t* pairs, con
     bf16* X0 = (bf16*)K->act[A_X0].p;
     bf16* Z1 = (bf16*)K->act[A_Z1].p;
     bf16* Z2 = (bf16*)K->act[A_Z2].p;
-    bf16 *dZ, *dY2; float* dX0;
+    bf16 *dZ, *dY2;
     AENSURE(A_DZ, R * kCh * 2, dZ);
     AENSURE(A_DY2, R * kCh * 2, dY2);
-    AENSURE(A_DX0, R * kEmb * 4, dX0);
-    int32_t* d_slen = reinterpret_cast<int32_t*>(
-        reinterpret_cast<int64_t*>((int32_t*)K->act[A_SEQ].p + ((ns + 1) & ~1LL)) + ns);
-    pool_bwd_kernel<<<blocks_for(R * kCh, 256), 256, 0, st>>>(dv, rowseq, d_slen, R, dZ);   // dY3
-    const unsigned g = blocks_for(R, kBM);
-    const unsigned gb = (unsigned)std::min<int64_t>(R, 1024);
-    // layer 3 (linear)
-    bias_grad_kernel<<<gb, kCh, 0, st>>>(dZ, R, K->grad + kOffB3);
+    pool_bwd_kernel<<<blocks_for(R * (kCh / 8), 256), 256, 0, st>>>(dv, rowseq, d_slen, R, dZ);  // dY3
+    // b3's gradient: every real row of a sequence carries dv / len, so the rows sum to dv
+    dv_sum_kernel<<<1, kCh, 0, st>>>(dv, d_slen, ns, K->grad + kOffB3);
+    c->stats.launches += 2;
+    ConvEpi ep{};
+    ep.rowseq = rowseq;
+    // layer 3 (linear): W3's gradient, then dY2 = gate(Z2) * conv^T(dY3) with b2's gradient
     if ((r = wgrad<kCh>(c, K, Z2, dZ, R, K->grad + kOffW3))) return r;
-    conv_rows_kernel<kCh, kCh, kEpiGate><<<g, 256, 0, st>>>(dZ, R, K->W3T, nullptr, rowseq, Z2,
-                                                            dY2, nullptr);           // dY2
-    // layer 2
-    bias_grad_kernel<<<gb, kCh, 0, st>>>(dY2, R, K->grad + kOffB2);
+    ep.gate = Z2;
+    ep.out = dY2;
+    ep.acc = K->grad + kOffB2;
+    if ((r = conv_tc<kCh, kCh, kEpiGate>(c, K, dZ, R, K->W3T, ep))) return r;
+    // layer 2: W2's gradient, then dY1 = gate(Z1) * conv^T(dY2) with b1's gradient
     if ((r = wgrad<kCh>(c, K, Z1, dY2, R, K->grad + kOffW2))) return r;
-    conv_rows_kernel<kCh, kCh, kEpiGate><<<g, 256, 0, st>>>(dY2, R, K->W2T, nullptr, rowseq, Z1,
-                                                            dZ, nullptr);            // dY1
-    // layer 1
-    bias_grad_kernel<<<gb, kCh, 0, st>>>(dZ, R, K->grad + kOffB1);
+    ep.gate = Z1;
+    ep.out = dZ;
+    ep.acc = K->grad + kOffB1;
+    if ((r = conv_tc<kCh, kCh, kEpiGate>(c, K, dY2, R, K->W2T, ep))) return r;
+    // layer 1: W1's gradient, then the embedding table's gradient from conv^T(dY1)
     if ((r = wgrad<kEmb>(c, K, X0, dZ, R, K->grad + kOffW1))) return r;
-    conv_rows_kernel<kCh, kEmb, kEpiF32><<<g, 256, 0, st>>>(dZ, R, K->W1T, nullptr, rowseq,
-                                                            nullptr, nullptr, dX0);
-    embed_bwd_kernel<<<std::min<unsigned>(blocks_for(R * kEmb, 256), 1024), 256, 0, st>>>(
-        codes, R, dX0, K->grad + kOffE);
-    CUDA_TRY(cudaGetLastError());
-    c->stats.launches += 12;
+    ep.gate = nullptr;
+    ep.out = nullptr;
+    ep.codes = codes;
+    ep.acc = K->grad + kOffE;
+    if ((r = conv_tc<kCh, kEmb, kEpiEmbed>(c, K, dZ, R, K->W1T, ep))) return r;
     if (loss_out) {
         CUDA_TRY(cudaMemcpyAsync(loss_out, d_loss, 4, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        if ((r = check_tc(c, K))) return r;
     }
     return CM_OK;
 }
@@ -825,7 +751,7 @@ int ranker_embed_device(cm_ctx* c, const Prepared& P, const int32_t* ids, int64_
                                  c->stream));
         i = j;
     }
-    return CM_OK;
+    return check_tc(c, K);
 }
 
 int ranker_alpha_beta(cm_ctx* c, float* ab)
@@ -1020,7 +946,11 @@ int cm_ranker_loss_grad(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, 
     if ((r = get_ranker(c, &K))) return r;
     if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters");
     CUDA_TRY(cudaMemsetAsync(K->grad, 0, kNumParams * 4, c->stream));
-    if ((r = loss_grad(c, P, K, pairs, labels, n_pairs, loss))) return r;
+    Packed B;
+    pack_batch(P, n_seqs, pairs, labels, nullptr, n_pairs, B);
+    PackedDev D;
+    if ((r = upload_packed(c, K, B, D))) return r;
+    if ((r = loss_grad_packed(c, P, K, B, D, 0, loss))) return r;
     if (grad) CUDA_TRY(cudaMemcpy(grad, K->grad, kNumParams * 4, cudaMemcpyDeviceToHost));
     return CM_OK;
 }
@@ -1042,37 +972,40 @@ int cm_ranker_train(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int3
     Ranker* K;
     if ((r = get_ranker(c, &K))) return r;
     if (!K->ready) return fail(c, CM_ERR_ARG, "ranker has no parameters (call cm_ranker_init)");
-    std::vector<int64_t> order((size_t)n_pairs);
-    std::iota(order.begin(), order.end(), 0);
+    // mini-batches (csrc/train_batches.h): shuffled chunks, or with CM_TRAIN_COMPONENTS whole
+    // components of the pair graph; a step embeds each distinct sequence of its batch once
+    const TrainComponents comps = (flags & CM_TRAIN_COMPONENTS)
+                                      ? train_components(pairs, n_pairs, n_seqs)
+                                      : train_one_component(n_pairs);
     std::mt19937_64 g(seed);
-    std::vector<int32_t> bp;
-    std::vector<float> by;
+    std::vector<int64_t> order, bounds;
     float loss = 0.f;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const Bf16Copies copies{K->E, K->W1, K->W1T, K->W2, K->W2T, K->W3, K->W3T};
     for (int ep = 0; ep < epochs; ++ep) {
-        std::shuffle(order.begin(), order.end(), g);
-        for (int64_t s = 0; s < n_pairs; s += batch_pairs) {
-            const int64_t e = std::min<int64_t>(n_pairs, s + batch_pairs);
-            bp.resize((size_t)(e - s) * 2);
-            by.resize((size_t)(e - s));
-            for (int64_t i = s; i < e; ++i) {
-                bp[2 * (i - s)] = pairs[2 * order[i]];
-                bp[2 * (i - s) + 1] = pairs[2 * order[i] + 1];
-                by[i - s] = labels[order[i]];
-            }
+        // the whole epoch's batches go to the device in one copy per array
+        train_epoch_batches(comps, batch_pairs, g, order, bounds);
+        const int64_t nb = (int64_t)bounds.size() - 1;
+        Packed B;
+        for (int64_t bi = 0; bi < nb; ++bi)
+            pack_batch(P, n_seqs, pairs, labels, order.data() + bounds[bi],
+                       bounds[bi + 1] - bounds[bi], B);
+        PackedDev D;
+        if ((r = upload_packed(c, K, B, D))) return r;
+        for (int64_t bi = 0; bi < nb; ++bi) {
             CUDA_TRY(cudaMemsetAsync(K->grad, 0, kNumParams * 4, c->stream));
-            const bool last = (ep == epochs - 1) && (e == n_pairs);
-            if ((r = loss_grad(c, P, K, bp.data(), by.data(), e - s, last ? &loss : nullptr))) return r;
+            const bool last = (ep == epochs - 1) && (bi == nb - 1);
+            if ((r = loss_grad_packed(c, P, K, B, D, (size_t)bi, last ? &loss : nullptr))) return r;
             ++K->step;
             const float bc1 = 1.f - std::pow(b1, (float)K->step), bc2 = 1.f - std::pow(b2, (float)K->step);
             adam_kernel<<<blocks_for(kNumParams, 256), 256, 0, c->stream>>>(
-                K->params, K->grad, K->m, K->v, kNumParams, lr, b1, b2, eps, bc1, bc2);
+                K->params, K->grad, K->m, K->v, kNumParams, lr, b1, b2, eps, bc1, bc2, copies);
             CUDA_TRY(cudaGetLastError());
             c->stats.launches += 1;
-            if ((r = refresh_bf16(c, K))) return r;
         }
     }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if ((r = check_tc(c, K))) return r;
     if (last_loss) *last_loss = loss;
     return CM_OK;
 }

@@ -1,0 +1,367 @@
+// The ranker's width-9 convolutions as implicit GEMMs on the 5th-generation tensor cores
+// (tcgen05.mma, BF16 operands, FP32 accumulator in tensor memory).  Rows are the residues of
+// a batch's concatenated sequences (with zero gap rows between them), channels are contiguous.
+//
+// conv_tc_kernel<CIN, NOUT, EPI>: out[r, n] = sum_t sum_c X[r + t - 4, c] * Wk[n, t*CIN + c]
+//   (forward: Wk[n, t*CIN + c] = W[t][c][n]; backward-data: X = dY, Wk[c, t*128 + n] =
+//   W[8-t][c][n]).  One CTA computes 128 rows x NOUT channels: K runs over the 9 taps x CIN
+//   channels in stages of BK channels; a stage's A tile is the 128 rows starting at
+//   r0 + t - 4, loaded by TMA straight from the activation matrix (rows before 0 or past the
+//   end come back as zeros), and its B tile the matching BK columns of Wk.  Warp 0 issues the
+//   TMA loads, warp 1 the MMAs (one thread each, STAGES-deep ring of stages on mbarriers),
+//   then all four warps read the accumulator back (warp w owns rows 32w .. 32w + 31 = TMEM
+//   lanes) and apply the epilogue.
+// wgrad_tc_kernel<CIN>: part[chunk][m = t*CIN + c][n] = sum over the chunk's rows r of
+//   X[r + t - 4, c] * dY[r, n] -- a GEMM whose K runs over rows.  Both operands are read
+//   MN-major (channels contiguous, one row per K index), so the tap shift stays on the row
+//   coordinate of the TMA load.  One CTA = 128 values of m (one tap of 128 channels, or four
+//   taps of 32) x 128 n, over `rows_per_chunk` rows in stages of 64.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "tc_gemm.cuh"
+
+namespace cm {
+
+// Epilogues of conv_tc_kernel (rows whose rowseq is negative are gap rows and give zeros):
+//   kEpiRelu   out = bf16(relu(acc + bias))
+//   kEpiPool   v[seq] += (acc + bias) / len(seq) for every real row (mean pooling; the
+//              pre-pooling activations are never stored)
+//   kEpiGate   out = bf16(gate > 0 ? acc : 0), and colsum[n] += the column sums of those
+//              values (the bias gradient of the layer below)
+//   kEpiEmbed  dE[code][c] += acc for every real row (the embedding table's gradient; dX0 is
+//              never stored)
+enum Epi : int { kEpiRelu = 0, kEpiPool = 1, kEpiGate = 2, kEpiEmbed = 3 };
+
+struct ConvEpi {
+    const float* bias;          // Relu, Pool
+    const int32_t* rowseq;      // every mode: sequence index of a row, < 0 for gap rows
+    const __nv_bfloat16* gate;  // Gate
+    __nv_bfloat16* out;         // Relu, Gate
+    const int32_t* slen;        // Pool: rows of every sequence
+    const uint8_t* codes;       // Embed: residue code of every row
+    float* acc;                 // Pool: v (ns x NOUT); Gate: column sums; Embed: dE (20 x NOUT)
+};
+
+namespace tc {
+
+constexpr int kTcRows = 128;        // rows (M) per CTA
+
+// Column sums of a warp's 32 x 32 tile (lane = row, v[0..31] = columns): a transposing
+// reduction (halve the columns a lane keeps at every step, adding the partner lane's copy of
+// them), 31 shuffles in all; afterwards lane c holds the sum of column c.  Overwrites v.
+__device__ __forceinline__ float warp_colsum32(float* v, int lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int k = 0; k < s; ++k) {
+            const float keep = up ? v[k + s] : v[k];
+            const float give = up ? v[k] : v[k + s];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, give, s);
+        }
+    }
+    return v[0];
+}
+constexpr int kTcStages = 3;
+
+template <int CIN, int NOUT>
+struct ConvCfg {
+    static constexpr int BK = (CIN == 32) ? 32 : 64;       // channels per stage = swizzle row
+    static constexpr int KB_PER_TAP = CIN / BK;
+    static constexpr int NKB = 9 * KB_PER_TAP;
+    static constexpr int A_BYTES = kTcRows * BK * 2;
+    static constexpr int B_BYTES = NOUT * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t SWZ = (BK == 64) ? kSwizzle128 : kSwizzle64;
+    static constexpr uint32_t SBO = 8 * BK * 2;
+    static constexpr uint32_t TMEM_COLS = NOUT < 32 ? 32 : NOUT;
+    static constexpr int SMEM = kTcStages * STAGE_BYTES + 1024;
+};
+
+template <int CIN, int NOUT, int EPI>
+__global__ void __launch_bounds__(128, 2)
+conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               int64_t R, const ConvEpi ep, int32_t* err)
+{
+    using C = ConvCfg<CIN, NOUT>;
+    constexpr uint32_t IDESC = idesc_bf16_f32(kTcRows, NOUT, false, false);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int32_t s_issued, s_consumed, s_abort;
+    __shared__ float s_red[EPI == kEpiEmbed ? 20 * NOUT : (EPI == kEpiGate ? NOUT : 1)];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * kTcRows;
+    if (EPI == kEpiEmbed || EPI == kEpiGate)
+        for (int i = threadIdx.x; i < (EPI == kEpiEmbed ? 20 * NOUT : NOUT); i += 128) s_red[i] = 0.f;
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+        for (int s = 0; s < kTcStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+        s_issued = 0;
+        s_consumed = 0;
+        s_abort = *reinterpret_cast<volatile int32_t*>(err);   // an earlier CTA gave up
+    }
+    __syncthreads();
+    if (s_abort) return;
+    if (warp == 2) tmem_alloc(&tmem_slot, C::TMEM_COLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int kb = 0;
+        for (; kb < C::NKB; ++kb) {
+            const int s = kb % kTcStages;
+            if (kb >= kTcStages && !mbar_wait(&empty[s], ((kb / kTcStages) - 1) & 1, err)) break;
+            const int tap = kb / C::KB_PER_TAP, c0 = (kb % C::KB_PER_TAP) * C::BK;
+            uint8_t* st = smem + s * C::STAGE_BYTES;
+            mbar_expect_tx(&full[s], C::STAGE_BYTES);
+            tma_load_2d(st, &tmA, c0, (int32_t)(r0 + tap - 4), &full[s]);
+            tma_load_2d(st + C::A_BYTES, &tmB, tap * CIN + c0, 0, &full[s]);
+        }
+        s_issued = kb;
+    } else if (warp == 1 && lane == 0) {
+        int kb = 0;
+        for (; kb < C::NKB; ++kb) {
+            const int s = kb % kTcStages;
+            if (!mbar_wait(&full[s], (kb / kTcStages) & 1, err)) break;
+            fence_after_sync();
+            const uint8_t* a = smem + s * C::STAGE_BYTES;
+            const uint8_t* b = a + C::A_BYTES;
+#pragma unroll
+            for (int k = 0; k < C::BK / 16; ++k)
+                mma_bf16(tmem, smem_desc(a + 32 * k, 16, C::SBO, C::SWZ),
+                         smem_desc(b + 32 * k, 16, C::SBO, C::SWZ), IDESC, (kb | k) != 0);
+            mma_commit(&empty[s]);
+        }
+        s_consumed = kb;
+        mma_commit(&done);            // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&done, 0, err);
+    fence_after_sync();
+    // warp-uniform: the TMEM loads below are warp-wide instructions
+    if (__all_sync(0xffffffffu, ok && *reinterpret_cast<volatile int32_t*>(err) == 0)) {
+        const int64_t r = r0 + warp * 32 + lane;
+        const bool in = r < R;
+        const int32_t seq = in ? ep.rowseq[r] : -1;
+        const bool real = seq >= 0;
+        // Pool: a warp whose real rows all belong to one sequence reduces its 32 rows first
+        int32_t lead = -1;
+        bool one_seq = false;
+        float inv_len = 0.f;
+        if (EPI == kEpiPool) {
+            lead = __reduce_max_sync(0xffffffffu, seq);
+            one_seq = __all_sync(0xffffffffu, seq < 0 || seq == lead);
+            if (real) inv_len = 1.f / (float)ep.slen[seq];
+        }
+#pragma unroll 1
+        for (int j = 0; j < NOUT / 32; ++j) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
+            const int n0 = j * 32;
+            if (EPI == kEpiEmbed) {
+                if (real) {
+                    float* bin = s_red + (int)ep.codes[r] * NOUT + n0;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) atomicAdd(bin + q, v[q]);
+                }
+                continue;
+            }
+            if (EPI == kEpiPool) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = real ? (v[q] + ep.bias[n0 + q]) * inv_len : 0.f;
+                if (one_seq) {
+                    const float t = warp_colsum32(v, lane);
+                    if (lead >= 0) atomicAdd(ep.acc + (int64_t)lead * NOUT + n0 + lane, t);
+                } else if (real) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) atomicAdd(ep.acc + (int64_t)seq * NOUT + n0 + q, v[q]);
+                }
+                continue;
+            }
+            if (EPI == kEpiRelu) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q] + ep.bias[n0 + q], 0.f);
+            } else if (EPI == kEpiGate && in) {
+                const uint4* g4 = reinterpret_cast<const uint4*>(ep.gate + r * NOUT + n0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 gw = g4[q];
+                    const uint32_t w[4] = {gw.x, gw.y, gw.z, gw.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const __nv_bfloat162 gz = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
+                        if (!(__bfloat162float(gz.x) > 0.f)) v[8 * q + 2 * h] = 0.f;
+                        if (!(__bfloat162float(gz.y) > 0.f)) v[8 * q + 2 * h + 1] = 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = real ? v[q] : 0.f;
+            if (in) {
+                uint4* o = reinterpret_cast<uint4*>(ep.out + r * NOUT + n0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const __nv_bfloat162 p = __floats2bfloat162_rn(v[8 * q + 2 * h],
+                                                                       v[8 * q + 2 * h + 1]);
+                        w[h] = *reinterpret_cast<const uint32_t*>(&p);
+                    }
+                    o[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            if (EPI == kEpiGate && ep.acc) {
+                const float t = warp_colsum32(v, lane);
+                atomicAdd(s_red + n0 + lane, t);
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // loads issued but never consumed (only after a wait gave up): let them land first
+        for (int kb = s_consumed; kb < s_issued; ++kb)
+            mbar_wait(&full[kb % kTcStages], (kb / kTcStages) & 1, err);
+    }
+    __syncthreads();
+    if (EPI == kEpiEmbed || (EPI == kEpiGate && ep.acc))
+        for (int i = threadIdx.x; i < (EPI == kEpiEmbed ? 20 * NOUT : NOUT); i += 128)
+            if (s_red[i] != 0.f) atomicAdd(ep.acc + i, s_red[i]);
+    if (warp == 2) tmem_free(tmem, C::TMEM_COLS);
+}
+
+template <int CIN>
+struct WgradCfg {
+    static constexpr int CW = (CIN == 32) ? 32 : 64;        // channels per swizzle row of A
+    static constexpr int A_BOXES = 128 / CW;                // boxes making up M = 128
+    static constexpr int BKR = 64;                          // rows (K) per stage
+    static constexpr int A_BYTES = 128 * BKR * 2;
+    static constexpr int B_BYTES = 128 * BKR * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t A_SWZ = (CW == 64) ? kSwizzle128 : kSwizzle64;
+    static constexpr uint32_t A_ROW = CW * 2;               // bytes per K row of one A box
+    static constexpr int SMEM = kTcStages * STAGE_BYTES + 1024;
+    static constexpr int MTILES = (9 * CIN + 127) / 128;
+};
+
+template <int CIN>
+__global__ void __launch_bounds__(128, 2)
+wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmD,
+                int64_t rows_per_chunk, float* __restrict__ part, int MPAD, int32_t* err)
+{
+    using C = WgradCfg<CIN>;
+    constexpr uint32_t IDESC = idesc_bf16_f32(128, 128, true, true);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int32_t s_issued, s_consumed, s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mtile = blockIdx.x;
+    const int64_t chunk = blockIdx.y;
+    const int64_t rbeg = chunk * rows_per_chunk;
+    const int nkb = (int)(rows_per_chunk / C::BKR);
+    // taps held by this m-tile's A boxes (a box past the last tap is not loaded)
+    const int nbox = (CIN == 32) ? min(C::A_BOXES, 9 - 4 * mtile) : C::A_BOXES;
+    const uint32_t stage_tx = (uint32_t)(nbox * (C::A_BYTES / C::A_BOXES) + C::B_BYTES);
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tmX);
+        prefetch_tmap(&tmD);
+        for (int s = 0; s < kTcStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+        s_issued = 0;
+        s_consumed = 0;
+        s_abort = *reinterpret_cast<volatile int32_t*>(err);
+    }
+    __syncthreads();
+    if (s_abort) return;
+    if (warp == 2) tmem_alloc(&tmem_slot, 128);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int kb = 0;
+        for (; kb < nkb; ++kb) {
+            const int s = kb % kTcStages;
+            if (kb >= kTcStages && !mbar_wait(&empty[s], ((kb / kTcStages) - 1) & 1, err)) break;
+            const int64_t rr = rbeg + (int64_t)kb * C::BKR;
+            uint8_t* st = smem + s * C::STAGE_BYTES;
+            mbar_expect_tx(&full[s], stage_tx);
+            for (int q = 0; q < nbox; ++q) {
+                // CIN = 128: tap = mtile, channel half q; CIN = 32: tap 4 mtile + q
+                const int tap = (CIN == 32) ? 4 * mtile + q : mtile;
+                const int c0 = (CIN == 32) ? 0 : q * 64;
+                tma_load_2d(st + q * (C::A_BYTES / C::A_BOXES), &tmX, c0,
+                            (int32_t)(rr + tap - 4), &full[s]);
+            }
+            tma_load_2d(st + C::A_BYTES, &tmD, 0, (int32_t)rr, &full[s]);
+            tma_load_2d(st + C::A_BYTES + C::B_BYTES / 2, &tmD, 64, (int32_t)rr, &full[s]);
+        }
+        s_issued = kb;
+    } else if (warp == 1 && lane == 0) {
+        int kb = 0;
+        for (; kb < nkb; ++kb) {
+            const int s = kb % kTcStages;
+            if (!mbar_wait(&full[s], (kb / kTcStages) & 1, err)) break;
+            fence_after_sync();
+            const uint8_t* a = smem + s * C::STAGE_BYTES;
+            const uint8_t* b = a + C::A_BYTES;
+#pragma unroll
+            for (int k = 0; k < C::BKR / 16; ++k)
+                mma_bf16(tmem,
+                         smem_desc(a + 16 * k * C::A_ROW, C::A_BYTES / C::A_BOXES, 8 * C::A_ROW,
+                                   C::A_SWZ),
+                         smem_desc(b + 16 * k * 128, C::B_BYTES / 2, 1024, kSwizzle128), IDESC,
+                         (kb | k) != 0);
+            mma_commit(&empty[s]);
+        }
+        s_consumed = kb;
+        mma_commit(&done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&done, 0, err);
+    fence_after_sync();
+    // warp-uniform: the TMEM loads below are warp-wide instructions
+    if (__all_sync(0xffffffffu, ok && *reinterpret_cast<volatile int32_t*>(err) == 0)) {
+        const int m = mtile * 128 + warp * 32 + lane;
+        float* dst = part + (chunk * (int64_t)MPAD + m) * 128;
+#pragma unroll 1
+        for (int j = 0; j < 4; ++j) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
+            float4* o = reinterpret_cast<float4*>(dst + j * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int kb = s_consumed; kb < s_issued; ++kb)
+            mbar_wait(&full[kb % kTcStages], (kb / kTcStages) & 1, err);
+    }
+    __syncthreads();
+    if (warp == 2) tmem_free(tmem, 128);
+}
+
+}  // namespace tc
+}  // namespace cm
