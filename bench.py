@@ -14,8 +14,16 @@ sequences go host->device and the significant pairs device->host inside every st
 Under torchrun (N > 1) every rank scores its own parts (weak scaling, no collective on the
 data path); rank 0 prints one JSON line.  `--impl reference` times the CPU oracle (scalar int64
 Gotoh on the host cores) on a bounded sample of the same workload.  The roofline object reports
-the SW kernel against the derived DPX-pipe peak at the sampled SM clock, and its DRAM traffic
-per launch from an ncu capture scaled by cells.
+the SW kernel against the DPX-pipe peak at the sampled SM clock (the DPX issue rate is measured
+in the same run by cm_dpx_rate), and its DRAM traffic per launch from an ncu capture scaled by
+cells.
+
+At N = 1 the line also carries `cluster_merge` (skip with --no-cm), the metric's second half:
+ClusterMerge of 100,000 proteome-shaped proteins, the plain merge against the learned path
+timed end to end (labelling 1M training pairs with the GPU SW path, training the ranker on the
+set, calibrating its pruning threshold on held-out pairs, the ranked merge), both recalls
+against the GPU all-against-all of the set, with its own SM-clock record.  It adds about four
+minutes.
 
 ClusterMerge experiments (`--workload cm`): plain merge of a proteome-shaped set
 (`--cm-seqs`, default 100,000; `--family-size`, `--singleton-frac`; `--long-tail K` adds K long
@@ -53,7 +61,8 @@ T_SIG = 100
 M_T, M_U = 138, 15
 GAP_OPEN, GAP_EXT = 11, 1
 PARTS_PER_GPU = 16
-CELLS_PER_CLK_PER_SM = 64.0 * 2.0 / 4.5   # half-rate DPX/ALU pipe, 2 cells / 4.5 ops
+OPS_PER_PACKED_CELL = 4.5    # DPX/ALU-pipe operations of the kernel's cell update, 2 cells each
+OPS_PER_PACKED_CELL_SURVEY = 7.0   # the plain per-cell count (E 2, F 2, H 2, running max 1)
 
 
 def workload_desc(n_parts):
@@ -397,8 +406,9 @@ def run_cluster_merge(args):
 
 
 # the learned-ranker recipe of the ClusterMerge comparison (training pairs drawn inside groups
-# of this many proteins, epochs, Adam learning rate, held-out positives kept by the pruning)
-CM_RECIPE = {"group": 128, "epochs": 40, "lr": 3e-4, "keep": 0.9995}
+# of this many proteins, epochs, peak Adam learning rate with warmup and cosine decay, held-out
+# positives kept by the pruning)
+CM_RECIPE = {"group": 128, "epochs": 20, "lr": 1e-3, "cosine": True, "keep": 0.9995}
 
 
 def cm_comparison(ctx, n_seqs=100000, recipes=(CM_RECIPE,), clocks_dir=None, device=0):
@@ -422,7 +432,8 @@ def cm_comparison(ctx, n_seqs=100000, recipes=(CM_RECIPE,), clocks_dir=None, dev
     for rc in recipes:
         t0 = time.perf_counter()
         info = train_ranker(ctx, n, 1000000, rc["epochs"], rc["keep"], lr=rc["lr"], train_set=ss,
-                            group=rc["group"])
+                            group=rc["group"], cosine=rc.get("cosine", False),
+                            seed=rc.get("seed", 13))
         t_train = time.perf_counter() - t0
         t0 = time.perf_counter()
         ranked = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT,
@@ -451,7 +462,8 @@ def cm_comparison(ctx, n_seqs=100000, recipes=(CM_RECIPE,), clocks_dir=None, dev
     def merge_stats(res):
         st = res["stats"]
         return {k: st[k] for k in ("rep_comparisons", "exchange_comparisons", "intra_comparisons",
-                                   "comparisons_scored", "full_merges", "exchanges", "rounds")}
+                                   "comparisons_scored", "full_merges", "exchanges", "rounds",
+                                   "t_rep", "t_cells", "t_exchange", "t_intra", "t_rank")}
 
     out = {"workload": "ClusterMerge of %d synthetic proteins (80%% in 10,000 families of 8, 20%% "
                        "singletons; lognormal lengths median 350 sigma 0.6 clipped 30-5000), "
@@ -485,42 +497,56 @@ def grouped_training_pairs(family, n_pairs, group, rng):
     family = np.asarray(family)
     order = np.argsort(family, kind="stable")
     bounds = np.flatnonzero(np.diff(family[order])) + 1
-    fams = np.split(order, bounds)
-    fams = [fams[i] for i in rng.permutation(len(fams))]
-    groups, cur = [], []
-    for f in fams:
-        cur.append(f)
-        if sum(len(x) for x in cur) >= group:
-            groups.append(cur)
-            cur = []
-    if cur:
-        groups.append(cur)
+    fstart = np.concatenate([[0], bounds])
+    fsize = np.diff(np.concatenate([fstart, [len(order)]]))
+    fperm = rng.permutation(len(fsize))
+    # members laid out family by family in the dealt order; groups cut at family boundaries
+    members = np.concatenate([order[fstart[f]:fstart[f] + fsize[f]] for f in fperm])
+    sizes = fsize[fperm]
+    cum = np.cumsum(sizes)
+    gid_fam = np.zeros(len(sizes), np.int64)
+    g, acc = 0, 0
+    for i, sz in enumerate(sizes):                  # a group closes once it holds `group`
+        gid_fam[i] = g
+        acc += sz
+        if acc >= group:
+            g, acc = g + 1, 0
+    ngroups = int(gid_fam[-1]) + 1
+    fam_off = cum - sizes                            # first member position of each family
+    first = np.searchsorted(gid_fam, np.arange(ngroups), side="left")
+    last = np.searchsorted(gid_fam, np.arange(ngroups), side="right") - 1
+    gstart = fam_off[first]
+    gend = cum[last]
+    gsize = gend - gstart
     n = len(family)
-    out, gid = [], []
-    for g, fl in enumerate(groups):
-        members = np.concatenate(fl)
-        k = max(2, int(round(n_pairs * len(members) / n)))
-        multi = [f for f in fl if len(f) > 1]
-        kpos = k // 2 if multi else 0
-        if kpos:
-            fi = rng.integers(0, len(multi), size=kpos)
-            pos = np.array([rng.choice(multi[i], 2, replace=False) for i in fi])
-        else:
-            pos = np.zeros((0, 2), np.int64)
-        a = rng.integers(0, len(members), size=k - kpos)
-        b = rng.integers(0, len(members) - 1, size=k - kpos)
-        b = np.where(b >= a, b + 1, b)
-        neg = np.stack([members[a], members[b]], 1)
-        out.append(np.concatenate([pos, neg]))
-        gid.append(np.full(k, g))
-    pairs = np.concatenate(out).astype(np.int32)
-    gid = np.concatenate(gid)
+    k = np.maximum(2, np.round(n_pairs * gsize / n).astype(np.int64))
+    multi = np.flatnonzero(sizes > 1)
+    mg = gid_fam[multi]
+    mcount = np.bincount(mg, minlength=ngroups)
+    mfirst = np.searchsorted(mg, np.arange(ngroups), side="left")
+    kpos = np.where(mcount > 0, k // 2, 0)
+    # within-family pairs: a multi-member family of the group, two distinct members of it
+    pg = np.repeat(np.arange(ngroups), kpos)
+    fam = multi[mfirst[pg] + rng.integers(0, np.maximum(mcount[pg], 1))]
+    a = rng.integers(0, sizes[fam])
+    b = rng.integers(0, sizes[fam] - 1)
+    b = np.where(b >= a, b + 1, b)
+    pos = np.stack([members[fam_off[fam] + a], members[fam_off[fam] + b]], 1)
+    # random pairs: two distinct proteins of the group
+    kneg = k - kpos
+    ng = np.repeat(np.arange(ngroups), kneg)
+    a = rng.integers(0, gsize[ng])
+    b = rng.integers(0, gsize[ng] - 1)
+    b = np.where(b >= a, b + 1, b)
+    neg = np.stack([members[gstart[ng] + a], members[gstart[ng] + b]], 1)
+    pairs = np.concatenate([pos, neg]).astype(np.int32)
+    gids = np.concatenate([pg, ng])
     perm = rng.permutation(len(pairs))[:n_pairs]
-    return pairs[perm], gid[perm]
+    return pairs[perm], gids[perm]
 
 
 def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, train_set=None,
-                 group=512):
+                 group=512, cosine=False):
     """Train the ranker on a synthetic proteome (an independent one, or `train_set` itself):
     pairs drawn inside groups of about `group` proteins, half within-family and half random
     (grouped_training_pairs), labelled [SW score > T] by the GPU path; 10 % held out to
@@ -555,7 +581,8 @@ def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, tra
     ctx.ranker_standardize(tr.seqs, tr.offsets, max_sample=2048)
     loss = ctx.ranker_train(tr.seqs, tr.offsets, pairs[:cut], y[:cut], epochs=epochs,
                             batch_pairs=batch_pairs, lr=lr, seed=seed,
-                            flags=cm.CM_TRAIN_COMPONENTS if group > 0 else 0)
+                            flags=(cm.CM_TRAIN_COMPONENTS if group > 0 else 0) |
+                                  (cm.CM_TRAIN_COSINE if cosine else 0))
     t_train = time.perf_counter() - t0
     z = ctx.ranker_logits(tr.seqs, tr.offsets, pairs[cut:])
     yh = y[cut:]
@@ -567,7 +594,7 @@ def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, tra
     auc = float((ranks[yh == 1].sum() - npos * (npos + 1) / 2) / (npos * (len(yh) - npos)))
     return {"train_seqs": len(tr), "transductive": train_set is not None,
             "train_pairs": int(cut), "heldout_pairs": int(len(pairs) - cut),
-            "group": group, "batch_pairs": batch_pairs,
+            "group": group, "batch_pairs": batch_pairs, "cosine": cosine,
             "positives": float(y.mean()), "epochs": epochs, "lr": lr, "last_batch_loss": loss,
             "label_seconds": t_label, "train_seconds": t_train, "heldout_auc": auc,
             "prune_logit": thr, "keep_heldout_positives": keep,
@@ -615,6 +642,8 @@ def main():
     ap.add_argument("--min-pairs", type=int, default=100000,
                     help="cm: merges with fewer rep x rep pairs stay unpruned")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cm", action="store_true",
+                    help="skip the ClusterMerge plain-vs-learned comparison of the default run")
     ap.add_argument("--clocks-dir", default=tempfile.gettempdir(),
                     help="where the SM-clock samples of the timed region are written")
     ap.add_argument("--parts-per-gpu", type=int, default=PARTS_PER_GPU,
@@ -648,6 +677,7 @@ def main():
         w, r = ctx.autotune(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, sample_seqs=3000)
         tuning.update(warps_per_cta=w, rows_per_warp=r,
                       autotune_seconds=round(time.perf_counter() - t0, 2))
+    dpx_rate = ctx.dpx_rate()
     ctx.reset_stats()
     n_parts = args.parts_per_gpu * world
     seq = part_sequence(n_parts, (args.warmup + args.steps) * world, args.part_offset)
@@ -701,7 +731,10 @@ def main():
     n_sm = props.multi_processor_count
     clk_mhz = clocks["sm_mhz"] if clocks else None
     achieved = st["cells"] / (st["sw16_ms"] * 1e-3) / 1e9 if st["sw16_ms"] > 0 else None
-    peak = n_sm * (clk_mhz * 1e6) * CELLS_PER_CLK_PER_SM / 1e9 if clk_mhz else None
+    # the DPX issue rate measured on this GPU in this run (cm_dpx_rate), lane-ops / clk / SM
+    rate = dpx_rate
+    peak = n_sm * (clk_mhz * 1e6) * rate * 2.0 / OPS_PER_PACKED_CELL / 1e9 if clk_mhz else None
+    peak7 = n_sm * (clk_mhz * 1e6) * rate * 2.0 / OPS_PER_PACKED_CELL_SURVEY / 1e9 if clk_mhz else None
     cells_per_launch = st["cells"] / max(st["sw16_launches"], 1)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
             "frac": (achieved / peak) if (achieved and peak) else None,
@@ -710,8 +743,12 @@ def main():
                              "small case (part 253 of 512: sw16_kernel<22,16,0>, 6.40e10 cells, "
                              "6.59 MB read, 0 written), scaled by cells per launch",
             "kernel": "sw16_kernel (int16x2 DPX wavefront)",
-            "peak_basis": "%d SMs x median SM clock under load x 64 DPX/ALU-pipe lane-ops per "
-                          "clk per SM x 2 cells per 4.5 ops (derived from the measured DPX pipe rate)" % n_sm,
+            "peak_basis": "%d SMs x median SM clock under load x %.2f DPX lane-ops per clk per SM "
+                          "(measured in this run by cm_dpx_rate) x 2 cells per %.1f ops (the "
+                          "kernel's cell update)" % (n_sm, rate, OPS_PER_PACKED_CELL),
+            "dpx_lane_ops_per_clk_per_sm": rate,
+            "frac_7op": (achieved / peak7) if (achieved and peak7) else None,
+            "peak_7op": peak7,
             "sw16_ms_per_launch": st["sw16_ms"] / max(st["sw16_launches"], 1),
             "cells_per_launch": st["cells"] / max(st["sw16_launches"], 1),
             "padded_cell_fraction": (st["cells"] / st["cells_padded"]) if st["cells_padded"] else None}
@@ -742,6 +779,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ss)
 
+    # the headline's second half: ClusterMerge at 100k proteins, plain vs learned (training
+    # included), recall against the GPU all-against-all; one GPU only
+    cmcmp = None
+    if world == 1 and not args.no_cm:
+        cmcmp = cm_comparison(ctx, args.cm_seqs, clocks_dir=args.clocks_dir, device=local)
+
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -754,7 +797,8 @@ def main():
                           "l2": "flushed between timed steps (256 MiB write)",
                           "tuning": tuning},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": int(st["launches"]), "clocks": clocks}
+               "gpu_launches": int(st["launches"]), "clocks": clocks,
+               "cluster_merge": cmcmp}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -61,6 +61,8 @@ extern "C" {
 #define CM_GAP_BLAST      0x4u  /* gap of k residues costs open + k*extend */
 #define CM_FORCE_INT32    0x8u  /* score every pair on the int32 path (no int16x2 first pass) */
 #define CM_TRAIN_COMPONENTS 0x10u /* cm_ranker_train: batches hold whole components of the pair graph */
+#define CM_TRAIN_COSINE   0x20u /* cm_ranker_train: learning rate warms up over the first 2 % of the
+                                   steps, then follows a half cosine from lr down to 0 */
 
 typedef struct cm_ctx cm_ctx;
 
@@ -105,6 +107,14 @@ int cm_set_wait_limit(cm_ctx *ctx, int32_t polls);
 int cm_autotune(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
                 const int8_t *matrix, int32_t gap_open, int32_t gap_extend, int32_t sample_seqs,
                 const char *cache_path, int32_t *warps_out, int32_t *rows_out, uint32_t flags);
+
+/* Issue rate of the packed 16-bit DPX max-add instructions the Smith-Waterman cell update is
+ * built from, measured on this GPU: one CTA of 1,024 threads per SM runs independent chains
+ * of __viaddmax_s16x2 / __vimax3_s16x2 (3:1) timed with each SM's clock64.  Writes
+ * lane-operations per clock per SM (the roofline denominator of the int16x2 kernel: peak
+ * cells/s = SMs x clock x rate x 2 cells / operations per packed cell).  No paper counterpart:
+ * a measurement of the hardware. */
+int cm_dpx_rate(cm_ctx *ctx, double *lane_ops_per_clk_per_sm);
 
 /* Counters of the work done since cm_create or the last cm_reset_stats. */
 typedef struct {
@@ -190,8 +200,21 @@ typedef struct {
                               aligned (treated as dissimilar); Algorithm 1 still visits the
                               kept pairs in set order */
     int32_t ranker_min_pairs;  /* only merges with |cs1|*|cs2| >= this use the ranker */
-    int32_t reserved[2];   /* must be 0 */
+    int32_t merge_mode;    /* CM_MERGE_SEQUENTIAL (0) or CM_MERGE_PARTIAL (1), below */
+    int32_t reserved;      /* must be 0 */
 } cm_params;
+
+/* merge_mode.  CM_MERGE_SEQUENTIAL: Algorithm 1 exactly, Set 1's clusters one after another.
+ * CM_MERGE_PARTIAL: every set merge runs as independent partial merges (Sec. 5), as the
+ * distributed runtime's workers do: each cluster of Set 1 runs Algorithm 1's inner loop
+ * against Set 2 as it stood when the merge began (it does not see what the other partial
+ * merges did: clusters they fully merged are still visited, members they added are not
+ * seen); then the additions to every Set-2 cluster are applied in Set-1 order without
+ * duplicates, and the merged set keeps the clusters of both sets that no partial merge fully
+ * merged (members added to a fully merged Set-2 cluster go with it).  Deterministic; it does
+ * a little more work than the sequential merge and its recall differs slightly. */
+#define CM_MERGE_SEQUENTIAL 0
+#define CM_MERGE_PARTIAL    1
 
 typedef struct {
     int32_t n_seqs;

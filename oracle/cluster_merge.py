@@ -18,6 +18,16 @@ Readings of the paper taken here:
   * Algorithm 2's FIFO starts in input order and pops two sets at a time.
   * output: the union over final clusters of the intra-cluster pairs (i < j) with score > T
     (Sec. 6.1), sorted by (i, j).
+
+Partial merges (Sec. 5): a merge of two large sets is split into partial merges, each merging
+one cluster of Set 1 into (a subset of) Set 2 by Algorithm 1's inner loop; the distributed
+runtime runs them on workers that never communicate, and its controller folds every returned
+result into the merge's state -- elements added to existing clusters, fully merged clusters
+marked -- and finally keeps the clusters of both sets that were not fully merged.
+`merge_partial` follows that description: every cluster of Set 1 runs the inner loop against
+Set 2 as it stood when the merge began (a worker's copy), the additions to each Set-2 cluster
+are applied afterwards in Set-1 order (duplicates dropped), and a Set-2 cluster that some
+partial merge fully merged is dropped together with whatever others added to it.
 """
 from __future__ import annotations
 
@@ -109,8 +119,51 @@ def merge(cs1, cs2, score, transitive, T, stats, keep=None, min_pairs=0):
     return new_set
 
 
-def bottom_up_merge(n, score, transitive, T, stats=None, keep=None, min_pairs=0):
-    """Algorithm 2: FIFO of singleton cluster sets, pop two, merge, push, until one is left."""
+def merge_partial(cs1, cs2, score, transitive, T, stats, keep=None, min_pairs=0):
+    """Algorithm 1 as independent partial merges (Sec. 5, see the module docstring)."""
+    prune = keep is not None and len(cs1) * len(cs2) >= min_pairs
+    snap2 = [list(c2.objs) for c2 in cs2]          # Set 2 as the merge began
+    added = [[] for _ in cs2]                       # what the partial merges add to each
+    merged2 = [False] * len(cs2)
+    new_set = []
+    for c1 in cs1:
+        for k, c2 in enumerate(cs2):
+            if prune and not keep(c1.rep, c2.rep):
+                continue
+            s = score(c1.rep, c2.rep)
+            stats["rep"] += 1
+            if s <= T:
+                continue
+            t21, t12 = transitive(c1.rep, c2.rep, s)
+            if t21:
+                added[k].extend(c1.objs)
+                c1.merged = True
+                stats["full_merges"] += 1
+                break
+            elif t12:
+                c1.append_all(snap2[k])
+                merged2[k] = True
+                stats["full_merges"] += 1
+            else:
+                view = Cluster(c2.rep)                  # the worker's copy of c2
+                view.append_all(snap2[k])
+                exchange_similar(c1, view, s, score, T, stats)
+                added[k].extend(view.objs[len(snap2[k]):])
+                stats["exchanges"] += 1
+        if not c1.merged:
+            new_set.append(c1)
+    for k, c2 in enumerate(cs2):
+        c2.append_all(added[k])
+        if not merged2[k]:
+            new_set.append(c2)
+    return new_set
+
+
+def bottom_up_merge(n, score, transitive, T, stats=None, keep=None, min_pairs=0,
+                    partial=False):
+    """Algorithm 2: FIFO of singleton cluster sets, pop two, merge, push, until one is left.
+    With partial=True every merge runs as independent partial merges (merge_partial)."""
+    merge_fn = merge_partial if partial else merge
     if stats is None:
         stats = new_stats()
     q = deque([Cluster(e)] for e in range(n))
@@ -119,7 +172,7 @@ def bottom_up_merge(n, score, transitive, T, stats=None, keep=None, min_pairs=0)
     while len(q) > 1:
         cs1 = q.popleft()
         cs2 = q.popleft()
-        q.append(merge(cs1, cs2, score, transitive, T, stats, keep, min_pairs))
+        q.append(merge_fn(cs1, cs2, score, transitive, T, stats, keep, min_pairs))
         stats["merges"] += 1
     return q.popleft(), stats
 
@@ -147,7 +200,7 @@ def intra_cluster_pairs(clusters, score, T, stats):
 
 
 def cluster_merge(seqs, offsets, S, gap_open, gap_extend, T, mT, mU, gap_mode=0,
-                  score_matrix=None, keep=None, min_pairs=0):
+                  score_matrix=None, keep=None, min_pairs=0, partial=False):
     """Full ClusterMerge over a sequence set: Algorithm 2 with protein transitivity (Sec. 4),
     then the intra-cluster all-against-all.  `score_matrix` (optional, n x n, from the oracle's
     own all_pairs) replaces direct SW calls by lookups; it is only used for symmetric S.
@@ -181,7 +234,8 @@ def cluster_merge(seqs, offsets, S, gap_open, gap_extend, T, mT, mU, gap_mode=0,
         uA, uB = uncovered(len(a), len(b), cells)
         return uA < mU, uB < mU
 
-    final, stats = bottom_up_merge(n, score, transitive, T, keep=keep, min_pairs=min_pairs)
+    final, stats = bottom_up_merge(n, score, transitive, T, keep=keep, min_pairs=min_pairs,
+                                   partial=partial)
     pairs = intra_cluster_pairs(final, score, T, stats)
     clusters = [(c.rep, list(c.objs)) for c in final]
     return {"clusters": clusters, "pairs": pairs, "stats": stats}

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib as _L
 from ._lib import (CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS,  # noqa: F401
-                   CM_TRAIN_COMPONENTS)
+                   CM_TRAIN_COMPONENTS, CM_TRAIN_COSINE, CM_MERGE_SEQUENTIAL, CM_MERGE_PARTIAL)
 
 __all__ = ["Context", "sw_score_batch", "sw_cells_batch", "sw_allpairs", "CMError",
            "default_context", "sw_cells_batch_noalloc", "cluster_merge", "ops_to_cigar"]
@@ -112,6 +112,12 @@ class Context:
 
     def reset_stats(self):
         _L.check(self._h, _L.lib().cm_reset_stats(self._h))
+
+    def dpx_rate(self):
+        """Measured DPX max-add issue rate, lane-operations per clock per SM (cm_dpx_rate)."""
+        v = ctypes.c_double(0.0)
+        _L.check(self._h, _L.lib().cm_dpx_rate(self._h, ctypes.byref(v)))
+        return v.value
 
     def autotune(self, seqs, offsets, matrix, gap_open, gap_extend, sample_seqs=0,
                  cache_path=None, flags=0):
@@ -238,7 +244,7 @@ class Context:
 
 
     def cluster_merge(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
-                      use_ranker=False, prune_logit=0.0, ranker_min_pairs=0):
+                      use_ranker=False, prune_logit=0.0, ranker_min_pairs=0, merge_mode=0):
         """ClusterMerge (Algorithms 1 and 2 with the Sec. 4 transitivity test) plus the
         intra-cluster all-against-all.  Returns a dict: clusters [(rep, [members])], pairs
         (k, 3) int64 (i, j, score) sorted, and the comparison counters."""
@@ -246,7 +252,7 @@ class Context:
         flags |= self._prep([seqs, offsets, matrix])
         n = int(offsets.shape[0]) - 1
         prm = _L.cm_params(int(T), int(mT), int(mU), int(bool(use_ranker)), float(prune_logit),
-                           int(ranker_min_pairs))
+                           int(ranker_min_pairs), int(merge_mode))
         res = ctypes.POINTER(_L.cm_result)()
         _L.check(self._h, _L.lib().cluster_merge(self._h, _ptr(seqs), _ptr(offsets), n,
                                                  _ptr(matrix), int(gap_open), int(gap_extend),
@@ -409,6 +415,7 @@ def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, c
 
 
 def cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
-                  use_ranker=False, prune_logit=0.0, ranker_min_pairs=0):
+                  use_ranker=False, prune_logit=0.0, ranker_min_pairs=0, merge_mode=0):
     return default_context().cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT,
-                                           mU, flags, use_ranker, prune_logit, ranker_min_pairs)
+                                           mU, flags, use_ranker, prune_logit, ranker_min_pairs,
+                                           merge_mode)

@@ -16,6 +16,9 @@ CM_ASCII = 0x2
 CM_GAP_BLAST = 0x4
 CM_FORCE_INT32 = 0x8
 CM_TRAIN_COMPONENTS = 0x10
+CM_TRAIN_COSINE = 0x20
+CM_MERGE_SEQUENTIAL = 0
+CM_MERGE_PARTIAL = 1
 
 _ERRNAMES = {-1: "CM_ERR_ARG", -2: "CM_ERR_RESIDUE", -3: "CM_ERR_OOM", -4: "CM_ERR_CUDA",
              -5: "CM_ERR_TIMEOUT", -6: "CM_ERR_CAPACITY", -7: "CM_ERR_INTERNAL"}
@@ -37,7 +40,8 @@ class cm_stats(ctypes.Structure):
 class cm_params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("mT", ctypes.c_int32), ("mU", ctypes.c_int32),
                 ("use_ranker", ctypes.c_int32), ("prune_logit", ctypes.c_float),
-                ("ranker_min_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("ranker_min_pairs", ctypes.c_int32), ("merge_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class cm_result(ctypes.Structure):
@@ -83,6 +87,7 @@ def lib():
         "cm_autotune": (ctypes.c_int, [p, p, p, i32, p, i32, i32, i32, ctypes.c_char_p,
                                        ctypes.POINTER(i32), ctypes.POINTER(i32), u32]),
         "cm_reset_stats": (ctypes.c_int, [p]),
+        "cm_dpx_rate": (ctypes.c_int, [p, ctypes.POINTER(ctypes.c_double)]),
         "sw_score_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
         "sw_cells_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, u32]),
         "sw_align_batch": (ctypes.c_int, [p, p, p, i32, p, i64, p, i32, i32, p, p, p, i64,

@@ -96,6 +96,66 @@ struct Driver {
                      const uint32_t* d_bits, const int32_t* d_reps,
                      std::vector<std::vector<SigPair>>& sigm);
     int finish(std::vector<int32_t>& final_set, cm_result* res);
+
+    // One merge's events as independent partial merges (CM_MERGE_PARTIAL): every event reads
+    // the cs2 cluster as the merge began; additions to cs2 clusters are applied after all
+    // events, in event (cs1) order.  Scores not in the memo are requested, as in the
+    // sequential replay.
+    void replay_partial(const std::vector<int32_t>& cs1, const std::vector<int32_t>& cs2,
+                        const std::vector<Event>& evs,
+                        std::unordered_map<int32_t, std::vector<int32_t>>& need,
+                        std::unordered_set<uint64_t>& needed, int64_t& lookups)
+    {
+        std::unordered_map<int32_t, std::vector<int32_t>> view, added;   // by cs2 index
+        for (const Event& ev : evs)
+            if (!view.count(ev.i2)) view[ev.i2] = arena[cs2[ev.i2]].objs;
+        auto score_of = [&](int32_t x, int32_t rep, int32_t self_rep, int32_t s, int32_t* out) {
+            if (x == self_rep) { *out = s; return true; }
+            ++lookups;
+            auto it = memo.find(key2(x, rep));
+            if (it == memo.end()) {
+                if (needed.insert(key2(x, rep)).second) need[rep].push_back(x);
+                return false;
+            }
+            *out = it->second;
+            return true;
+        };
+        for (const Event& ev : evs) {
+            Cluster& c1 = arena[cs1[ev.i1]];
+            const std::vector<int32_t>& v2 = view[ev.i2];
+            std::vector<int32_t>& add2 = added[ev.i2];
+            const int32_t rep2 = arena[cs2[ev.i2]].rep;
+            if (ev.kind == kAbsorbInto2) {
+                add2.insert(add2.end(), c1.objs.begin(), c1.objs.end());
+            } else if (ev.kind == kAbsorbInto1) {
+                for (int32_t x : v2) c1.add(x);
+            } else {
+                // the partial merge's own copy of c2, then ExchangeSimilar on it
+                std::unordered_set<int32_t> vmem(v2.begin(), v2.end());
+                const std::vector<int32_t> s1 = c1.objs;
+                for (int32_t x : s1) {
+                    if (vmem.count(x)) continue;
+                    int32_t sm;
+                    if (!score_of(x, rep2, c1.rep, ev.s, &sm)) continue;
+                    if (sm > prm.T) {
+                        vmem.insert(x);
+                        add2.push_back(x);
+                    }
+                }
+                for (int32_t x : v2) {
+                    if (c1.mem.count(x)) continue;
+                    int32_t sm;
+                    if (!score_of(x, c1.rep, rep2, ev.s, &sm)) continue;
+                    if (sm > prm.T) c1.add(x);
+                }
+            }
+        }
+        std::vector<int32_t> touched;
+        for (const auto& kv : added) touched.push_back(kv.first);
+        std::sort(touched.begin(), touched.end());
+        for (int32_t i2 : touched)
+            for (int32_t x : added[i2]) arena[cs2[i2]].add(x);
+    }
 };
 
 int Driver::run_round(const std::vector<Merge>& ms)
@@ -265,6 +325,9 @@ int Driver::run_round(const std::vector<Merge>& ms)
     // Visits are counted as Algorithm 1 makes them: i1's loop over cs2 (the plain merge) or
     // over its selected candidates (a ranked merge), up to the break, skipping c2 already
     // merged when i1's loop starts; the cs2 merged during i1's own loop were visited first.
+    // With partial merges (CM_MERGE_PARTIAL) every cs1 cluster's loop sees cs2 as the merge
+    // began: it visits the cs2 clusters other loops merged, and the counts do not discount them.
+    const bool partial = prm.merge_mode == CM_MERGE_PARTIAL;
     std::vector<std::vector<Event>> events(nm);
     std::vector<std::vector<int32_t>> out_sets(nm);
     for (size_t m = 0; m < nm; ++m) {
@@ -283,7 +346,7 @@ int Driver::run_round(const std::vector<Merge>& ms)
             std::vector<int32_t> newly;
             for (size_t q = p; q < p_end; ++q) {
                 const int32_t i2 = sg[q].i2;
-                if (merged2[i2]) continue;
+                if (merged2[i2] && !partial) continue;
                 const int32_t s = sg[q].s;
                 bool t21 = false, t12 = false;
                 if (s > prm.mT) {
@@ -310,7 +373,8 @@ int Driver::run_round(const std::vector<Merge>& ms)
                     ++exchanges;
                 }
             }
-            const int64_t before = std::lower_bound(merged_before.begin(), merged_before.end(),
+            const int64_t before = partial ? 0 :
+                                   std::lower_bound(merged_before.begin(), merged_before.end(),
                                                     (int32_t)std::min<int64_t>(end, INT32_MAX)) -
                                    merged_before.begin();
             if (!ranked[m]) {
@@ -320,7 +384,7 @@ int Driver::run_round(const std::vector<Merge>& ms)
                 const uint32_t* row = bitmap.data() + bitbase[m] + (int64_t)i1 * words[m];
                 int64_t vis = 0;
                 for (int64_t w = 0; w * 32 < end; ++w) {
-                    uint32_t x = row[w] & ~merged_bits[w];
+                    uint32_t x = partial ? row[w] : row[w] & ~merged_bits[w];
                     if ((w + 1) * 32 > end) x &= (1u << (end - w * 32)) - 1u;
                     vis += __builtin_popcount(x);
                 }
@@ -367,6 +431,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
         for (size_t m = 0; m < nm; ++m) {
             const auto& cs1 = sets[ms[m].left];
             const auto& cs2 = sets[ms[m].right];
+            if (partial) {
+                replay_partial(cs1, cs2, events[m], need, needed, lookups);
+                continue;
+            }
             for (const Event& ev : events[m]) {
                 Cluster& c1 = arena[cs1[ev.i1]];
                 Cluster& c2 = arena[cs2[ev.i2]];
@@ -751,6 +819,8 @@ int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_
     if (r) return r;
     if (!P.symmetric)
         return fail(c, CM_ERR_ARG, "cluster_merge needs a symmetric substitution matrix");
+    if (params->merge_mode != CM_MERGE_SEQUENTIAL && params->merge_mode != CM_MERGE_PARTIAL)
+        return fail(c, CM_ERR_ARG, "merge_mode must be CM_MERGE_SEQUENTIAL or CM_MERGE_PARTIAL");
     const uint32_t dflags = flags & CM_FORCE_INT32;     // device data is resident from here on
     cm_result* res = (cm_result*)std::calloc(1, sizeof(cm_result));
     if (!res) return fail(c, CM_ERR_OOM, "host allocation failed");

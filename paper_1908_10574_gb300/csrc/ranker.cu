@@ -111,6 +111,14 @@ __global__ void embed_fwd_kernel(const uint8_t* __restrict__ codes, int64_t R,
     X0[i] = (code < 20) ? E[code * kEmb + c] : __float2bfloat16(0.f);
 }
 
+// pooled vectors from their 64-bit fixed-point sums (units of 2^-32)
+__global__ void fixed_to_float_kernel(const unsigned long long* __restrict__ in, int64_t n,
+                                      float* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)((double)(long long)in[i] / kPoolScale);
+}
+
 // dY3[r] = dv[s] / len(s) for the real rows r of sequence s, 0 for gap rows (the gradient of
 // the mean pooling); one thread per 8 channels of a row
 __global__ void pool_bwd_kernel(const float* __restrict__ dv, const int32_t* __restrict__ rowseq,
@@ -368,7 +376,8 @@ struct Ranker {
 };
 
 enum ActId { A_CODES, A_ROWSEQ, A_X0, A_Z1, A_Z2, A_DZ, A_DY2, A_PART, A_V, A_DV,
-             A_SEQ, A_PIDX, A_Y, A_LOGIT, A_EP_SID, A_EP_SROW, A_EP_SLEN, A_EP_PIDX, A_EP_Y };
+             A_SEQ, A_PIDX, A_Y, A_LOGIT, A_EP_SID, A_EP_SROW, A_EP_SLEN, A_EP_PIDX, A_EP_Y,
+             A_V64 };
 
 namespace {
 
@@ -520,17 +529,18 @@ int forward_dev(cm_ctx* c, const Prepared& P, Ranker* K, const int32_t* d_sid,
                 const int64_t* d_srow, const int32_t* d_slen, int64_t ns, int64_t R, float** V_out)
 {
     const cudaStream_t st = c->stream;
-    uint8_t* codes; int32_t* rowseq; bf16 *X0, *Z1, *Z2; float* V;
+    uint8_t* codes; int32_t* rowseq; bf16 *X0, *Z1, *Z2; float* V; unsigned long long* V64;
     AENSURE(A_CODES, R, codes);
     AENSURE(A_ROWSEQ, R * 4, rowseq);
     AENSURE(A_X0, R * kEmb * 2, X0);
     AENSURE(A_Z1, R * kCh * 2, Z1);
     AENSURE(A_Z2, R * kCh * 2, Z2);
     AENSURE(A_V, ns * kCh * 4, V);
+    AENSURE(A_V64, ns * kCh * 8, V64);
     int r;
     CUDA_TRY(cudaMemsetAsync(codes, 0xff, R, st));
     CUDA_TRY(cudaMemsetAsync(rowseq, 0xff, R * 4, st));
-    CUDA_TRY(cudaMemsetAsync(V, 0, ns * kCh * 4, st));
+    CUDA_TRY(cudaMemsetAsync(V64, 0, ns * kCh * 8, st));
     gather_rows_kernel<<<(unsigned)ns, 128, 0, st>>>(P.db, P.off, d_sid, d_srow, d_slen, (int32_t)ns,
                                                      codes, rowseq);
     embed_fwd_kernel<<<blocks_for(R * kEmb, 256), 256, 0, st>>>(codes, R, K->E, X0);
@@ -548,8 +558,11 @@ int forward_dev(cm_ctx* c, const Prepared& P, Ranker* K, const int32_t* d_sid,
     ep.bias = K->params + kOffB3;
     ep.out = nullptr;
     ep.slen = d_slen;
-    ep.acc = V;
+    ep.acc64 = V64;
     if ((r = conv_tc<kCh, kCh, kEpiPool>(c, K, Z2, R, K->W3, ep))) return r;
+    fixed_to_float_kernel<<<blocks_for(ns * kCh, 256), 256, 0, st>>>(V64, ns * kCh, V);
+    CUDA_TRY(cudaGetLastError());
+    c->stats.launches += 1;
     *V_out = V;
     return CM_OK;
 }
@@ -982,10 +995,12 @@ int cm_ranker_train(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int3
     float loss = 0.f;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const Bf16Copies copies{K->E, K->W1, K->W1T, K->W2, K->W2T, K->W3, K->W3T};
+    int64_t total_steps = 0, t_step = 0;      // for CM_TRAIN_COSINE (batches per epoch are fixed)
     for (int ep = 0; ep < epochs; ++ep) {
         // the whole epoch's batches go to the device in one copy per array
         train_epoch_batches(comps, batch_pairs, g, order, bounds);
         const int64_t nb = (int64_t)bounds.size() - 1;
+        if (ep == 0) total_steps = nb * (int64_t)epochs;
         Packed B;
         for (int64_t bi = 0; bi < nb; ++bi)
             pack_batch(P, n_seqs, pairs, labels, order.data() + bounds[bi],
@@ -998,8 +1013,15 @@ int cm_ranker_train(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int3
             if ((r = loss_grad_packed(c, P, K, B, D, (size_t)bi, last ? &loss : nullptr))) return r;
             ++K->step;
             const float bc1 = 1.f - std::pow(b1, (float)K->step), bc2 = 1.f - std::pow(b2, (float)K->step);
+            float lr_t = lr;
+            if (flags & CM_TRAIN_COSINE) {
+                const double T_ = (double)std::max<int64_t>(total_steps, 1);
+                const double warm = std::min(1.0, (double)(t_step + 1) / std::max(1.0, 0.02 * T_));
+                lr_t = (float)(lr * warm * 0.5 * (1.0 + std::cos(3.141592653589793 * (double)t_step / T_)));
+            }
+            ++t_step;
             adam_kernel<<<blocks_for(kNumParams, 256), 256, 0, c->stream>>>(
-                K->params, K->grad, K->m, K->v, kNumParams, lr, b1, b2, eps, bc1, bc2, copies);
+                K->params, K->grad, K->m, K->v, kNumParams, lr_t, b1, b2, eps, bc1, bc2, copies);
             CUDA_TRY(cudaGetLastError());
             c->stats.launches += 1;
         }

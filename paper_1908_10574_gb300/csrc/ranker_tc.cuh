@@ -27,7 +27,9 @@ namespace cm {
 // Epilogues of conv_tc_kernel (rows whose rowseq is negative are gap rows and give zeros):
 //   kEpiRelu   out = bf16(relu(acc + bias))
 //   kEpiPool   v[seq] += (acc + bias) / len(seq) for every real row (mean pooling; the
-//              pre-pooling activations are never stored)
+//              pre-pooling activations are never stored).  The sums are kept in 64-bit fixed
+//              point (units of 2^-32) so that the atomic adds commute: v does not depend on
+//              the order in which CTAs finish, and neither do the ranker's logits.
 //   kEpiGate   out = bf16(gate > 0 ? acc : 0), and colsum[n] += the column sums of those
 //              values (the bias gradient of the layer below)
 //   kEpiEmbed  dE[code][c] += acc for every real row (the embedding table's gradient; dX0 is
@@ -41,8 +43,16 @@ struct ConvEpi {
     __nv_bfloat16* out;         // Relu, Gate
     const int32_t* slen;        // Pool: rows of every sequence
     const uint8_t* codes;       // Embed: residue code of every row
-    float* acc;                 // Pool: v (ns x NOUT); Gate: column sums; Embed: dE (20 x NOUT)
+    float* acc;                 // Gate: column sums; Embed: dE (20 x NOUT)
+    unsigned long long* acc64;  // Pool: v (ns x NOUT) in units of 2^-32
 };
+
+constexpr double kPoolScale = 4294967296.0;   // 2^32: fixed-point unit of the pooled sums
+
+__device__ __forceinline__ void add_fixed(unsigned long long* p, float v)
+{
+    atomicAdd(p, (unsigned long long)__double2ll_rn((double)v * kPoolScale));
+}
 
 namespace tc {
 
@@ -183,10 +193,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 for (int q = 0; q < 32; ++q) v[q] = real ? (v[q] + ep.bias[n0 + q]) * inv_len : 0.f;
                 if (one_seq) {
                     const float t = warp_colsum32(v, lane);
-                    if (lead >= 0) atomicAdd(ep.acc + (int64_t)lead * NOUT + n0 + lane, t);
+                    if (lead >= 0) add_fixed(ep.acc64 + (int64_t)lead * NOUT + n0 + lane, t);
                 } else if (real) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) atomicAdd(ep.acc + (int64_t)seq * NOUT + n0 + q, v[q]);
+                    for (int q = 0; q < 32; ++q) add_fixed(ep.acc64 + (int64_t)seq * NOUT + n0 + q, v[q]);
                 }
                 continue;
             }

@@ -6,7 +6,7 @@
 // output slot of a plan is written exactly once.
 //
 // Input (stdin, whitespace separated): K instances, each
-//   n T mT mU use_ranker ranker_min_pairs
+//   n T mT mU use_ranker ranker_min_pairs merge_mode
 //   len[n]  M[n*n]  cov[n*n]  keep[n*n]
 // Output per instance: "clusters C" then C lines "rep size members...", "pairs P" then P lines
 // "i j s", then "stats rep exchange intra full_merges exchanges merges", or "error code msg".
@@ -237,7 +237,8 @@ int main()
     for (int inst = 0; inst < K; ++inst) {
         Instance I;
         int32_t T, mT, mU, use_ranker, min_pairs;
-        std::cin >> I.n >> T >> mT >> mU >> use_ranker >> min_pairs;
+        int merge_mode = 0;
+        std::cin >> I.n >> T >> mT >> mU >> use_ranker >> min_pairs >> merge_mode;
         const size_t nn = (size_t)I.n * I.n;
         I.len.resize(I.n);
         I.off.assign(I.n + 1, 0);
@@ -262,6 +263,7 @@ int main()
         prm.use_ranker = use_ranker;
         prm.prune_logit = 0.f;
         prm.ranker_min_pairs = min_pairs;
+        prm.merge_mode = merge_mode;
         int8_t mat[400] = {};
         uint8_t dummy = 0;
         cm_result* res = nullptr;

@@ -9,7 +9,8 @@ transposed blocks of long representatives and the device-planned lists of ranked
 checked on hundreds of random merge trees, including ones the GPU tests never reach.  The
 oracle runs Algorithm 2 with the same similarity (`score`, `transitive` and the pruning hook
 `keep`); clusters with their member order, similar pairs and all comparison counts must be
-identical."""
+identical, for sequential merges and for independent partial merges (CM_MERGE_PARTIAL, the
+oracle's merge_partial)."""
 import importlib
 import os
 import shutil
@@ -64,15 +65,16 @@ def _instance(rng):
     keep = keep | keep.T
     use_ranker = int(rng.random() < 0.5)
     min_pairs = int(rng.choice([0, 1, 4, 30]))
+    partial = int(rng.random() < 0.4)
     return dict(n=n, T=T, mT=mT, mU=mU, use_ranker=use_ranker, min_pairs=min_pairs, L=L, M=M,
-                cov=cov, keep=keep)
+                cov=cov, keep=keep, partial=partial)
 
 
 def _serialise(insts):
     out = [str(len(insts))]
     for d in insts:
-        out.append("%d %d %d %d %d %d" % (d["n"], d["T"], d["mT"], d["mU"], d["use_ranker"],
-                                         d["min_pairs"]))
+        out.append("%d %d %d %d %d %d %d" % (d["n"], d["T"], d["mT"], d["mU"], d["use_ranker"],
+                                            d["min_pairs"], d["partial"]))
         for key in ("L", "M", "cov", "keep"):
             out.append(" ".join(str(int(v)) for v in np.asarray(d[key]).reshape(-1)))
     return "\n".join(out) + "\n"
@@ -119,7 +121,7 @@ def _oracle(d):
 
     kf = (lambda a, b: bool(keep[a, b])) if d["use_ranker"] else None
     final, stats = ocm.bottom_up_merge(d["n"], score, transitive, T, keep=kf,
-                                       min_pairs=d["min_pairs"])
+                                       min_pairs=d["min_pairs"], partial=bool(d["partial"]))
     pairs = ocm.intra_cluster_pairs(final, score, T, stats)
     clusters = [(c.rep, list(c.objs)) for c in final]
     return clusters, [tuple(map(int, p)) for p in pairs.tolist()], \
@@ -140,7 +142,7 @@ def test_driver_replay_matches_oracle(tmp_path):
                          timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     got = _parse(out.stdout, len(insts))
-    exercised = {"ranked": 0, "full": 0, "exchange": 0, "long": 0}
+    exercised = {"ranked": 0, "full": 0, "exchange": 0, "long": 0, "partial": 0}
     for d, g in zip(insts, got):
         want = _oracle(d)
         assert g[0] == want[0], ("clusters", d["n"], d["use_ranker"])
@@ -150,4 +152,5 @@ def test_driver_replay_matches_oracle(tmp_path):
         exercised["full"] += want[2][3] > 0
         exercised["exchange"] += want[2][4] > 0
         exercised["long"] += bool((d["L"] > 4096).any())
+        exercised["partial"] += d["partial"] and want[2][3] > 0 and want[2][4] > 0
     assert min(exercised.values()) >= 20, exercised

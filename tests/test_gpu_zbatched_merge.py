@@ -89,3 +89,31 @@ def test_batch_limit_argument_checks():
     with pytest.raises(cm.CMError):
         ctx.set_batch_limit(1000)
     ctx.set_batch_limit(0)
+
+
+def test_partial_merges_on_the_2k_subset(case2k):
+    """Independent partial merges (CM_MERGE_PARTIAL, Sec. 5) on the 2k subset: clusters,
+    similar pairs and counts equal the oracle's partial-merge Algorithm 2, every pair found
+    is in the all-against-all truth, and recall is within 0.1 % of the sequential merge's."""
+    ss, want_seq = case2k
+    _, scores = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=100)
+    n = len(ss)
+    M = np.zeros((n, n), np.int64)
+    M[np.triu_indices(n, 1)] = scores
+    M = M + M.T
+    want = oracle.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T=100, mT=138, mU=15,
+                                score_matrix=M, partial=True)
+    ctx = cm.Context(0)
+    got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 100, 138, 15,
+                            merge_mode=cm.CM_MERGE_PARTIAL)
+    _check(got, want)
+    truth, _ = oracle.all_pairs(ss.seqs, ss.offsets, S62, 11, 1, T=100)
+    tset = {(int(i), int(j)) for i, j, _ in truth}
+    assert all((int(i), int(j)) in tset for i, j, _ in got["pairs"])
+    r_par = oracle.recall(got["pairs"], truth)
+    r_seq = oracle.recall(want_seq["pairs"], truth)
+    assert abs(r_par - r_seq) <= 1e-3, (r_par, r_seq)
+    # partial merges visit the clusters other partial merges fully merged
+    assert got["stats"]["rep_comparisons"] >= want_seq["stats"]["rep"]
+    with pytest.raises(cm.CMError):
+        ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, 100, 138, 15, merge_mode=2)

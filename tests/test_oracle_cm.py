@@ -163,3 +163,56 @@ def test_pruning_hook_keep_all_is_plain_and_keep_none_skips_large_merges():
                                  keep=lambda a, b: False, min_pairs=2)
     assert st3["rep"] == 2
     assert [(c.rep, list(c.objs)) for c in final] == [(0, [0, 1]), (1, [1, 0]), (2, [2]), (3, [3])]
+
+
+def run_partial(n, F, trans):
+    def score(x, y):
+        return F[(min(x, y), max(x, y))]
+
+    def transitive(r1, r2, s):
+        return trans.get((r1, r2), (False, False))
+
+    final, st = bottom_up_merge(n, score, transitive, T, partial=True)
+    return [(c.rep, list(c.objs)) for c in final], st
+
+
+def test_partial_merges_see_set2_as_the_merge_began():
+    """Sec. 5's partial merges, traced by hand on the case where the sequential merge skips a
+    merged cluster (test_n4_has_been_merged_skip).  Merges (0,1) and (2,3): no similarity.
+    Merge A=[C0,C1] with B=[C2,C3]: C0's partial merge absorbs C2 (t12) and skips C3 (4 <= T).
+    C1's partial merge still sees C2 unmerged: f(1,2) = 99 > T, not transitive, so it
+    exchanges the reps (C2's copy gains 1, C1 gains 2); then C3 absorbs C1 = [1, 2] (t21) and
+    the loop breaks.  Result: C0 = [0, 2] and C3 = [3, 1, 2]; C2 was fully merged, so what C1
+    added to it goes with it.  Visits: 1 + 1 + 2 + 2 = 6 (the sequential merge makes 5)."""
+    F = {(0, 1): 1, (2, 3): 2, (0, 2): 30, (0, 3): 4, (1, 3): 25, (1, 2): 99}
+    trans = {(0, 2): (False, True), (1, 3): (True, False)}
+    cl, st = run_partial(4, F, trans)
+    assert cl == [(0, [0, 2]), (3, [3, 1, 2])]
+    assert st["rep"] == 6 and st["full_merges"] == 2 and st["exchanges"] == 1
+    assert st["exchange"] == 0
+    seq, st2 = run(4, F, trans)
+    assert seq == [(0, [0, 2]), (3, [3, 1])] and st2["rep"] == 5
+
+
+def test_partial_merges_exchange_members_of_the_snapshot_only():
+    """A Set-2 cluster's members added by one partial merge are not scored by another.  Merges
+    (0,1) and (2,3): no similarity.  Merge A=[C0,C1] with B=[C2,C3], f(0,2) = f(1,2) = 50, the
+    rest <= T, no transitivity.  Sequentially, C0 exchanges with C2 (C2 = [2, 0], C0 = [0, 2]);
+    then C1 exchanges with C2 = [2, 0]: rep 1 joins C2, and C2's member 0 is scored against
+    rep 1 (f = 1: one exchange comparison, not added).  As partial merges, C1 sees C2 = [2]
+    only, so 0 is never scored; C2 still ends as [2, 0, 1] from the two merges' additions."""
+    F = {(0, 1): 1, (2, 3): 2, (0, 2): 50, (1, 2): 50, (0, 3): 3, (1, 3): 4}
+    want = [(0, [0, 2]), (1, [1, 2]), (2, [2, 0, 1]), (3, [3])]
+    seq, st_seq = run(4, F, {})
+    par, st_par = run_partial(4, F, {})
+    assert seq == want and par == want
+    assert st_seq["exchange"] == 1 and st_par["exchange"] == 0
+    assert st_seq["rep"] == st_par["rep"] == 6
+
+
+def test_partial_merges_without_full_merges_give_full_recall(small):
+    ss, S, truth, M = small
+    res = oracle.cluster_merge(ss.seqs, ss.offsets, S, 11, 1, T=60, mT=10 ** 9, mU=15,
+                               score_matrix=M, partial=True)
+    assert res["stats"]["full_merges"] == 0
+    assert oracle.recall(res["pairs"], truth) == 1.0
