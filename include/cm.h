@@ -248,6 +248,21 @@ int cluster_merge(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int3
                   const cm_params *params, cm_result **out, uint32_t flags);
 void cm_result_free(cm_result *result);
 
+/* greedy_cluster -- incremental greedy clustering, the comparison method of Sec. 2 (after
+ * Wittwer et al.), on the same kernels: sequences in input order are compared with every
+ * cluster representative in creation order; a sequence joins the cluster of every
+ * representative with score > T, and becomes the representative of a new cluster unless
+ * some representative represents it (score > mT and fewer than mU of its residues outside
+ * their optimal local alignment, the Sec. 4 test).  Then the intra-cluster all-against-all
+ * (Sec. 6.1), as cluster_merge.  params: T, mT, mU; use_ranker and merge_mode must be 0.
+ * Result as cluster_merge: clusters in creation order (members in joining order, rep
+ * first), rep_comparisons = the comparisons with representatives, full_merges = sequences
+ * represented by an existing cluster, rounds = device batches of sequences (2,048 each, the
+ * chunk scored against the representatives before it and, speculatively, against itself). */
+int greedy_cluster(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs,
+                   const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
+                   const cm_params *params, cm_result **out, uint32_t flags);
+
 /* ---- learned representative ranker (orders and prunes rep x rep comparisons) ----
  * The paper has no learned component; this network only decides which representative pairs
  * are aligned (and in which order) inside Algorithm 1 — the exact Smith-Waterman score alone

@@ -35,7 +35,8 @@ class GreedyCluster:
 def greedy(n, score, uncovered_x, T, mT, mU, stats=None):
     """Clusters (representatives in creation order, members in joining order, rep first).
     `score(x, r)` is f; `uncovered_x(x, r)` the residues of x outside the optimal local
-    alignment of (x, r)."""
+    alignment of (x, r).  stats["rep"] counts comparisons with representatives,
+    stats["full_merges"] the sequences an existing cluster represents."""
     if stats is None:
         stats = new_stats()
     clusters = []
@@ -51,6 +52,8 @@ def greedy(n, score, uncovered_x, T, mT, mU, stats=None):
                 represented = True
         if not represented:
             clusters.append(GreedyCluster(x))
+        else:
+            stats["full_merges"] += 1          # represented by an existing cluster
     return clusters, stats
 
 

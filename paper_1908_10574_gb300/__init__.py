@@ -257,6 +257,23 @@ class Context:
         _L.check(self._h, _L.lib().cluster_merge(self._h, _ptr(seqs), _ptr(offsets), n,
                                                  _ptr(matrix), int(gap_open), int(gap_extend),
                                                  ctypes.byref(prm), ctypes.byref(res), flags))
+        return self._result(res)
+
+    def greedy_cluster(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0):
+        """Incremental greedy clustering (the paper's comparison method) plus the
+        intra-cluster all-against-all; same result dict as cluster_merge."""
+        seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
+        flags |= self._prep([seqs, offsets, matrix])
+        n = int(offsets.shape[0]) - 1
+        prm = _L.cm_params(int(T), int(mT), int(mU), 0, 0.0, 0, 0)
+        res = ctypes.POINTER(_L.cm_result)()
+        _L.check(self._h, _L.lib().greedy_cluster(self._h, _ptr(seqs), _ptr(offsets), n,
+                                                  _ptr(matrix), int(gap_open), int(gap_extend),
+                                                  ctypes.byref(prm), ctypes.byref(res), flags))
+        return self._result(res)
+
+    @staticmethod
+    def _result(res):
         try:
             R = res.contents
             nc = R.n_clusters

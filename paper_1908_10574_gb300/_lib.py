@@ -96,6 +96,8 @@ def lib():
                                        ctypes.POINTER(i64), u32]),
         "cluster_merge": (ctypes.c_int, [p, p, p, i32, p, i32, i32, ctypes.POINTER(cm_params),
                                          ctypes.POINTER(ctypes.POINTER(cm_result)), u32]),
+        "greedy_cluster": (ctypes.c_int, [p, p, p, i32, p, i32, i32, ctypes.POINTER(cm_params),
+                                          ctypes.POINTER(ctypes.POINTER(cm_result)), u32]),
         "cm_result_free": (None, [ctypes.POINTER(cm_result)]),
         "cm_ranker_num_params": (i64, []),
         "cm_ranker_init": (ctypes.c_int, [p, ctypes.c_uint64]),

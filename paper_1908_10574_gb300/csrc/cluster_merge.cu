@@ -16,6 +16,7 @@
 // The result (clusters, member order, similar pairs, logical comparison counts) equals the
 // plain sequential algorithm's; speculation only adds alignments that are never looked at.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -96,6 +97,7 @@ struct Driver {
                      const uint32_t* d_bits, const int32_t* d_reps,
                      std::vector<std::vector<SigPair>>& sigm);
     int finish(std::vector<int32_t>& final_set, cm_result* res);
+    int run_greedy(int32_t n, int32_t chunk, std::vector<int32_t>& final_set);
 
     // One merge's events as independent partial merges (CM_MERGE_PARTIAL): every event reads
     // the cs2 cluster as the merge began; additions to cs2 clusters are applied after all
@@ -797,6 +799,150 @@ int Driver::finish(std::vector<int32_t>& final_set, cm_result* res)
     return CM_OK;
 }
 
+// Incremental greedy clustering (the comparison method of Sec. 2, after Wittwer et al.): each
+// sequence in input order is compared with every representative in creation order, joins the
+// cluster of every one with s > T, and starts a new cluster unless some representative
+// represents it (s > mT and fewer than mU of its residues outside the alignment, the Sec. 4
+// test with the sequence in the absorbed role).  Sequences are taken in chunks: one device
+// batch scores the chunk against the representatives before it (CROSS) and against itself
+// (TRI, speculative: any earlier chunk member may become a representative), a second the
+// alignment cells of every pair above mT; the host then replays the chunk in input order.
+int Driver::run_greedy(int32_t n, int32_t chunk, std::vector<int32_t>& final_set)
+{
+    NvtxRange range("cm greedy");
+    arena.clear();
+    std::vector<int32_t> cluster_of((size_t)std::max(n, 1), -1);   // representative -> cluster
+    for (int32_t x0 = 0; x0 < n; x0 += chunk) {
+        const int32_t x1 = std::min<int32_t>(n, x0 + chunk);
+        const int32_t nr = (int32_t)arena.size();
+        std::vector<int32_t> ids;
+        std::vector<BlockReq> req;
+        std::vector<int32_t> members((size_t)(x1 - x0));
+        std::iota(members.begin(), members.end(), x0);
+        members = by_length(members);
+        BlockReq tri{};
+        tri.kind = kTri;
+        tri.a_begin = tri.b_begin = 0;
+        tri.a_count = tri.b_count = (int64_t)members.size();
+        ids.insert(ids.end(), members.begin(), members.end());
+        req.push_back(tri);
+        std::vector<int32_t> short_reps, long_reps;
+        for (int32_t k = 0; k < nr; ++k)
+            (P.len(arena[k].rep) > kLongSubject ? long_reps : short_reps).push_back(arena[k].rep);
+        if (!short_reps.empty()) {                        // chunk (queries) x reps (subjects)
+            BlockReq b{};
+            b.kind = kCross;
+            b.a_begin = 0;
+            b.a_count = (int64_t)members.size();
+            b.b_begin = (int64_t)ids.size();
+            b.b_count = (int64_t)short_reps.size();
+            ids.insert(ids.end(), short_reps.begin(), short_reps.end());
+            req.push_back(b);
+        }
+        if (!long_reps.empty()) {                         // long reps (queries) x chunk
+            BlockReq b{};
+            b.kind = kCross;
+            b.swap = 1;
+            b.a_begin = (int64_t)ids.size();
+            b.a_count = (int64_t)long_reps.size();
+            ids.insert(ids.end(), long_reps.begin(), long_reps.end());
+            b.b_begin = 0;
+            b.b_count = (int64_t)members.size();
+            req.push_back(b);
+        }
+        std::vector<std::pair<int64_t, int32_t>> sig;
+        std::vector<int64_t> base;
+        double t0 = now_s();
+        int r = score_blocks_sig(c, P, ids, req, prm.T, sig, base, flags);
+        if (r) return r;
+        t_rep += now_s() - t0;
+        ++batches;
+        for (const BlockReq& b : req)
+            scored += b.kind == kTri ? b.a_count * (b.a_count - 1) / 2 : b.a_count * b.b_count;
+        // similar pairs (x, y, s) of the chunk: y a representative before it or an earlier
+        // chunk member
+        std::vector<SigPair> simp;
+        size_t q = 0;
+        for (size_t bi = 0; bi < req.size(); ++bi) {
+            const BlockReq& b = req[bi];
+            const int64_t end = bi + 1 < req.size() ? base[bi + 1] : INT64_MAX;
+            for (; q < sig.size() && sig[q].first < end; ++q) {
+                const int64_t loc = sig[q].first - base[bi];
+                int32_t u, v;
+                if (b.kind == kTri) {
+                    int64_t k = (int64_t)((1.0 + std::sqrt(1.0 + 8.0 * (double)loc)) / 2.0);
+                    while (k * (k - 1) / 2 > loc) --k;
+                    while ((k + 1) * k / 2 <= loc) ++k;
+                    u = ids[b.a_begin + k];
+                    v = ids[b.a_begin + (loc - k * (k - 1) / 2)];
+                    if (u < v) std::swap(u, v);             // (later, earlier) in input order
+                } else {
+                    const int32_t qa = ids[b.a_begin + loc / b.b_count];
+                    const int32_t sb = ids[b.b_begin + loc % b.b_count];
+                    u = b.swap ? sb : qa;                   // the chunk member
+                    v = b.swap ? qa : sb;                   // the representative
+                }
+                simp.push_back({u, v, sig[q].second});
+            }
+        }
+        // alignment cells of every candidate representation (s > mT), pair (x, y)
+        std::vector<int32_t> cp;
+        for (const SigPair& e : simp)
+            if (e.s > prm.mT) { cp.push_back(e.i1); cp.push_back(e.i2); }
+        std::vector<int32_t> cells(cp.size() / 2 * 5);
+        std::unordered_map<uint64_t, int64_t> cidx;
+        if (!cp.empty()) {
+            t0 = now_s();
+            r = run_cells(c, P, cp.data(), (int64_t)cp.size() / 2, cells.data());
+            if (r) return r;
+            t_cells += now_s() - t0;
+            cells_pairs += (int64_t)cp.size() / 2;
+            for (size_t k = 0; k < cp.size() / 2; ++k)
+                cidx[key2(cp[2 * k], cp[2 * k + 1])] = (int64_t)k;
+        }
+        // replay in input order; a sequence's candidates in its representatives' creation
+        // order (those before the chunk first, by cluster; then chunk members by input order)
+        std::sort(simp.begin(), simp.end(), [&](const SigPair& a, const SigPair& b) {
+            if (a.i1 != b.i1) return a.i1 < b.i1;
+            const bool ea = a.i2 < x0, eb = b.i2 < x0;
+            if (ea != eb) return ea;
+            return ea ? cluster_of[a.i2] < cluster_of[b.i2] : a.i2 < b.i2;
+        });
+        size_t p = 0;
+        int32_t chunk_reps = 0;
+        for (int32_t x = x0; x < x1; ++x) {
+            rep_cmp += nr + chunk_reps;
+            bool represented = false;
+            for (; p < simp.size() && simp[p].i1 == x; ++p) {
+                const SigPair& e = simp[p];
+                const int32_t cl = cluster_of[e.i2];
+                if (cl < 0) continue;                       // not a representative
+                arena[cl].objs.push_back(x);
+                if (e.s > prm.mT) {
+                    const int32_t* ce = &cells[cidx.at(key2(x, e.i2)) * 5];
+                    const int64_t lx = P.len(x);
+                    const int64_t ux = ce[0] ? lx - (ce[2] - ce[1] + 1) : lx;
+                    if (ux < prm.mU) represented = true;
+                }
+            }
+            if (!represented) {
+                Cluster nc;
+                nc.rep = x;
+                nc.objs = {x};
+                cluster_of[x] = (int32_t)arena.size();
+                arena.push_back(std::move(nc));
+                ++chunk_reps;
+            } else {
+                ++full_merges;
+            }
+        }
+        ++rounds;
+    }
+    final_set.resize(arena.size());
+    std::iota(final_set.begin(), final_set.end(), 0);
+    return CM_OK;
+}
+
 }  // namespace
 }  // namespace cm
 
@@ -865,6 +1011,36 @@ int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_
     std::vector<int32_t> final_set;
     if (!q.empty()) final_set = D.sets[q.front()];
     r = D.finish(final_set, res);
+    if (r) { cm_result_free(res); return r; }
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = res;
+    return CM_OK;
+}
+
+int greedy_cluster(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                   const int8_t* matrix, int32_t gap_open, int32_t gap_extend,
+                   const cm_params* params, cm_result** out, uint32_t flags)
+{
+    if (!c) return CM_ERR_ARG;
+    NvtxRange range("greedy_cluster");
+    if (!out || !params) return fail(c, CM_ERR_ARG, "null params / out");
+    *out = nullptr;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    Prepared P;
+    int r = prepare(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, flags, P);
+    if (r) return r;
+    if (!P.symmetric)
+        return fail(c, CM_ERR_ARG, "greedy_cluster needs a symmetric substitution matrix");
+    if (params->use_ranker || params->merge_mode)
+        return fail(c, CM_ERR_ARG, "greedy_cluster takes neither the ranker nor a merge mode");
+    cm_result* res = (cm_result*)std::calloc(1, sizeof(cm_result));
+    if (!res) return fail(c, CM_ERR_OOM, "host allocation failed");
+    res->n_seqs = n_seqs;
+    Driver D(c, P, *params, flags & CM_FORCE_INT32);
+    std::vector<int32_t> final_set;
+    r = D.run_greedy(n_seqs, std::max(1, c->greedy_chunk), final_set);
+    if (!r) r = D.finish(final_set, res);
     if (r) { cm_result_free(res); return r; }
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = res;

@@ -38,6 +38,7 @@ struct cm_ctx {
     int rows_per_warp = 8192;
     int64_t max_batch_slots = (int64_t)1 << 32;   // slots of one rep-wave device batch
     int32_t wait_limit = 1 << 24;           // polls (~100 ns each) of a bounded device wait
+    int32_t greedy_chunk = 2048;            // sequences per device batch of greedy_cluster
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t aux = nullptr;             // second stream: alternate length bins overlap tails
     cudaEvent_t fork = nullptr, join = nullptr;

@@ -6,7 +6,7 @@
 // output slot of a plan is written exactly once.
 //
 // Input (stdin, whitespace separated): K instances, each
-//   n T mT mU use_ranker ranker_min_pairs merge_mode
+//   n T mT mU use_ranker ranker_min_pairs merge_mode algorithm (0 cluster_merge, 1 greedy)
 //   len[n]  M[n*n]  cov[n*n]  keep[n*n]
 // Output per instance: "clusters C" then C lines "rep size members...", "pairs P" then P lines
 // "i j s", then "stats rep exchange intra full_merges exchanges merges", or "error code msg".
@@ -237,8 +237,8 @@ int main()
     for (int inst = 0; inst < K; ++inst) {
         Instance I;
         int32_t T, mT, mU, use_ranker, min_pairs;
-        int merge_mode = 0;
-        std::cin >> I.n >> T >> mT >> mU >> use_ranker >> min_pairs >> merge_mode;
+        int merge_mode = 0, algorithm = 0;
+        std::cin >> I.n >> T >> mT >> mU >> use_ranker >> min_pairs >> merge_mode >> algorithm;
         const size_t nn = (size_t)I.n * I.n;
         I.len.resize(I.n);
         I.off.assign(I.n + 1, 0);
@@ -256,6 +256,7 @@ int main()
         g_buf.clear();
         mock::selection().keep = [](int32_t x, int32_t y) { return g->keep[(size_t)x * g->n + y] != 0; };
         cm_ctx ctx;
+        ctx.greedy_chunk = 1 + (int32_t)((I.n * 7 + T) % 9);     // several chunks per instance
         cm_params prm{};
         prm.T = T;
         prm.mT = mT;
@@ -267,7 +268,8 @@ int main()
         int8_t mat[400] = {};
         uint8_t dummy = 0;
         cm_result* res = nullptr;
-        const int r = cluster_merge(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm, &res, 0);
+        const int r = algorithm ? greedy_cluster(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm, &res, 0)
+                                : cluster_merge(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm, &res, 0);
         if (r) {
             std::printf("error %d %s\n", r, ctx.err.c_str());
             continue;

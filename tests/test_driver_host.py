@@ -9,8 +9,9 @@ transposed blocks of long representatives and the device-planned lists of ranked
 checked on hundreds of random merge trees, including ones the GPU tests never reach.  The
 oracle runs Algorithm 2 with the same similarity (`score`, `transitive` and the pruning hook
 `keep`); clusters with their member order, similar pairs and all comparison counts must be
-identical, for sequential merges and for independent partial merges (CM_MERGE_PARTIAL, the
-oracle's merge_partial)."""
+identical, for sequential merges, for independent partial merges (CM_MERGE_PARTIAL, the
+oracle's merge_partial) and for the incremental greedy clustering (greedy_cluster, the
+oracle's greedy)."""
 import importlib
 import os
 import shutil
@@ -20,6 +21,7 @@ import numpy as np
 import pytest
 
 ocm = importlib.import_module("oracle.cluster_merge")   # the module (the package re-exports a function of that name)
+ogr = importlib.import_module("oracle.greedy")
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_1908_10574_gb300", "csrc")
@@ -66,15 +68,18 @@ def _instance(rng):
     use_ranker = int(rng.random() < 0.5)
     min_pairs = int(rng.choice([0, 1, 4, 30]))
     partial = int(rng.random() < 0.4)
+    greedy = int(rng.random() < 0.25)
+    if greedy:
+        use_ranker = partial = 0
     return dict(n=n, T=T, mT=mT, mU=mU, use_ranker=use_ranker, min_pairs=min_pairs, L=L, M=M,
-                cov=cov, keep=keep, partial=partial)
+                cov=cov, keep=keep, partial=partial, greedy=greedy)
 
 
 def _serialise(insts):
     out = [str(len(insts))]
     for d in insts:
-        out.append("%d %d %d %d %d %d %d" % (d["n"], d["T"], d["mT"], d["mU"], d["use_ranker"],
-                                            d["min_pairs"], d["partial"]))
+        out.append("%d %d %d %d %d %d %d %d" % (d["n"], d["T"], d["mT"], d["mU"], d["use_ranker"],
+                                               d["min_pairs"], d["partial"], d["greedy"]))
         for key in ("L", "M", "cov", "keep"):
             out.append(" ".join(str(int(v)) for v in np.asarray(d[key]).reshape(-1)))
     return "\n".join(out) + "\n"
@@ -120,8 +125,11 @@ def _oracle(d):
         return int(L[r1] - cov[r1, r2]) < mU, int(L[r2] - cov[r2, r1]) < mU
 
     kf = (lambda a, b: bool(keep[a, b])) if d["use_ranker"] else None
-    final, stats = ocm.bottom_up_merge(d["n"], score, transitive, T, keep=kf,
-                                       min_pairs=d["min_pairs"], partial=bool(d["partial"]))
+    if d["greedy"]:
+        final, stats = ogr.greedy(d["n"], score, lambda x, r: int(L[x] - cov[x, r]), T, mT, mU)
+    else:
+        final, stats = ocm.bottom_up_merge(d["n"], score, transitive, T, keep=kf,
+                                           min_pairs=d["min_pairs"], partial=bool(d["partial"]))
     pairs = ocm.intra_cluster_pairs(final, score, T, stats)
     clusters = [(c.rep, list(c.objs)) for c in final]
     return clusters, [tuple(map(int, p)) for p in pairs.tolist()], \
@@ -142,7 +150,7 @@ def test_driver_replay_matches_oracle(tmp_path):
                          timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     got = _parse(out.stdout, len(insts))
-    exercised = {"ranked": 0, "full": 0, "exchange": 0, "long": 0, "partial": 0}
+    exercised = {"ranked": 0, "full": 0, "exchange": 0, "long": 0, "partial": 0, "greedy": 0}
     for d, g in zip(insts, got):
         want = _oracle(d)
         assert g[0] == want[0], ("clusters", d["n"], d["use_ranker"])
@@ -153,4 +161,5 @@ def test_driver_replay_matches_oracle(tmp_path):
         exercised["exchange"] += want[2][4] > 0
         exercised["long"] += bool((d["L"] > 4096).any())
         exercised["partial"] += d["partial"] and want[2][3] > 0 and want[2][4] > 0
+        exercised["greedy"] += d["greedy"] and want[2][3] > 0 and d["n"] > 8
     assert min(exercised.values()) >= 20, exercised
