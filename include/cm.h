@@ -25,7 +25,11 @@
  *     CM_ERR_OOM before any output is written.
  *   - Matrix: 400 int8 entries, row-major, matrix[x*20 + y] = score of residue x of the
  *     pair's FIRST sequence against residue y of its SECOND sequence.  Entries must lie in
- *     [-1000, 1000]; it need not be symmetric.
+ *     [-1000, 1000]; it need not be symmetric.  With CM_MATRIX24 the matrix has 576 entries
+ *     (matrix[x*24 + y]) over the 24 letters ARNDCQEGHILKMFPSTWYVBZX* (B = D or N, Z = E or Q,
+ *     X = any, * = stop; the layout of the published 24 x 24 tables), residue codes may be
+ *     0..23 and CM_ASCII also accepts B, Z, X and *.  The learned ranker embeds codes 20..23
+ *     as zero vectors.
  *   - Gaps: 1 <= first-gap cost (gap_open, or gap_open+gap_extend with CM_GAP_BLAST) <= 1000,
  *     0 <= gap_extend <= first-gap cost.
  *   - Pointers: host memory by default; with CM_DEVICE_PTRS every array argument is device
@@ -60,6 +64,7 @@ extern "C" {
 #define CM_ASCII          0x2u  /* seqs holds ASCII letters (upper or lower case) */
 #define CM_GAP_BLAST      0x4u  /* gap of k residues costs open + k*extend */
 #define CM_FORCE_INT32    0x8u  /* score every pair on the int32 path (no int16x2 first pass) */
+#define CM_MATRIX24       0x40u /* 24 x 24 matrix over ARNDCQEGHILKMFPSTWYVBZX* (codes 0..23) */
 #define CM_TRAIN_COMPONENTS 0x10u /* cm_ranker_train: batches hold whole components of the pair graph */
 #define CM_TRAIN_COSINE   0x20u /* cm_ranker_train: learning rate warms up over the first 2 % of the
                                    steps, then follows a half cosine from lr down to 0 */

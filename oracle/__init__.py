@@ -60,8 +60,14 @@ def _lib():
 
 
 def _matrix(S):
-    S = np.ascontiguousarray(np.asarray(S, dtype=np.int32).reshape(20, 20))
-    return S
+    """The 24 x 24 int32 table the C code reads: a 24 x 24 matrix as given, a 20 x 20 one in
+    its top-left corner (rows and columns of B, Z, X, * unused then)."""
+    S = np.asarray(S, dtype=np.int32)
+    k = int(round(np.sqrt(S.size)))
+    assert k * k == S.size and k in (20, 24), "matrix must be 20 x 20 or 24 x 24"
+    out = np.zeros((24, 24), dtype=np.int32)
+    out[:k, :k] = S.reshape(k, k)
+    return np.ascontiguousarray(out)
 
 
 def _codes(x):

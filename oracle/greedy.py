@@ -63,7 +63,8 @@ def greedy_cluster(seqs, offsets, S, gap_open, gap_extend, T, mT, mU, gap_mode=0
     dict(clusters=[(rep, [members...]) ...], pairs=(k, 3) array, stats=dict)."""
     from . import sw_score, sw_cells, uncovered
 
-    S = np.asarray(S, dtype=np.int32).reshape(20, 20)
+    S = np.asarray(S, dtype=np.int32)
+    S = S.reshape(int(round(np.sqrt(S.size))), -1)
     n = len(offsets) - 1
     offsets = np.asarray(offsets, dtype=np.int64)
     seqs = np.asarray(seqs, dtype=np.uint8)

@@ -11,7 +11,8 @@
  *   gap_mode 0: a gap of k residues costs o + (k-1)*e
  *   gap_mode 1: a gap of k residues costs o + k*e            (BLAST-style)
  *
- * Recurrences over a (rows i = 1..m) and b (columns j = 1..n), S[x*20+y] = score(x, y):
+ * Recurrences over a (rows i = 1..m) and b (columns j = 1..n), S[x*24+y] = score(x, y) (a
+ * 24 x 24 table over ARNDCQEGHILKMFPSTWYVBZX*; 20-letter matrices fill its top-left corner):
  *   E(i,j) = max(E(i,j-1) - e, H(i,j-1) - g1)     horizontal gap, g1 = cost of a 1-gap
  *   F(i,j) = max(F(i-1,j) - e, H(i-1,j) - g1)     vertical gap
  *   H(i,j) = max(0, H(i-1,j-1) + S(a_i, b_j), E(i,j), F(i,j))
@@ -50,7 +51,7 @@ static int64_t gotoh(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n, i
             uint8_t bj_res = reverse ? b[n - j] : b[j - 1];
             E = max64(E - e, Hcur[j - 1] - g1);
             F[j] = max64(F[j] - e, Hprev[j] - g1);
-            int64_t h = Hprev[j - 1] + (int64_t)S[ai * 20 + bj_res];
+            int64_t h = Hprev[j - 1] + (int64_t)S[ai * 24 + bj_res];
             h = max64(h, E);
             h = max64(h, F[j]);
             h = max64(h, 0);
@@ -124,7 +125,7 @@ int64_t cm_oracle_sw_align(const uint8_t *a, int64_t m, const uint8_t *b, int64_
         for (int64_t j = 1; j <= q; j++) {
             E[i * W + j] = max64(H[i * W + j - 1] - g1, E[i * W + j - 1] - e);
             F[i * W + j] = max64(H[(i - 1) * W + j] - g1, F[(i - 1) * W + j] - e);
-            int64_t h = H[(i - 1) * W + j - 1] + (int64_t)S[A[i - 1] * 20 + B[j - 1]];
+            int64_t h = H[(i - 1) * W + j - 1] + (int64_t)S[A[i - 1] * 24 + B[j - 1]];
             h = max64(h, F[i * W + j]);
             h = max64(h, E[i * W + j]);
             H[i * W + j] = h;
@@ -138,7 +139,7 @@ int64_t cm_oracle_sw_align(const uint8_t *a, int64_t m, const uint8_t *b, int64_
         if (i == 0) { rev[len++] = 2; j--; continue; }
         if (j == 0) { rev[len++] = 1; i--; continue; }
         if (state == 0) {
-            if (H[i * W + j] == H[(i - 1) * W + j - 1] + (int64_t)S[A[i - 1] * 20 + B[j - 1]]) {
+            if (H[i * W + j] == H[(i - 1) * W + j - 1] + (int64_t)S[A[i - 1] * 24 + B[j - 1]]) {
                 rev[len++] = 0; i--; j--;
             } else if (H[i * W + j] == F[i * W + j]) {
                 state = 1;

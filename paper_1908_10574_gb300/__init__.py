@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _lib as _L
 from ._lib import (CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS,  # noqa: F401
-                   CM_TRAIN_COMPONENTS, CM_TRAIN_COSINE, CM_MERGE_SEQUENTIAL, CM_MERGE_PARTIAL)
+                   CM_TRAIN_COMPONENTS, CM_TRAIN_COSINE, CM_MERGE_SEQUENTIAL, CM_MERGE_PARTIAL,
+                   CM_MATRIX24)
 
 __all__ = ["Context", "sw_score_batch", "sw_cells_batch", "sw_allpairs", "CMError",
            "default_context", "sw_cells_batch_noalloc", "cluster_merge", "ops_to_cigar"]
@@ -97,13 +98,23 @@ class Context:
                     raise TypeError("device inputs must be contiguous %s" % dt)
             if pairs is not None and (pairs.dtype != torch.int32 or not pairs.is_contiguous()):
                 raise TypeError("device pairs must be contiguous int32")
+            if matrix.numel() not in (400, 576):
+                raise ValueError("matrix must have 400 (20 x 20) or 576 (24 x 24) entries")
             return seqs, offsets, matrix, pairs
         seqs = self._host(seqs, np.uint8)
         offsets = self._host(offsets, np.int64)
-        matrix = self._host(matrix, np.int8, (400,))
+        matrix = self._host(matrix, np.int8, (-1,))
+        if matrix.size not in (400, 576):
+            raise ValueError("matrix must have 400 (20 x 20) or 576 (24 x 24) entries")
         if pairs is not None:
             pairs = self._host(pairs, np.int32, (-1, 2))
         return seqs, offsets, matrix, pairs
+
+    @staticmethod
+    def _matrix_flag(matrix):
+        """CM_MATRIX24 for a 24 x 24 matrix (576 entries), else 0."""
+        n = matrix.numel() if hasattr(matrix, "numel") else matrix.size
+        return CM_MATRIX24 if n == 576 else 0
 
     def stats(self):
         s = _L.cm_stats()
@@ -125,6 +136,7 @@ class Context:
         returns (warps_per_cta, rows_per_warp)."""
         seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
         flags |= self._prep([seqs, offsets, matrix])
+        flags |= self._matrix_flag(matrix)
         w, r = ctypes.c_int32(0), ctypes.c_int32(0)
         _L.check(self._h, _L.lib().cm_autotune(
             self._h, _ptr(seqs), _ptr(offsets), int(offsets.shape[0]) - 1, _ptr(matrix),
@@ -149,6 +161,7 @@ class Context:
                        out=None):
         seqs, offsets, matrix, pairs = self._inputs(seqs, offsets, matrix, pairs)
         flags |= self._prep([seqs, offsets, matrix, pairs])
+        flags |= self._matrix_flag(matrix)
         n = int(offsets.shape[0]) - 1
         npairs = int(pairs.shape[0])
         if out is None:
@@ -167,6 +180,7 @@ class Context:
                        out=None):
         seqs, offsets, matrix, pairs = self._inputs(seqs, offsets, matrix, pairs)
         flags |= self._prep([seqs, offsets, matrix, pairs])
+        flags |= self._matrix_flag(matrix)
         n = int(offsets.shape[0]) - 1
         npairs = int(pairs.shape[0])
         if out is None:
@@ -188,6 +202,7 @@ class Context:
         1 = I, 2 = D (see ops_to_cigar)."""
         seqs, offsets, matrix, pairs = self._inputs(seqs, offsets, matrix, pairs)
         flags |= self._prep([seqs, offsets, matrix, pairs])
+        flags |= self._matrix_flag(matrix)
         if flags & CM_DEVICE_PTRS:
             raise TypeError("sw_align_batch takes host arrays")
         n = int(offsets.shape[0]) - 1
@@ -215,6 +230,7 @@ class Context:
         Returns (pairs (k, 2) int32, scores (k,) int32)."""
         seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
         flags |= self._prep([seqs, offsets, matrix])
+        flags |= self._matrix_flag(matrix)
         n = int(offsets.shape[0]) - 1
         found = ctypes.c_int64(0)
         dev = bool(flags & CM_DEVICE_PTRS)
@@ -250,6 +266,7 @@ class Context:
         (k, 3) int64 (i, j, score) sorted, and the comparison counters."""
         seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
         flags |= self._prep([seqs, offsets, matrix])
+        flags |= self._matrix_flag(matrix)
         n = int(offsets.shape[0]) - 1
         prm = _L.cm_params(int(T), int(mT), int(mU), int(bool(use_ranker)), float(prune_logit),
                            int(ranker_min_pairs), int(merge_mode))
@@ -264,6 +281,7 @@ class Context:
         intra-cluster all-against-all; same result dict as cluster_merge."""
         seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
         flags |= self._prep([seqs, offsets, matrix])
+        flags |= self._matrix_flag(matrix)
         n = int(offsets.shape[0]) - 1
         prm = _L.cm_params(int(T), int(mT), int(mU), 0, 0.0, 0, 0)
         res = ctypes.POINTER(_L.cm_result)()

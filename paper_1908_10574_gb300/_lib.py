@@ -17,6 +17,7 @@ CM_GAP_BLAST = 0x4
 CM_FORCE_INT32 = 0x8
 CM_TRAIN_COMPONENTS = 0x10
 CM_TRAIN_COSINE = 0x20
+CM_MATRIX24 = 0x40
 CM_MERGE_SEQUENTIAL = 0
 CM_MERGE_PARTIAL = 1
 

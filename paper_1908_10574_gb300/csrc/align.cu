@@ -25,7 +25,7 @@ namespace cm {
 namespace {
 
 struct AlnMatrix {
-    int16_t v[400];
+    int16_t v[kAlpha * kAlpha];
 };
 
 struct AlnJob {
@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(128) align_kernel(const uint8_t* __restrict__ 
                                                     int32_t* __restrict__ nops,
                                                     int32_t* __restrict__ err)
 {
-    __shared__ int16_t mat[400];
-    for (int i = threadIdx.x; i < 400; i += blockDim.x) mat[i] = mat_in.v[i];
+    __shared__ int16_t mat[kAlpha * kAlpha];
+    for (int i = threadIdx.x; i < kAlpha * kAlpha; i += blockDim.x) mat[i] = mat_in.v[i];
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= njobs) return;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(128) align_kernel(const uint8_t* __restrict__ 
         Frow[j] = kAlnNeg;
     }
     for (int i = 1; i <= p; ++i) {
-        const int16_t* srow = mat + A[i - 1] * 20;
+        const int16_t* srow = mat + A[i - 1] * kAlpha;
         int32_t diag = Hrow[0];                   // H(i-1, 0)
         int32_t hleft = -(g1 + (i - 1) * ge);     // H(i, 0)
         Hrow[0] = hleft;

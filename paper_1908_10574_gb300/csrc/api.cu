@@ -73,19 +73,23 @@ int prepare(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_se
                                    "0 <= gap_extend <= first-gap cost");
     P.g1 = (int32_t)g1;
     P.ge = gap_extend;
-    // matrix
-    int8_t hm[400];
-    if (dev) CUDA_TRY(cudaMemcpy(hm, matrix, 400, cudaMemcpyDeviceToHost));
-    else std::memcpy(hm, matrix, 400);
+    // matrix: 20 x 20, or 24 x 24 over ARNDCQEGHILKMFPSTWYVBZX* with CM_MATRIX24; either sits
+    // in the 24 x 24 table the kernels read (a 20 x 20 one in its top-left corner)
+    const int A = (flags & CM_MATRIX24) ? kAlpha : 20;
+    P.alpha = A;
+    int8_t hm[kAlpha * kAlpha];
+    if (dev) CUDA_TRY(cudaMemcpy(hm, matrix, (size_t)A * A, cudaMemcpyDeviceToHost));
+    else std::memcpy(hm, matrix, (size_t)A * A);
     int mn = 0, mx = 0;
-    for (int i = 0; i < 400; ++i) {
-        P.mat[i] = hm[i];
-        mn = std::min<int>(mn, hm[i]);
-        mx = std::max<int>(mx, hm[i]);
-    }
-    for (int x = 0; x < 20; ++x)
-        for (int y = 0; y < 20; ++y)
-            if (hm[x * 20 + y] != hm[y * 20 + x]) P.symmetric = false;
+    for (int i = 0; i < kAlpha * kAlpha; ++i) P.mat[i] = 0;
+    for (int x = 0; x < A; ++x)
+        for (int y = 0; y < A; ++y) {
+            const int8_t v = hm[x * A + y];
+            P.mat[x * kAlpha + y] = v;
+            mn = std::min<int>(mn, v);
+            mx = std::max<int>(mx, v);
+            if (v != hm[y * A + x]) P.symmetric = false;
+        }
     P.beta = std::max<int32_t>(P.g1 + P.ge, -mn) + 1;
     P.sat_thr = 32767 - std::max(mx, 0);
     return prepare_seqs(c, seqs, offsets, n_seqs, flags, P);
@@ -128,16 +132,16 @@ int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t
             if (r) return r;
             src = raw;
         }
-        CUDA_TRY(launch_ascii_to_codes(src, db, total, flags_d, c->stream));
+        CUDA_TRY(launch_ascii_to_codes(src, db, total, P.alpha, flags_d, c->stream));
         P.db = db;
     } else if (dev) {
         P.db = seqs;
-        CUDA_TRY(launch_check_codes(seqs, total, flags_d, c->stream));
+        CUDA_TRY(launch_check_codes(seqs, total, P.alpha, flags_d, c->stream));
     } else {
         ENSURE(B_DB, total, db);
         int r = copy_in(c, db, seqs, total, false);
         if (r) return r;
-        CUDA_TRY(launch_check_codes(db, total, flags_d, c->stream));
+        CUDA_TRY(launch_check_codes(db, total, P.alpha, flags_d, c->stream));
         P.db = db;
     }
     if (dev) {
@@ -153,8 +157,8 @@ int prepare_seqs(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t
     CUDA_TRY(cudaMemcpyAsync(&bad, flags_d, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (bad) return fail(c, CM_ERR_RESIDUE, (flags & CM_ASCII)
-                                                ? "non-amino-acid letter in seqs"
-                                                : "residue code >= 20 in seqs");
+                                                ? "a letter outside the matrix's alphabet in seqs"
+                                                : "a residue code outside the matrix's alphabet in seqs");
     return CM_OK;
 }
 

@@ -13,15 +13,19 @@ namespace cm {
 
 // ---- residue streams -------------------------------------------------------------------
 // A block's subjects are concatenated into one byte stream, one byte per DP row:
-// bits 0-4 residue code (0..19, 20 = pad row whose scores are all non-positive),
+// bits 0-4 residue code (0..23, 24 = pad row whose scores are all non-positive),
 // bit 7 = first row of a subject, bit 6 = last row of a subject.  Every subject occupies a
 // multiple of kRowGroup rows (pad rows follow it), so subjects start on group boundaries and a
 // kernel step can cover up to kRowGroup rows; an empty subject is one group of pad rows, the
 // first carrying both flags, so its score comes out 0.
 constexpr uint8_t kFirst = 0x80;
 constexpr uint8_t kLast = 0x40;
-constexpr uint8_t kPadCode = 20;
-constexpr int kProfRows = 21;          // 20 residues + pad row
+// Residue codes: ARNDCQEGHILKMFPSTWYV = 0..19, then B, Z, X, * = 20..23 (24-letter matrices,
+// CM_MATRIX24); a 20 x 20 matrix sits in the top-left corner of the 24 x 24 one every kernel
+// reads, and calls with it accept codes 0..19 only.
+constexpr int kAlpha = 24;             // letters of the largest alphabet (matrix stride)
+constexpr uint8_t kPadCode = 24;
+constexpr int kProfRows = 25;          // 24 residues + pad row
 
 // rows a subject of `len` residues occupies in a stream: a multiple of kRowGroup (at least
 // one group), so subjects start on group boundaries and a kernel step can cover a group
@@ -90,7 +94,7 @@ struct SwArgs {
     uint2* bnd;                 // multi-pass boundary columns, bnd_stride rows per warp
     int64_t bnd_stride;
     int32_t* err;               // set non-zero by a kernel's own bounds checks
-    int16_t mat[400];           // substitution matrix
+    int16_t mat[kAlpha * kAlpha];   // substitution matrix, [first residue][second residue]
     int32_t gap_open;           // first-gap cost (already includes extend for BLAST mode)
     int32_t gap_extend;
     int32_t beta;               // int16 bias: stored = true + beta
@@ -150,9 +154,11 @@ cudaError_t launch_cells_wf(int grid, const SwArgs& a, const CellJob* jobs, int3
                             int32_t* counter, int32_t* res, cudaStream_t st);
 
 // ---- pack.cu ---------------------------------------------------------------------------
-cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t* bad,
-                                  cudaStream_t st);
-cudaError_t launch_check_codes(const uint8_t* in, int64_t n, int32_t* bad, cudaStream_t st);
+// letters of the 20-letter alphabet (alpha 20) or also B, Z, X, * (alpha 24) -> codes
+cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t alpha,
+                                  int32_t* bad, cudaStream_t st);
+cudaError_t launch_check_codes(const uint8_t* in, int64_t n, int32_t alpha, int32_t* bad,
+                               cudaStream_t st);
 cudaError_t launch_gather_stream(const uint8_t* db, const int64_t* off, const int32_t* ids,
                                  int32_t nb, const int64_t* srow, uint8_t* stream,
                                  cudaStream_t st);

@@ -103,7 +103,8 @@ struct Prepared {
     const uint8_t* db = nullptr;     // device residue codes
     const int64_t* off = nullptr;    // device offsets
     std::vector<int64_t> hoff;       // host offsets
-    int16_t mat[400];
+    int16_t mat[kAlpha * kAlpha];    // [first][second], stride kAlpha
+    int32_t alpha = 20;              // letters of the call's matrix (20, or 24 with CM_MATRIX24)
     int32_t g1 = 0, ge = 0;          // first-gap cost, extension cost
     int32_t beta = 0, sat_thr = 0;
     bool symmetric = true;

@@ -39,7 +39,7 @@ long_pair_kernel(const __grid_constant__ SwArgs a, const PairRef* __restrict__ p
     constexpr int LS = kLR;                                   // dense rows: 2-way conflicts only
     constexpr int ROWW = 32 * LS;
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int16_t s_mat[400];
+    __shared__ int16_t s_mat[kAlpha * kAlpha];
     __shared__ volatile int32_t s_pass[kLW];                 // pass whose boundary is in slot w
     __shared__ volatile int32_t s_prog[kLW];                 // rows of it written so far
     __shared__ int s_job;
@@ -47,7 +47,7 @@ long_pair_kernel(const __grid_constant__ SwArgs a, const PairRef* __restrict__ p
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int32_t* prof = reinterpret_cast<int32_t*>(smem) + (size_t)warp * kProfRows * ROWW;
     uint8_t* qres = smem + (size_t)kLW * kProfRows * ROWW * 4 + (size_t)warp * G::COLS;
-    for (int i = tid; i < 400; i += kLW * 32) s_mat[i] = a.mat[i];
+    for (int i = tid; i < kAlpha * kAlpha; i += kLW * 32) s_mat[i] = a.mat[i];
     const int o = a.gap_open, ge = a.gap_extend;
     int2* slots = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * kLW * a.bnd_stride);
 
@@ -99,7 +99,7 @@ long_pair_kernel(const __grid_constant__ SwArgs a, const PairRef* __restrict__ p
                 const int q = qres[c];
                 int32_t s = kSpad;
                 if (x != kPadCode && q != kPadCode)
-                    s = (CELLS || J.swap) ? s_mat[x * 20 + q] : s_mat[q * 20 + x];
+                    s = (CELLS || J.swap) ? s_mat[x * kAlpha + q] : s_mat[q * kAlpha + x];
                 prof[x * ROWW + ln * LS + k] = s;
             }
             __syncwarp();

@@ -18,16 +18,18 @@ __device__ __forceinline__ int64_t tri_row(int64_t v)
 }
 
 __global__ void ascii_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                             int64_t n, int32_t* bad)
+                             int64_t n, int32_t alpha, int32_t* bad)
 {
-    // ARNDCQEGHILKMFPSTWYV -> 0..19, case-insensitive; anything else flags `bad`
+    // ARNDCQEGHILKMFPSTWYV -> 0..19 (and with alpha 24: B, Z, X, * -> 20..23), letters
+    // case-insensitive; anything else flags `bad`
     __shared__ uint8_t lut[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = 255;
     __syncthreads();
-    if (threadIdx.x < 20) {
-        const char* A = "ARNDCQEGHILKMFPSTWYV";
-        lut[(uint8_t)A[threadIdx.x]] = (uint8_t)threadIdx.x;
-        lut[(uint8_t)(A[threadIdx.x] + 32)] = (uint8_t)threadIdx.x;
+    if (threadIdx.x < alpha) {
+        const char* A = "ARNDCQEGHILKMFPSTWYVBZX*";
+        const uint8_t ch = (uint8_t)A[threadIdx.x];
+        lut[ch] = (uint8_t)threadIdx.x;
+        if (ch >= 'A' && ch <= 'Z') lut[ch + 32] = (uint8_t)threadIdx.x;
     }
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -38,11 +40,12 @@ __global__ void ascii_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict
     }
 }
 
-__global__ void check_kernel(const uint8_t* __restrict__ in, int64_t n, int32_t* bad)
+__global__ void check_kernel(const uint8_t* __restrict__ in, int64_t n, int32_t alpha,
+                             int32_t* bad)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        if (in[i] >= 20) atomicExch(bad, 1);
+        if (in[i] >= alpha) atomicExch(bad, 1);
 }
 
 // one warp per subject: copy its residues into the block stream with first/last flags
@@ -282,18 +285,19 @@ int grid_for(int64_t n, int threads)
 
 }  // namespace
 
-cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t* bad,
-                                  cudaStream_t st)
+cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t alpha,
+                                  int32_t* bad, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    ascii_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, bad);
+    ascii_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n, alpha, bad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_check_codes(const uint8_t* in, int64_t n, int32_t* bad, cudaStream_t st)
+cudaError_t launch_check_codes(const uint8_t* in, int64_t n, int32_t alpha, int32_t* bad,
+                               cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    check_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, n, bad);
+    check_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, n, alpha, bad);
     return cudaGetLastError();
 }
 

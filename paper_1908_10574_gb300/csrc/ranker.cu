@@ -68,27 +68,6 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
-                                        const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
-                                          const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // sum the per-chunk partials into the gradient vector (first M rows of the padded tile)
 __global__ void reduce_parts_kernel(const float* __restrict__ part, int64_t nchunks, int MPAD,
                                     int M, float* __restrict__ grad)
@@ -286,74 +265,84 @@ __global__ void unit_rows_kernel(const float* __restrict__ V, int64_t n, bf16* _
     for (int c = lane; c < kCh; c += 32) U[i * kCh + c] = __float2bfloat16(V[i * kCh + c] * inv);
 }
 
-// Pair selection: for every tile (block, 128 A rows x 128 B rows) compute the logits
-// alpha * <U_a, U_b> + beta on tensor cores and append the pairs at or above `thr`.
-__global__ void __launch_bounds__(256) pairsel_kernel(const bf16* __restrict__ U,
-                                                      const int32_t* __restrict__ rows,
-                                                      const SelTile* __restrict__ tiles,
-                                                      const float* __restrict__ ab, float thr,
-                                                      uint32_t* __restrict__ bitmap)
+// Pair selection: for every tile (128 A rows x 128 B rows of a block) the logits
+// alpha * <U_a, U_b> + beta on the tensor cores (tcgen05.mma, M = N = 128, K = 128 in eight
+// steps of 16, FP32 accumulator in TMEM) and the bits of the pairs at or above `thr`.  The
+// rows are gathered by index with cp.async into the 128-byte-swizzled K-major layout the MMA
+// reads (16-byte chunk c of row r at chunk position c ^ (r & 7), two 64-channel halves of
+// 16 KB per operand), made visible to the tensor core's proxy by a proxy fence.  Tiles start
+// at multiples of 128 columns, so every thread (one A row) ORs whole bitmap words.
+__global__ void __launch_bounds__(128) pairsel_tc_kernel(const bf16* __restrict__ U,
+                                                         const int32_t* __restrict__ rows,
+                                                         const SelTile* __restrict__ tiles,
+                                                         const float* __restrict__ ab, float thr,
+                                                         uint32_t* __restrict__ bitmap,
+                                                         int32_t* err)
 {
-    constexpr int Str = kCh + 8;
-    __shared__ __align__(16) bf16 sA[128 * Str];
-    __shared__ __align__(16) bf16 sB[128 * Str];
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 128, false, false);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;                   // [2 halves][128 rows][128 B]
+    uint8_t* sB = smem + 32768;
+    __shared__ __align__(8) uint64_t done;
+    __shared__ uint32_t tmem_slot;
     const SelTile T = tiles[blockIdx.x];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int id = tid; id < 128 * 16; id += 256) {
-        const int i = id >> 4, part = id & 15;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        tc::mbar_init(&done, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 2) tc::tmem_alloc(&tmem_slot, 128);
+    // gather: 128 rows x 16 chunks of 16 bytes per operand
+    for (int id = tid; id < 128 * 16; id += 128) {
+        const int i = id >> 4, c16 = id & 15, h = c16 >> 3, c = c16 & 7;
+        const uint32_t dst = (uint32_t)(h * 16384 + i * 128 + ((c ^ (i & 7)) << 4));
         const bool oka = i < T.na, okb = i < T.nb;
         const int32_t ra = oka ? rows[T.a + i] : 0, rb = okb ? rows[T.b + i] : 0;
-        cp_async16(&sA[i * Str + part * 8], U + (int64_t)ra * kCh + part * 8, oka);
-        cp_async16(&sB[i * Str + part * 8], U + (int64_t)rb * kCh + part * 8, okb);
+        cp_async16(sA + dst, U + (int64_t)ra * kCh + c16 * 8, oka);
+        cp_async16(sB + dst, U + (int64_t)rb * kCh + c16 * 8, okb);
     }
     cp_commit();
     cp_wait0();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    tc::fence_before_sync();
     __syncthreads();
-    const int wm0 = (warp % 4) * 32, wn0 = (warp / 4) * 64;
-    float acc[2][8][4];
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    if (tid == 32) {
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+        for (int k = 0; k < 8; ++k) {
+            const int off = (k >> 2) * 16384 + (k & 3) * 32;
+            tc::mma_bf16(tmem, tc::smem_desc(sA + off, 16, 1024, tc::kSwizzle128),
+                         tc::smem_desc(sB + off, 16, 1024, tc::kSwizzle128), IDESC, k != 0);
+        }
+        tc::mma_commit(&done);
+    }
+    __syncwarp();
+    const bool ok = tc::mbar_wait(&done, 0, err);
+    tc::fence_after_sync();
+    if (__all_sync(0xffffffffu, ok)) {
+        const float alpha = ab[0], beta = ab[1];
+        const int i = warp * 32 + lane;
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
+            uint32_t mask = 0;
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < kCh; ks += 16) {
-        uint32_t af[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-            ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
-                    &sA[(wm0 + mt * 16 + (lane & 15)) * Str + ks + (lane >> 4) * 8]);
-#pragma unroll
-        for (int np = 0; np < 4; ++np) {
-            uint32_t b0, b1, b2, b3;
-            ldsm_x4(b0, b1, b2, b3,
-                    &sB[(wn0 + np * 16 + (lane & 7) + (lane >> 4) * 8) * Str + ks +
-                        ((lane >> 3) & 1) * 8]);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                mma_bf16(acc[mt][2 * np], af[mt], b0, b1);
-                mma_bf16(acc[mt][2 * np + 1], af[mt], b2, b3);
-            }
+            for (int q = 0; q < 32; ++q)
+                if (ch * 32 + q < T.nb && alpha * v[q] + beta >= thr) mask |= 1u << q;
+            if (i < T.na && mask)
+                atomicOr(&bitmap[T.bits + (int64_t)(T.i0 + i) * T.words + ((T.j0 + ch * 32) >> 5)], mask);
         }
     }
-    const float alpha = ab[0], beta = ab[1];
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int i = wm0 + mt * 16 + g + (q >> 1) * 8;
-                const int j = wn0 + nt * 8 + 2 * t + (q & 1);
-                const float z = alpha * acc[mt][nt][q] + beta;
-                if (i < T.na && j < T.nb && z >= thr) {
-                    const int32_t bi = T.i0 + i, bj = T.j0 + j;
-                    atomicOr(&bitmap[T.bits + (int64_t)bi * T.words + (bj >> 5)], 1u << (bj & 31));
-                }
-            }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 2) tc::tmem_free(tmem, 128);
 }
+
+constexpr int kPairselSmem = 65536 + 1024;
 
 }  // namespace
 
@@ -797,15 +786,18 @@ int ranker_select(cm_ctx* c, const void* Uv, const std::vector<int32_t>& rows,
     if ((r = copy_in(c, d_rows, rows.data(), rows.size() * 4, false))) return r;
     if ((r = copy_in(c, d_tiles, tiles.data(), tiles.size() * sizeof(SelTile), false))) return r;
     CUDA_TRY(cudaMemsetAsync(d_bits, 0, nwords * 4, c->stream));
+    CUDA_TRY(cudaFuncSetAttribute(pairsel_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kPairselSmem));
     for (size_t t0 = 0; t0 < tiles.size(); t0 += 65535) {
         const unsigned nt = (unsigned)std::min<size_t>(65535, tiles.size() - t0);
-        pairsel_kernel<<<nt, 256, 0, c->stream>>>(U, d_rows, d_tiles + t0, K->params + kOffAlpha,
-                                                  thr, d_bits);
+        pairsel_tc_kernel<<<nt, 128, kPairselSmem, c->stream>>>(U, d_rows, d_tiles + t0,
+                                                                K->params + kOffAlpha, thr,
+                                                                d_bits, K->tc_err);
         c->stats.launches += 1;
     }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(bitmap.data(), d_bits, nwords * 4, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if ((r = check_tc(c, K))) return r;
     if (d_bits_out) *d_bits_out = d_bits;
     if (d_rows_out) *d_rows_out = d_rows;
     return CM_OK;

@@ -161,7 +161,7 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
     const uint32_t BMO2 = (uint32_t)(beta - o) * 0x10001u;   // H - o of an empty prefix; E, F floor
     const uint32_t O2 = (uint32_t)o * 0x10001u;
     const uint32_t NEGE = pack2(-ge, -ge);
-    const uint32_t PADW = 0x14141414u >> (32 - 8 * NR);          // kPadCode in every byte
+    const uint32_t PADW = (kPadCode * 0x01010101u) >> (32 - 8 * NR);   // kPadCode in every byte
     // boundary records of one step: (H - o, E) of the last column of each of its rows, as
     // uint4 pairs of rows (one uint2 when a step has one row)
     constexpr int NB = (NR >= 2) ? NR / 2 : 1;
@@ -357,11 +357,11 @@ sw16_kernel(const __grid_constant__ SwArgs a)
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* prof = reinterpret_cast<uint32_t*>(smem);
     uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;          // [2][COLS]
-    __shared__ int16_t s_mat[400];
+    __shared__ int16_t s_mat[kAlpha * kAlpha];
     __shared__ int s_task[2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < 400; i += W * 32) s_mat[i] = a.mat[i];
+    for (int i = tid; i < kAlpha * kAlpha; i += W * 32) s_mat[i] = a.mat[i];
     if (tid == 0) s_task[0] = atomicAdd(a.task_counter, 1);
     __syncthreads();
 
@@ -420,8 +420,8 @@ sw16_kernel(const __grid_constant__ SwArgs a)
                 const int ql = qres[c], qh = qres[G::COLS + c];
                 int sl = kSpad, sh = TWO ? 0 : kSpad;
                 if (x != kPadCode) {          // +o: the DP keeps H - o as its diagonal input
-                    if (ql != kPadCode) sl = (B.swap ? s_mat[x * 20 + ql] : s_mat[ql * 20 + x]) + a.gap_open;
-                    if (!TWO && qh != kPadCode) sh = (B.swap ? s_mat[x * 20 + qh] : s_mat[qh * 20 + x]) + a.gap_open;
+                    if (ql != kPadCode) sl = (B.swap ? s_mat[x * kAlpha + ql] : s_mat[ql * kAlpha + x]) + a.gap_open;
+                    if (!TWO && qh != kPadCode) sh = (B.swap ? s_mat[x * kAlpha + qh] : s_mat[qh * kAlpha + x]) + a.gap_open;
                 }
                 prof[x * G::ROWW + ln * G::LS + k] = pack2(sl, sh);
             }
@@ -444,9 +444,9 @@ __global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs
     extern __shared__ __align__(16) uint8_t smem[];
     int32_t* prof = reinterpret_cast<int32_t*>(smem);
     uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;
-    __shared__ int16_t s_mat[400];
+    __shared__ int16_t s_mat[kAlpha * kAlpha];
     const int lane = threadIdx.x;
-    for (int i = lane; i < 400; i += 32) s_mat[i] = a.mat[i];
+    for (int i = lane; i < kAlpha * kAlpha; i += 32) s_mat[i] = a.mat[i];
     __syncwarp();
     const int o = a.gap_open, ge = a.gap_extend;
     int2* bnd = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * a.bnd_stride);
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs
                 const int ln = c / R, k = c - ln * R;
                 const int q = qres[c];
                 int s = kSpad;
-                if (x != kPadCode && q != kPadCode) s = P.swap ? s_mat[x * 20 + q] : s_mat[q * 20 + x];
+                if (x != kPadCode && q != kPadCode) s = P.swap ? s_mat[x * kAlpha + q] : s_mat[q * kAlpha + x];
                 prof[x * G::ROWW + ln * G::LS + k] = s;
             }
             __syncwarp();
@@ -559,9 +559,9 @@ __global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ Sw
     extern __shared__ __align__(16) uint8_t smem[];
     int32_t* prof = reinterpret_cast<int32_t*>(smem);
     uint8_t* qres = smem + (size_t)G::PROF_WORDS * 4;
-    __shared__ int16_t s_mat[400];
+    __shared__ int16_t s_mat[kAlpha * kAlpha];
     const int lane = threadIdx.x;
-    for (int i = lane; i < 400; i += 32) s_mat[i] = a.mat[i];
+    for (int i = lane; i < kAlpha * kAlpha; i += 32) s_mat[i] = a.mat[i];
     __syncwarp();
     const int o = a.gap_open, ge = a.gap_extend;
     int2* bnd = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * a.bnd_stride);
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ Sw
                 const int ln = c / R, k = c - ln * R;
                 const int q = qres[c];
                 prof[x * G::ROWW + ln * G::LS + k] =
-                    (x != kPadCode && q != kPadCode) ? s_mat[x * 20 + q] : kSpad;
+                    (x != kPadCode && q != kPadCode) ? s_mat[x * kAlpha + q] : kSpad;
             }
             __syncwarp();
             int32_t hp[R], fp[R];

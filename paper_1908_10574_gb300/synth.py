@@ -47,6 +47,56 @@ BLOSUM62 = np.array([
     [ 0, -3, -3, -3, -1, -2, -2, -3, -3,  3,  1, -2,  1, -1, -2, -2,  0, -3, -1,  4],  # V
 ], dtype=np.int8)
 
+#: the 24-letter alphabet of the published 24 x 24 tables: B = D or N, Z = E or Q, X = any,
+#: * = stop (residue codes 20..23)
+ALPHABET24 = ALPHABET + "BZX*"
+
+#: BLOSUM62 over ALPHABET24 (published NCBI table: the 20 x 20 block above plus B, Z, X, *)
+BLOSUM62_24 = np.zeros((24, 24), dtype=np.int8)
+BLOSUM62_24[:20, :20] = BLOSUM62
+_B62_EXTRA = {
+    "B": [-2, -1, 3, 4, -3, 0, 1, -1, 0, -3, -4, 0, -3, -3, -2, 0, -1, -4, -3, -3, 4, 1, -1, -4],
+    "Z": [-1, 0, 0, 1, -3, 3, 4, -2, 0, -3, -3, 1, -1, -3, -1, 0, -1, -3, -2, -2, 1, 4, -1, -4],
+    "X": [0, -1, -1, -1, -2, -1, -1, -1, -1, -1, -1, -1, -1, -1, -2, 0, 0, -2, -1, -1, -1, -1, -1, -4],
+    "*": [-4] * 23 + [1],
+}
+for _k, _row in enumerate("BZX*"):
+    BLOSUM62_24[20 + _k, :] = _B62_EXTRA[_row]
+    BLOSUM62_24[:, 20 + _k] = _B62_EXTRA[_row]
+
+#: PAM250 (Dayhoff et al. 1978, the matrix the paper clusters with, Sec. 4) over ALPHABET24,
+#: rows/columns in the layout of the published NCBI table
+PAM250_24 = np.array([
+    # A   R   N   D   C   Q   E   G   H   I   L   K   M   F   P   S   T   W   Y   V   B   Z   X   *
+    [ 2, -2,  0,  0, -2,  0,  0,  1, -1, -1, -2, -1, -1, -3,  1,  1,  1, -6, -3,  0,  0,  0,  0, -8],  # A
+    [-2,  6,  0, -1, -4,  1, -1, -3,  2, -2, -3,  3,  0, -4,  0,  0, -1,  2, -4, -2, -1,  0, -1, -8],  # R
+    [ 0,  0,  2,  2, -4,  1,  1,  0,  2, -2, -3,  1, -2, -3,  0,  1,  0, -4, -2, -2,  2,  1,  0, -8],  # N
+    [ 0, -1,  2,  4, -5,  2,  3,  1,  1, -2, -4,  0, -3, -6, -1,  0,  0, -7, -4, -2,  3,  3, -1, -8],  # D
+    [-2, -4, -4, -5, 12, -5, -5, -3, -3, -2, -6, -5, -5, -4, -3,  0, -2, -8,  0, -2, -4, -5, -3, -8],  # C
+    [ 0,  1,  1,  2, -5,  4,  2, -1,  3, -2, -2,  1, -1, -5,  0, -1, -1, -5, -4, -2,  1,  3, -1, -8],  # Q
+    [ 0, -1,  1,  3, -5,  2,  4,  0,  1, -2, -3,  0, -2, -5, -1,  0,  0, -7, -4, -2,  3,  3, -1, -8],  # E
+    [ 1, -3,  0,  1, -3, -1,  0,  5, -2, -3, -4, -2, -3, -5,  0,  1,  0, -7, -5, -1,  0,  0, -1, -8],  # G
+    [-1,  2,  2,  1, -3,  3,  1, -2,  6, -2, -2,  0, -2, -2,  0, -1, -1, -3,  0, -2,  1,  2, -1, -8],  # H
+    [-1, -2, -2, -2, -2, -2, -2, -3, -2,  5,  2, -2,  2,  1, -2, -1,  0, -5, -1,  4, -2, -2, -1, -8],  # I
+    [-2, -3, -3, -4, -6, -2, -3, -4, -2,  2,  6, -3,  4,  2, -3, -3, -2, -2, -1,  2, -3, -3, -1, -8],  # L
+    [-1,  3,  1,  0, -5,  1,  0, -2,  0, -2, -3,  5,  0, -5, -1,  0,  0, -3, -4, -2,  1,  0, -1, -8],  # K
+    [-1,  0, -2, -3, -5, -1, -2, -3, -2,  2,  4,  0,  6,  0, -2, -2, -1, -4, -2,  2, -2, -2, -1, -8],  # M
+    [-3, -4, -3, -6, -4, -5, -5, -5, -2,  1,  2, -5,  0,  9, -5, -3, -3,  0,  7, -1, -4, -5, -2, -8],  # F
+    [ 1,  0,  0, -1, -3,  0, -1,  0,  0, -2, -3, -1, -2, -5,  6,  1,  0, -6, -5, -1, -1,  0, -1, -8],  # P
+    [ 1,  0,  1,  0,  0, -1,  0,  1, -1, -1, -3,  0, -2, -3,  1,  2,  1, -2, -3, -1,  0,  0,  0, -8],  # S
+    [ 1, -1,  0,  0, -2, -1,  0,  0, -1,  0, -2,  0, -1, -3,  0,  1,  3, -5, -3,  0,  0, -1,  0, -8],  # T
+    [-6,  2, -4, -7, -8, -5, -7, -7, -3, -5, -2, -3, -4,  0, -6, -2, -5, 17,  0, -6, -5, -6, -4, -8],  # W
+    [-3, -4, -2, -4,  0, -4, -4, -5,  0, -1, -1, -4, -2,  7, -5, -3, -3,  0, 10, -2, -3, -4, -2, -8],  # Y
+    [ 0, -2, -2, -2, -2, -2, -2, -1, -2,  4,  2, -2,  2, -1, -1, -1,  0, -6, -2,  4, -2, -2, -1, -8],  # V
+    [ 0, -1,  2,  3, -4,  1,  3,  0,  1, -2, -3,  1, -2, -4, -1,  0,  0, -5, -3, -2,  3,  2, -1, -8],  # B
+    [ 0,  0,  1,  3, -5,  3,  3,  0,  2, -2, -3,  0, -2, -5,  0,  0, -1, -6, -4, -2,  2,  3, -1, -8],  # Z
+    [ 0, -1,  0, -1, -3, -1, -1, -1, -1, -1, -1, -1, -1, -2, -1,  0,  0, -4, -2, -1, -1, -1, -1, -8],  # X
+    [-8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8, -8,  1],  # *
+], dtype=np.int8)
+
+#: PAM250 restricted to the 20 amino acids (ALPHABET order)
+PAM250 = np.ascontiguousarray(PAM250_24[:20, :20])
+
 #: Background amino-acid frequencies (Robinson & Robinson 1991), ALPHABET order, normalised.
 _BG_RAW = np.array([0.07805, 0.05129, 0.04487, 0.05364, 0.01925, 0.04264, 0.06295, 0.07377,
                     0.02199, 0.05142, 0.09019, 0.05744, 0.02243, 0.03856, 0.05203, 0.07120,
@@ -60,21 +110,22 @@ GAP_EXTEND = 1
 SEED = 1908
 
 _CODE = np.full(256, 255, dtype=np.uint8)
-for _i, _c in enumerate(ALPHABET):
+for _i, _c in enumerate(ALPHABET24):
     _CODE[ord(_c)] = _i
     _CODE[ord(_c.lower())] = _i
 
 
-def encode(s: str) -> np.ndarray:
-    """Map an amino-acid string to residue codes 0..19 (raises on any other letter)."""
+def encode(s: str, alphabet24: bool = False) -> np.ndarray:
+    """Map an amino-acid string to residue codes 0..19 (0..23 with alphabet24: B, Z, X, *
+    too); raises on any other letter."""
     a = _CODE[np.frombuffer(s.encode("ascii"), dtype=np.uint8)]
-    if (a == 255).any():
-        raise ValueError("non-amino-acid letter in %r" % s[:40])
+    if (a == 255).any() or (not alphabet24 and (a >= 20).any()):
+        raise ValueError("letter outside the alphabet in %r" % s[:40])
     return a
 
 
 def decode(codes) -> str:
-    return "".join(ALPHABET[int(c)] for c in codes)
+    return "".join(ALPHABET24[int(c)] for c in codes)
 
 
 class SeqSet:

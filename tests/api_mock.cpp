@@ -184,20 +184,21 @@ int sw16_ctas_per_sm(int, int, int) { return 1; }
 int sw32_ctas_per_sm() { return 1; }
 int cells_wf_ctas_per_sm() { return 1; }
 
-cudaError_t launch_check_codes(const uint8_t* in, int64_t n, int32_t* bad, cudaStream_t)
+cudaError_t launch_check_codes(const uint8_t* in, int64_t n, int32_t alpha, int32_t* bad, cudaStream_t)
 {
     for (int64_t i = 0; i < n; ++i)
-        if (in[i] >= 20) *bad = 1;
+        if (in[i] >= alpha) *bad = 1;
     return cudaSuccess;
 }
 
-cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t* bad,
-                                  cudaStream_t)
+cudaError_t launch_ascii_to_codes(const uint8_t* in, uint8_t* out, int64_t n, int32_t alpha,
+                                  int32_t* bad, cudaStream_t)
 {
-    const char* A = "ARNDCQEGHILKMFPSTWYV";
+    const std::string A = std::string("ARNDCQEGHILKMFPSTWYVBZX*").substr(0, (size_t)alpha);
     for (int64_t i = 0; i < n; ++i) {
-        const char* p = std::strchr(A, in[i] >= 'a' && in[i] <= 'z' ? in[i] - 32 : in[i]);
-        if (!p || !in[i]) { *bad = 1; out[i] = 0; } else out[i] = (uint8_t)(p - A);
+        const char ch = in[i] >= 'a' && in[i] <= 'z' ? (char)(in[i] - 32) : (char)in[i];
+        const size_t p = A.find(ch);
+        if (p == std::string::npos || !in[i]) { *bad = 1; out[i] = 0; } else out[i] = (uint8_t)p;
     }
     return cudaSuccess;
 }
