@@ -91,6 +91,7 @@ struct Driver {
     }
 
     int run_round(const std::vector<Merge>& ms);
+    bool partial_mode() const { return prm.merge_mode == CM_MERGE_PARTIAL; }
     int score_ranked(const std::vector<Merge>& ms, const std::vector<char>& ranked,
                      const std::vector<uint32_t>& bitmap, const std::vector<int64_t>& bitbase,
                      const std::vector<int64_t>& words, const std::vector<int64_t>& repb0,
@@ -219,14 +220,11 @@ int Driver::run_round(const std::vector<Merge>& ms)
             ++batches;
         }
     }
-    std::vector<int32_t> ids;
-    std::vector<BlockReq> req;
     // Plain merges: queries = cs1 reps (length order) against the cs2 reps in set order.  A
     // subject is one warp's stream and cannot be split, so cs2 reps longer than kLongSubject
     // become queries of a second block against the cs1 reps instead (f is symmetric here).
     std::vector<std::vector<int32_t>> qorder(nm), sorder(nm);   // block rows / subjects -> index
     std::vector<std::vector<int32_t>> lorder(nm);                 // long cs2 reps (queries)
-    std::vector<std::pair<int32_t, int32_t>> owner;        // plain blocks: (merge, 0 | 1 transposed)
     for (size_t m = 0; m < nm; ++m) {
         const auto& cs1 = sets[ms[m].left];
         const auto& cs2 = sets[ms[m].right];
@@ -243,53 +241,161 @@ int Driver::run_round(const std::vector<Merge>& ms)
         for (int32_t i2 = 0; i2 < (int32_t)cs2.size(); ++i2)
             (P.len(arena[cs2[i2]].rep) > kLongSubject ? lorder[m] : sorder[m]).push_back(i2);
         by_len(cs2, lorder[m]);
-        if (!sorder[m].empty()) {
-            BlockReq b{};
-            b.kind = kCross;
-            b.swap = 0;                                      // pair (rep1, rep2)
-            b.a_begin = (int64_t)ids.size();
-            b.a_count = (int64_t)cs1.size();
-            for (int32_t k : order) ids.push_back(arena[cs1[k]].rep);
-            b.b_begin = (int64_t)ids.size();
-            b.b_count = (int64_t)sorder[m].size();
-            for (int32_t i2 : sorder[m]) ids.push_back(arena[cs2[i2]].rep);
-            req.push_back(b);
-            owner.push_back({(int32_t)m, 0});
-        }
-        if (!lorder[m].empty()) {
-            BlockReq b{};
-            b.kind = kCross;
-            b.swap = 1;                                      // pair (rep1, rep2) = (subject, query)
-            b.a_begin = (int64_t)ids.size();
-            b.a_count = (int64_t)lorder[m].size();
-            for (int32_t i2 : lorder[m]) ids.push_back(arena[cs2[i2]].rep);
-            b.b_begin = (int64_t)ids.size();
-            b.b_count = (int64_t)cs1.size();
-            for (int32_t ci : cs1) ids.push_back(arena[ci].rep);
-            req.push_back(b);
-            owner.push_back({(int32_t)m, 1});
-        }
     }
     // only the pairs with s > T can act in Algorithm 1 (every other visit is a `continue`),
-    // so only they come back from the device
-    std::vector<std::pair<int64_t, int32_t>> sig;
+    // so only they come back from the device.  A plain merge of at least chunk_pairs rep pairs
+    // scores cs2 in rep_chunks column ranges: after each range the replay restricted to the
+    // columns scored so far is exact (a cs2 cluster an earlier row merged was merged at a
+    // column already scored), so the rows that broke are known and the later ranges skip
+    // them -- Algorithm 1 never visits the rest of a row after its cluster is absorbed.
     std::vector<std::vector<SigPair>> sigm(nm);       // per merge: (i1, i2, s), s > T
-    if (!req.empty()) {
-        int64_t dev_batches = 1;
-        r = score_blocks_sig(c, P, ids, req, prm.T, sig, base, flags, &dev_batches);
+    std::vector<int32_t> cp;                          // candidate full merges: rep pairs
+    std::vector<std::vector<std::pair<uint64_t, int64_t>>> cidx(nm);   // (i1, i2) -> cp index / 2
+    std::vector<std::unordered_set<uint64_t>> have_cells(nm);
+    std::vector<int32_t> cells;
+    auto add_cells = [&](bool only_chunked, const std::vector<int32_t>& nchunks) -> int {
+        const size_t first = cp.size() / 2;
+        for (size_t m = 0; m < nm; ++m) {
+            if (only_chunked && nchunks[m] < 2) continue;
+            const auto& cs1 = sets[ms[m].left];
+            const auto& cs2 = sets[ms[m].right];
+            for (const SigPair& e : sigm[m])
+                if (e.s > prm.mT && have_cells[m].insert(key2(e.i1, e.i2)).second) {
+                    cidx[m].push_back({key2(e.i1, e.i2), (int64_t)cp.size() / 2});
+                    cp.push_back(arena[cs1[e.i1]].rep);
+                    cp.push_back(arena[cs2[e.i2]].rep);
+                }
+        }
+        const size_t nnew = cp.size() / 2 - first;
+        if (nnew == 0) return CM_OK;
+        cells.resize(cp.size() / 2 * 5);
+        const double tc0 = now_s();
+        const int rc = run_cells(c, P, cp.data() + 2 * first, (int64_t)nnew, cells.data() + 5 * first);
+        if (rc) return rc;
+        t_cells += now_s() - tc0;
+        cells_pairs += (int64_t)nnew;
+        ++batches;
+        return CM_OK;
+    };
+    auto transit = [&](size_t m, const std::unordered_map<uint64_t, int64_t>& cmap, int32_t i1,
+                       int32_t i2, bool* t21, bool* t12) {
+        const auto& cs1 = sets[ms[m].left];
+        const auto& cs2 = sets[ms[m].right];
+        const int32_t* cl = &cells[cmap.at(key2(i1, i2)) * 5];
+        const int64_t la = P.len(arena[cs1[i1]].rep), lb = P.len(arena[cs2[i2]].rep);
+        const int64_t ua = cl[0] ? la - (cl[2] - cl[1] + 1) : la;
+        const int64_t ub = cl[0] ? lb - (cl[4] - cl[3] + 1) : lb;
+        *t21 = ua < prm.mU;
+        *t12 = ub < prm.mU;
+    };
+    std::vector<int32_t> nchunks(nm, 1);
+    int32_t max_chunks = 1;
+    for (size_t m = 0; m < nm; ++m) {
+        const int64_t pairs = (int64_t)sets[ms[m].left].size() * (int64_t)sets[ms[m].right].size();
+        if (!ranked[m] && pairs >= c->chunk_pairs && sets[ms[m].right].size() > 1) {
+            nchunks[m] = (int32_t)std::min<int64_t>(std::max(1, c->rep_chunks),
+                                                   (int64_t)sets[ms[m].right].size());
+            max_chunks = std::max(max_chunks, nchunks[m]);
+        }
+    }
+    std::vector<std::vector<char>> dead(nm);
+    for (size_t m = 0; m < nm; ++m) dead[m].assign(sets[ms[m].left].size(), 0);
+    for (int32_t k = 0; k < max_chunks; ++k) {
+        // blocks of range k of every merge (all of cs2 for an unchunked merge at k = 0)
+        std::vector<int32_t> kids;
+        std::vector<BlockReq> kreq;
+        std::vector<std::vector<int32_t>> rowsel, colsel;   // per block: row and column indices
+        std::vector<std::pair<int32_t, int32_t>> kown;      // per block: (merge, transposed)
+        for (size_t m = 0; m < nm; ++m) {
+            if (ranked[m] || k >= nchunks[m]) continue;
+            const int64_t n2 = (int64_t)sets[ms[m].right].size();
+            const int32_t lo = (int32_t)(n2 * k / nchunks[m]), hi = (int32_t)(n2 * (k + 1) / nchunks[m]);
+            std::vector<int32_t> rows_alive;
+            for (int32_t i1 : qorder[m]) if (!dead[m][i1]) rows_alive.push_back(i1);
+            if (rows_alive.empty()) continue;
+            std::vector<int32_t> sc, lc;
+            for (int32_t i2 : sorder[m]) if (i2 >= lo && i2 < hi) sc.push_back(i2);
+            for (int32_t i2 : lorder[m]) if (i2 >= lo && i2 < hi) lc.push_back(i2);
+            const auto& cs1 = sets[ms[m].left];
+            const auto& cs2 = sets[ms[m].right];
+            if (!sc.empty()) {
+                BlockReq b{};
+                b.kind = kCross;
+                b.swap = 0;                                  // pair (rep1, rep2)
+                b.a_begin = (int64_t)kids.size();
+                b.a_count = (int64_t)rows_alive.size();
+                for (int32_t i1 : rows_alive) kids.push_back(arena[cs1[i1]].rep);
+                b.b_begin = (int64_t)kids.size();
+                b.b_count = (int64_t)sc.size();
+                for (int32_t i2 : sc) kids.push_back(arena[cs2[i2]].rep);
+                kreq.push_back(b);
+                rowsel.push_back(rows_alive);
+                colsel.push_back(sc);
+                kown.push_back({(int32_t)m, 0});
+            }
+            if (!lc.empty()) {
+                BlockReq b{};
+                b.kind = kCross;
+                b.swap = 1;                                  // pair (rep1, rep2) = (subject, query)
+                b.a_begin = (int64_t)kids.size();
+                b.a_count = (int64_t)lc.size();
+                for (int32_t i2 : lc) kids.push_back(arena[cs2[i2]].rep);
+                b.b_begin = (int64_t)kids.size();
+                b.b_count = (int64_t)rows_alive.size();
+                for (int32_t i1 : rows_alive) kids.push_back(arena[cs1[i1]].rep);
+                kreq.push_back(b);
+                rowsel.push_back(rows_alive);
+                colsel.push_back(lc);
+                kown.push_back({(int32_t)m, 1});
+            }
+        }
+        if (!kreq.empty()) {
+            std::vector<std::pair<int64_t, int32_t>> sig;
+            int64_t dev_batches = 1;
+            r = score_blocks_sig(c, P, kids, kreq, prm.T, sig, base, flags, &dev_batches);
+            if (r) return r;
+            batches += std::max<int64_t>(dev_batches - 1, 0) + (k > 0 ? 1 : 0);
+            for (const BlockReq& b : kreq) scored += b.a_count * b.b_count;
+            size_t bi = 0;
+            for (const auto& e : sig) {
+                while (bi + 1 < kreq.size() && base[bi + 1] <= e.first) ++bi;
+                const size_t m = (size_t)kown[bi].first;
+                const int64_t local = e.first - base[bi];
+                const int64_t nb = kreq[bi].b_count;
+                if (kown[bi].second == 0)
+                    sigm[m].push_back({rowsel[bi][local / nb], colsel[bi][local % nb], e.second});
+                else
+                    sigm[m].push_back({rowsel[bi][local % nb], colsel[bi][local / nb], e.second});
+            }
+        }
+        if (k + 1 >= max_chunks) break;
+        // the rows of the chunked merges that break within the columns scored so far
+        for (size_t m = 0; m < nm; ++m)
+            if (nchunks[m] > 1) std::sort(sigm[m].begin(), sigm[m].end());
+        r = add_cells(true, nchunks);
         if (r) return r;
-        batches += std::max<int64_t>(dev_batches - 1, 0);   // the wave counts one below
-        scored += base.empty() ? 0 : base.back();
-        size_t bi = 0;
-        for (const auto& e : sig) {
-            while (bi + 1 < req.size() && base[bi + 1] <= e.first) ++bi;
-            const size_t m = (size_t)owner[bi].first;
-            const int64_t local = e.first - base[bi];
-            const int64_t nb = req[bi].b_count;
-            if (owner[bi].second == 0)
-                sigm[m].push_back({qorder[m][local / nb], sorder[m][local % nb], e.second});
-            else
-                sigm[m].push_back({(int32_t)(local % nb), lorder[m][local / nb], e.second});
+        for (size_t m = 0; m < nm; ++m) {
+            if (nchunks[m] < 2 || k + 1 >= nchunks[m]) continue;
+            const int64_t n2 = (int64_t)sets[ms[m].right].size();
+            const int32_t hi = (int32_t)(n2 * (k + 1) / nchunks[m]);
+            std::unordered_map<uint64_t, int64_t> cmap(cidx[m].begin(), cidx[m].end());
+            std::vector<char> merged2((size_t)n2, 0);
+            for (size_t q = 0; q < sigm[m].size();) {
+                const int32_t i1 = sigm[m][q].i1;
+                size_t q1 = q;
+                while (q1 < sigm[m].size() && sigm[m][q1].i1 == i1) ++q1;
+                for (; q < q1; ++q) {
+                    const SigPair& e = sigm[m][q];
+                    if (e.i2 >= hi) continue;
+                    if (merged2[e.i2] && !partial_mode()) continue;
+                    if (e.s <= prm.mT) continue;
+                    bool t21, t12;
+                    transit(m, cmap, i1, e.i2, &t21, &t12);
+                    if (t21) { dead[m][i1] = 1; break; }
+                    if (t12) merged2[e.i2] = 1;
+                }
+                q = q1;
+            }
         }
     }
     if (d_bits) {
@@ -300,28 +406,10 @@ int Driver::run_round(const std::vector<Merge>& ms)
     t_rep += now_s() - t0;
     ++batches;
 
-    // ---- wave 2: alignment cells of every candidate full merge (s > mT and s > T) ----
-    std::vector<int32_t> cp;
-    std::vector<std::vector<std::pair<uint64_t, int64_t>>> cidx(nm);
-    for (size_t m = 0; m < nm; ++m) {
-        const auto& cs1 = sets[ms[m].left];
-        const auto& cs2 = sets[ms[m].right];
-        for (const SigPair& e : sigm[m])
-            if (e.s > prm.mT) {
-                cidx[m].push_back({key2(e.i1, e.i2), (int64_t)cp.size() / 2});
-                cp.push_back(arena[cs1[e.i1]].rep);
-                cp.push_back(arena[cs2[e.i2]].rep);
-            }
-    }
-    std::vector<int32_t> cells(cp.size() / 2 * 5);
-    if (!cp.empty()) {
-        t0 = now_s();
-        r = run_cells(c, P, cp.data(), (int64_t)cp.size() / 2, cells.data());
-        if (r) return r;
-        t_cells += now_s() - t0;
-        cells_pairs += (int64_t)cp.size() / 2;
-        ++batches;
-    }
+    // ---- wave 2: alignment cells of every candidate full merge (s > mT and s > T) not yet
+    // computed by a chunked merge's break search ----
+    r = add_cells(false, nchunks);
+    if (r) return r;
 
     // ---- Algorithm 1 control flow per merge -> event list ----
     // Visits are counted as Algorithm 1 makes them: i1's loop over cs2 (the plain merge) or

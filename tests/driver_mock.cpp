@@ -257,6 +257,8 @@ int main()
         mock::selection().keep = [](int32_t x, int32_t y) { return g->keep[(size_t)x * g->n + y] != 0; };
         cm_ctx ctx;
         ctx.greedy_chunk = 1 + (int32_t)((I.n * 7 + T) % 9);     // several chunks per instance
+        ctx.chunk_pairs = 1 + (I.n * 3 + mU) % 7;                // rep waves in column ranges
+        ctx.rep_chunks = 2 + (I.n + mT) % 4;
         cm_params prm{};
         prm.T = T;
         prm.mT = mT;
