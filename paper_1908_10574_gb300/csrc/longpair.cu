@@ -2,15 +2,16 @@
 // query spans many column passes (tandem repeats of 10,000-35,000 residues).  One warp per
 // pair would run the passes one after another; here the CTA's LW warps run them as a
 // pipeline: warp w takes passes w, w + LW, w + 2 LW, ...; pass p reads the boundary column
-// (H, E of its left neighbour column for every row) that pass p - 1 writes, trailing it by at
-// least 32 rows.  The boundary of pass p lives in global slot (p mod LW) of the CTA; a warp
-// publishes how many rows of its current pass are written in shared memory (tagged with the
-// pass), after a block fence.  Waits only point from pass p to pass p - 1 (never backwards),
-// and the warps of a CTA are co-resident, so the pipeline always advances; every wait is still
-// bounded (SwArgs::wait_limit polls of ~100 ns) and sets the error flag (2) when it gives up.
-// Slot p mod LW is rewritten by pass p + LW, which trails its reader (pass p + 1) by at least
-// 32 (LW - 1) rows through the chain of waits, so a row is never overwritten before it has
-// been read.
+// (H - o and E of its left neighbour column for every row) that pass p - 1 writes, trailing it
+// by at least 32 row groups (the wavefront of dp32.cuh: four rows per step).  The boundary of
+// pass p lives in global slot (p mod LW) of the CTA; a warp publishes how many rows of its
+// current pass are written in shared memory (tagged with the pass), after a block fence.
+// Waits only point from pass p to pass p - 1 (never backwards), and the warps of a CTA are
+// co-resident, so the pipeline always advances; every wait is still bounded
+// (SwArgs::wait_limit polls of ~100 ns) and sets the error flag (2) when it gives up.  Slot
+// p mod LW is rewritten by pass p + LW, which trails its reader (pass p + 1) by at least
+// 32 (LW - 1) row groups through the chain of waits, so a row is never overwritten before it
+// has been read.
 #include "sw16_kernel.cuh"
 
 namespace cm {
@@ -74,7 +75,7 @@ long_pair_kernel(const __grid_constant__ SwArgs a, const PairRef* __restrict__ p
         int64_t m = J.m;
         const int64_t n = J.n;
         const int npass = (int)((n + G::COLS - 1) / G::COLS);
-        if (m > a.bnd_stride) {                                 // boundary slots too short
+        if (m > a.bnd_stride || m >= ((int64_t)1 << 30)) {     // boundary slots too short
             if (tid == 0) atomicExch(a.err, 1);
             m = 0;
         }
@@ -97,139 +98,54 @@ long_pair_kernel(const __grid_constant__ SwArgs a, const PairRef* __restrict__ p
                 const int x = i / G::COLS, c = i - x * G::COLS;
                 const int ln = c / kLR, k = c - ln * kLR;
                 const int q = qres[c];
-                int32_t s = kSpad;
+                int32_t s = kSpad;                // +o: the DP keeps H - o as its diagonal input
                 if (x != kPadCode && q != kPadCode)
-                    s = (CELLS || J.swap) ? s_mat[x * kAlpha + q] : s_mat[q * kAlpha + x];
+                    s = ((CELLS || J.swap) ? s_mat[x * kAlpha + q] : s_mat[q * kAlpha + x]) + o;
                 prof[x * ROWW + ln * LS + k] = s;
             }
             __syncwarp();
             const int src = (warp + kLW - 1) % kLW;               // slot of pass - 1
-            const int2* in = slots + (int64_t)src * a.bnd_stride;
-            int2* outb = slots + (int64_t)warp * a.bnd_stride;
-            const bool has_out = pass + 1 < npass;
-            int32_t hp[kLR], fp[kLR];
-#pragma unroll
-            for (int k = 0; k < kLR; ++k) { hp[k] = 0; fp[k] = -o; }
-            int32_t out_h = 0, out_e = -o, diag0 = 0, best = 0, out_acc = 0;
-            int32_t lbest = 0, lrow = -1, lcol = -1;
-            uint32_t cur = kPadCode, prev = kPadCode;
-            int32_t bh = 0, be = -o;
-            const int32_t* plane = prof + lane * LS;
-            const int32_t col0 = (int32_t)c0 + lane * kLR;
-            for (int64_t t = 0; t < m + 31; ++t) {
-                const int j = (int)(t & 31);
-                if (j == 0) {
-                    if (pass > 0) {                              // rows [t, t + 32) of pass - 1
-                        const int32_t need = (int32_t)((t + 32 < m) ? t + 32 : m);
-                        int ok = 1;
-                        if (lane == 0) {
-                            int spins = 0;
-                            for (;;) {
-                                const int32_t ps = s_pass[src];
-                                if (ps > pass - 1 || (ps == pass - 1 && s_prog[src] >= need)) break;
-                                if (++spins > a.wait_limit) { ok = 0; break; }
-                                __nanosleep(100);
-                            }
-                            __threadfence_block();
-                        }
-                        ok = __shfl_sync(kFull, ok, 0);
-                        if (!ok) {
-                            if (lane == 0) atomicExch(a.err, 2);
-                            gave_up = true;
-                            break;
-                        }
+            // rows [0, need) of pass - 1's boundary written: lane 0 polls, bounded
+            auto wait = [&](int32_t need) {
+                int ok = 1;
+                if (lane == 0) {
+                    int spins = 0;
+                    for (;;) {
+                        const int32_t ps = s_pass[src];
+                        if (ps > pass - 1 || (ps == pass - 1 && s_prog[src] >= need)) break;
+                        if (++spins > a.wait_limit) { ok = 0; break; }
+                        __nanosleep(100);
                     }
-                    prev = cur;
-                    const int64_t r = t + lane;
-                    cur = (r < m) ? (uint32_t)(J.reverse ? J.ra[m - 1 - r] : J.ra[r]) : (uint32_t)kPadCode;
-                    if (pass > 0) {
-                        if (r < m) { const int2 v = __ldcg(in + r); bh = v.x; be = v.y; }
-                        else { bh = 0; be = -o; }
-                    }
+                    __threadfence_block();
                 }
-                const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-                int32_t hl = __shfl_up_sync(kFull, out_h, 1);
-                int32_t el = __shfl_up_sync(kFull, out_e, 1);
-                int32_t ai = __shfl_up_sync(kFull, out_acc, 1);
-                if (pass > 0) {
-                    const int32_t x = __shfl_sync(kFull, bh, j), y = __shfl_sync(kFull, be, j);
-                    if (lane == 0) { hl = x; el = y; }
-                } else if (lane == 0) {
-                    hl = 0; el = -o;
-                }
-                if (lane == 0) ai = 0;
-                int32_t dg = diag0;
-                diag0 = hl;
-                const int32_t row = (int32_t)(t - lane);
-                const int32_t* prow = plane + (int)min(rv & 31u, (uint32_t)kPadCode) * ROWW;
-                int32_t h = hl, e = el;
-#pragma unroll
-                for (int j4 = 0; j4 < kLR / 4; ++j4) {
-                    const int4 sv = *reinterpret_cast<const int4*>(prow + 4 * j4);
-                    const int32_t s4[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int k = 4 * j4 + u;
-                        e = __viaddmax_s32(h, -o, e - ge);
-                        const int32_t f = __viaddmax_s32(hp[k], -o, fp[k] - ge);
-                        fp[k] = f;
-                        const int32_t d = __viaddmax_s32(dg, s4[u], 0);
-                        dg = hp[k];
-                        h = __vimax3_s32(d, e, f);
-                        hp[k] = h;
-                        if (CELLS) {
-                            if (h > lbest) { lbest = h; lrow = row; lcol = col0 + k; }
-                        } else {
-                            best = max(best, h);
-                        }
-                    }
-                }
-                out_h = h;
-                out_e = e;
-                if (!CELLS) {
-                    out_acc = max(ai, best);
-                    if (lane == 31 && t - 31 == m - 1) gbest = max(gbest, out_acc);
-                }
-                if (has_out && t >= 31) {
-                    if (lane == 31) __stcg(outb + (t - 31), make_int2(out_h, out_e));
-                    if (j == 31 && lane == 31) {                // publish rows [0, t - 30)
-                        __threadfence_block();
-                        s_prog[warp] = (int32_t)(t - 30);
-                    }
-                }
-            }
-            if (gave_up) break;
-            if (has_out && lane == 31) {
+                return __shfl_sync(kFull, ok, 0) != 0;
+            };
+            auto publish = [&](int32_t rows) {
                 __threadfence_block();
-                s_prog[warp] = (int32_t)m;
+                s_prog[warp] = rows;
+            };
+            D32Best r;
+            if (!dp32_pass<kLR, LS, CELLS>(prof + lane * LS, J.ra, m, J.reverse != 0, o, ge,
+                                           pass > 0 ? slots + (int64_t)src * a.bnd_stride : nullptr,
+                                           pass + 1 < npass ? slots + (int64_t)warp * a.bnd_stride : nullptr,
+                                           (int32_t)c0 + lane * kLR, wait, publish, r)) {
+                if (lane == 0) atomicExch(a.err, 2);
+                gave_up = true;
+                break;
             }
             if (CELLS) {
-                // pad rows / columns stay below the maximum over real cells
-                for (int d = 16; d >= 1; d >>= 1) {
-                    const int32_t ob = __shfl_xor_sync(kFull, lbest, d);
-                    const int32_t orw = __shfl_xor_sync(kFull, lrow, d);
-                    const int32_t oc = __shfl_xor_sync(kFull, lcol, d);
-                    const bool better = ob > lbest ||
-                                        (ob == lbest && (orw < lrow || (orw == lrow && oc < lcol)));
-                    if (better) { lbest = ob; lrow = orw; lcol = oc; }
-                }
-                const bool better = lbest > gbest ||
-                                    (lbest == gbest && lbest > 0 &&
-                                     (lrow < grow || (lrow == grow && lcol < gcol)));
-                if (better) { gbest = lbest; grow = lrow; gcol = lcol; }
+                if (first_max(r.b, r.r, r.c, gbest, grow, gcol)) { gbest = r.b; grow = r.r; gcol = r.c; }
+            } else {
+                gbest = max(gbest, r.b);
             }
         }
         // combine the warps' passes: largest score, then smallest row, then smallest column
-        if (!CELLS) gbest = __shfl_sync(kFull, gbest, 31);
         if (lane == 0) { s_best[warp] = gbest; s_row[warp] = grow; s_col[warp] = gcol; }
         __syncthreads();
         if (tid == 0) {
             int32_t b = 0, rw = -1, cl = -1;
-            for (int w = 0; w < kLW; ++w) {
-                const int32_t ob = s_best[w], orw = s_row[w], oc = s_col[w];
-                const bool better = ob > b || (ob == b && ob > 0 && (orw < rw || (orw == rw && oc < cl)));
-                if (better) { b = ob; rw = orw; cl = oc; }
-            }
+            for (int w = 0; w < kLW; ++w)
+                if (first_max(s_best[w], s_row[w], s_col[w], b, rw, cl)) { b = s_best[w]; rw = s_row[w]; cl = s_col[w]; }
             if (CELLS) {
                 res[3 * out_idx] = b;
                 res[3 * out_idx + 1] = b > 0 ? rw : -1;

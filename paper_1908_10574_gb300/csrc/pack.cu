@@ -61,7 +61,9 @@ __global__ void gather_kernel(const uint8_t* __restrict__ db, const int64_t* __r
         uint8_t* dst = stream + srow[s];
         const int64_t rows = srow[s + 1] - srow[s];        // len rounded up to the row group
         for (int64_t r = lane; r < rows; r += 32) {
-            uint8_t v = (r < len) ? db[b + r] : kPadCode;
+            // codes above kPadCode never reach a stream (the SW kernels index profile rows
+            // by the low five bits without a clamp); validated input has none anyway
+            uint8_t v = (r < len) ? (uint8_t)min((int)db[b + r], (int)kPadCode) : kPadCode;
             if (r == 0) v |= kFirst;
             if (r == (len > 0 ? len - 1 : 0)) v |= kLast;
             dst[r] = v;

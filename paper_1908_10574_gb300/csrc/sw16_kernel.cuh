@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "cm_internal.h"
+#include "dp32.cuh"
 
 namespace cm {
 
@@ -166,6 +167,7 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
     // uint4 pairs of rows (one uint2 when a step has one row)
     constexpr int NB = (NR >= 2) ? NR / 2 : 1;
     uint4* bnd4 = reinterpret_cast<uint4*>(bnd);
+    const uint32_t CODEMASK = 0x1f1f1f1fu >> (32 - 8 * NR);           // residue code bits
     uint32_t LASTBITS = 0;
 #pragma unroll
     for (int q = 0; q < NR; ++q) LASTBITS |= (uint32_t)kLast << (8 * q);
@@ -261,12 +263,15 @@ __device__ __forceinline__ void warp_dp16(const SwArgs& a, const SwBlock& B,
             best = (best & keep) | (BETA2 & ~keep);
             dg[0] = (dg[0] & keep) | (BMO2 & ~keep);
         }
+        // profile row of each residue: one mask takes the flags off all NR bytes, one byte
+        // permute moves a code to the low byte (the stream writer keeps codes <= kPadCode)
+        const uint32_t rc = rv & CODEMASK, rc2 = TWO ? (rw & CODEMASK) : 0u;
         const uint32_t* prow[NR];
         const uint32_t* prow2[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
-            prow[q] = plane + min((rv >> (8 * q)) & 31u, (uint32_t)kPadCode) * G::ROWW;
-            if (TWO) prow2[q] = plane + min((rw >> (8 * q)) & 31u, (uint32_t)kPadCode) * G::ROWW;
+            prow[q] = plane + __byte_perm(rc, 0u, 0x4440u | q) * G::ROWW;
+            if (TWO) prow2[q] = plane + __byte_perm(rc2, 0u, 0x4440u | q) * G::ROWW;
             h[q] = hL[q];
             e[q] = eL[q];
         }
@@ -435,6 +440,9 @@ sw16_kernel(const __grid_constant__ SwArgs a)
 }
 
 // ---- int32 rescoring of pairs flagged by the int16 pass: one warp per pair -----------------
+// Rows stream the subject x, columns hold the query q in passes of 32 R columns; the passes of
+// a pair run one after another on the warp, the boundary column kept in the warp's own slot
+// of `bnd` (read ahead of where the same pass writes it).
 template <int R>
 __global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs a,
                                                  const PairRef* __restrict__ pr,
@@ -450,6 +458,8 @@ __global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs
     __syncwarp();
     const int o = a.gap_open, ge = a.gap_extend;
     int2* bnd = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * a.bnd_stride);
+    auto no_wait = [](int32_t) { return true; };
+    auto no_publish = [](int32_t) {};
 
     for (;;) {
         int p = 0;
@@ -461,12 +471,12 @@ __global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs
         const int64_t xoff = a.off[P.x];
         int64_t n = a.off[P.x + 1] - xoff;
         const int npass = (m <= G::COLS) ? 1 : (int)((m + G::COLS - 1) / G::COLS);
-        if (npass > 1 && n > a.bnd_stride) {
+        if ((npass > 1 && n > a.bnd_stride) || n >= ((int64_t)1 << 30)) {
             if (lane == 0) atomicExch(a.err, 1);
             n = 0;
         }
         int32_t result = 0;
-        for (int pass = 0; pass < npass; ++pass) {
+        for (int pass = 0; pass < npass && n > 0; ++pass) {
             const int64_t c0 = (int64_t)pass * G::COLS;
             __syncwarp();
             for (int c = lane; c < G::COLS; c += 32)
@@ -476,79 +486,27 @@ __global__ void __launch_bounds__(32) sw32_kernel(const __grid_constant__ SwArgs
                 const int x = i / G::COLS, c = i - x * G::COLS;
                 const int ln = c / R, k = c - ln * R;
                 const int q = qres[c];
-                int s = kSpad;
-                if (x != kPadCode && q != kPadCode) s = P.swap ? s_mat[x * kAlpha + q] : s_mat[q * kAlpha + x];
+                int s = kSpad;                    // +o: the DP keeps H - o as its diagonal input
+                if (x != kPadCode && q != kPadCode)
+                    s = (P.swap ? s_mat[x * kAlpha + q] : s_mat[q * kAlpha + x]) + o;
                 prof[x * G::ROWW + ln * G::LS + k] = s;
             }
             __syncwarp();
-            int32_t hp[R], fp[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) { hp[k] = 0; fp[k] = -o; }
-            int32_t best = 0, out_h = 0, out_e = -o, out_acc = 0, diag0 = 0;
-            uint32_t cur = kPadCode, prev = kPadCode;
-            int32_t bh = 0, be = -o;
-            const int32_t* plane = prof + lane * G::LS;
-            for (int64_t t = 0; t < n + 31; ++t) {
-                const int j = (int)(t & 31);
-                if (j == 0) {
-                    prev = cur;
-                    const int64_t r = t + lane;
-                    cur = (r < n) ? (uint32_t)a.db[xoff + r] : (uint32_t)kPadCode;
-                    if (pass > 0) {
-                        if (r < n) { const int2 v = bnd[r]; bh = v.x; be = v.y; }
-                        else { bh = 0; be = -o; }
-                    }
-                }
-                const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-                int32_t hl = __shfl_up_sync(kFull, out_h, 1);
-                int32_t el = __shfl_up_sync(kFull, out_e, 1);
-                int32_t ai = __shfl_up_sync(kFull, out_acc, 1);
-                if (pass > 0) {
-                    const int32_t x = __shfl_sync(kFull, bh, j), y = __shfl_sync(kFull, be, j);
-                    if (lane == 0) { hl = x; el = y; }
-                } else if (lane == 0) {
-                    hl = 0; el = -o;
-                }
-                if (lane == 0) ai = 0;
-                int32_t dg = diag0;
-                diag0 = hl;
-                const int32_t* prow = plane + (int)min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-                int32_t h = hl, e = el;
-#pragma unroll
-                for (int j4 = 0; j4 < R / 4; ++j4) {
-                    const int4 sv = *reinterpret_cast<const int4*>(prow + 4 * j4);
-                    const int32_t s4[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int k = 4 * j4 + u;
-                        e = __viaddmax_s32(h, -o, e - ge);
-                        const int32_t f = __viaddmax_s32(hp[k], -o, fp[k] - ge);
-                        fp[k] = f;
-                        const int32_t d = __viaddmax_s32(dg, s4[u], 0);
-                        dg = hp[k];
-                        h = __vimax3_s32(d, e, f);
-                        hp[k] = h;
-                        best = max(best, h);
-                    }
-                }
-                out_h = h;
-                out_e = e;
-                out_acc = max(ai, best);
-                const int64_t r = t - lane;
-                if (lane == 31 && n > 0 && r == n - 1) result = max(result, out_acc);
-                if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_int2(out_h, out_e);
-            }
+            D32Best r;
+            dp32_pass<R, G::LS, false>(prof + lane * G::LS, a.db + xoff, n, false, o, ge,
+                                       pass > 0 ? bnd : nullptr,
+                                       pass + 1 < npass ? bnd : nullptr,
+                                       (int32_t)c0 + lane * R, no_wait, no_publish, r);
+            result = max(result, r.b);
         }
-        if (lane == 31) a.out[P.slot] = result;
+        if (lane == 0) a.out[P.slot] = result;
     }
 }
 
 // ---- alignment cells: score plus the first row-major cell reaching it, one warp per job ----
 // Rows stream the job's first sequence a[0..m) (reversed when J.reverse), columns hold its
 // second sequence b[0..n) (reversed likewise); cell scores are matrix[a residue][b residue].
-// Every lane keeps the first (row, column) of its own best in row-major order (strict >); the
-// warp and the column passes then keep the largest score, then the smallest row, then the
-// smallest column.
+// The passes keep the largest score, then the smallest row, then the smallest column.
 template <int R>
 __global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ SwArgs a,
                                                      const CellJob* __restrict__ jobs,
@@ -565,6 +523,8 @@ __global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ Sw
     __syncwarp();
     const int o = a.gap_open, ge = a.gap_extend;
     int2* bnd = reinterpret_cast<int2*>(a.bnd + (int64_t)blockIdx.x * a.bnd_stride);
+    auto no_wait = [](int32_t) { return true; };
+    auto no_publish = [](int32_t) {};
 
     for (;;) {
         int p = 0;
@@ -577,7 +537,7 @@ __global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ Sw
         int64_t m = J.m;
         const int64_t n = J.n;
         const int npass = (n <= G::COLS) ? 1 : (int)((n + G::COLS - 1) / G::COLS);
-        if (npass > 1 && m > a.bnd_stride) {
+        if ((npass > 1 && m > a.bnd_stride) || m >= ((int64_t)1 << 30)) {
             if (lane == 0) atomicExch(a.err, 1);
             m = 0;
         }
@@ -595,78 +555,14 @@ __global__ void __launch_bounds__(32) cells_wf_kernel(const __grid_constant__ Sw
                 const int ln = c / R, k = c - ln * R;
                 const int q = qres[c];
                 prof[x * G::ROWW + ln * G::LS + k] =
-                    (x != kPadCode && q != kPadCode) ? s_mat[x * kAlpha + q] : kSpad;
+                    (x != kPadCode && q != kPadCode) ? s_mat[x * kAlpha + q] + o : kSpad;
             }
             __syncwarp();
-            int32_t hp[R], fp[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) { hp[k] = 0; fp[k] = -o; }
-            int32_t out_h = 0, out_e = -o, diag0 = 0;
-            int32_t lbest = 0, lrow = -1, lcol = -1;
-            uint32_t cur = kPadCode, prev = kPadCode;
-            int32_t bh = 0, be = -o;
-            const int32_t* plane = prof + lane * G::LS;
-            const int32_t col0 = (int32_t)c0 + lane * R;
-            for (int64_t t = 0; t < m + 31; ++t) {
-                const int j = (int)(t & 31);
-                if (j == 0) {
-                    prev = cur;
-                    const int64_t r = t + lane;
-                    cur = (r < m) ? (uint32_t)(J.reverse ? ra[m - 1 - r] : ra[r]) : (uint32_t)kPadCode;
-                    if (pass > 0) {
-                        if (r < m) { const int2 v = bnd[r]; bh = v.x; be = v.y; }
-                        else { bh = 0; be = -o; }
-                    }
-                }
-                const uint32_t rv = __shfl_sync(kFull, (lane <= j) ? cur : prev, (j - lane) & 31);
-                int32_t hl = __shfl_up_sync(kFull, out_h, 1);
-                int32_t el = __shfl_up_sync(kFull, out_e, 1);
-                if (pass > 0) {
-                    const int32_t x = __shfl_sync(kFull, bh, j), y = __shfl_sync(kFull, be, j);
-                    if (lane == 0) { hl = x; el = y; }
-                } else if (lane == 0) {
-                    hl = 0; el = -o;
-                }
-                int32_t dg = diag0;
-                diag0 = hl;
-                const int32_t row = (int32_t)(t - lane);
-                const int32_t* prow = plane + (int)min(rv & 31u, (uint32_t)kPadCode) * G::ROWW;
-                int32_t h = hl, e = el;
-#pragma unroll
-                for (int j4 = 0; j4 < R / 4; ++j4) {
-                    const int4 sv = *reinterpret_cast<const int4*>(prow + 4 * j4);
-                    const int32_t s4[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int k = 4 * j4 + u;
-                        e = __viaddmax_s32(h, -o, e - ge);
-                        const int32_t f = __viaddmax_s32(hp[k], -o, fp[k] - ge);
-                        fp[k] = f;
-                        const int32_t d = __viaddmax_s32(dg, s4[u], 0);
-                        dg = hp[k];
-                        h = __vimax3_s32(d, e, f);
-                        hp[k] = h;
-                        if (h > lbest) { lbest = h; lrow = row; lcol = col0 + k; }
-                    }
-                }
-                out_h = h;
-                out_e = e;
-                if (lane == 31 && pass + 1 < npass && t >= 31) bnd[t - 31] = make_int2(out_h, out_e);
-            }
-            // cells of pad rows / pad columns stay below the maximum over real cells, so the
-            // warp's maximum (and its first cell) lies in a real row and column
-            for (int d = 16; d >= 1; d >>= 1) {
-                const int32_t ob = __shfl_xor_sync(kFull, lbest, d);
-                const int32_t orw = __shfl_xor_sync(kFull, lrow, d);
-                const int32_t oc = __shfl_xor_sync(kFull, lcol, d);
-                const bool better = ob > lbest ||
-                                    (ob == lbest && (orw < lrow || (orw == lrow && oc < lcol)));
-                if (better) { lbest = ob; lrow = orw; lcol = oc; }
-            }
-            const bool better = lbest > gbest ||
-                                (lbest == gbest && lbest > 0 &&
-                                 (lrow < grow || (lrow == grow && lcol < gcol)));
-            if (better) { gbest = lbest; grow = lrow; gcol = lcol; }
+            D32Best r;
+            dp32_pass<R, G::LS, true>(prof + lane * G::LS, ra, m, J.reverse != 0, o, ge,
+                                      pass > 0 ? bnd : nullptr, pass + 1 < npass ? bnd : nullptr,
+                                      (int32_t)c0 + lane * R, no_wait, no_publish, r);
+            if (first_max(r.b, r.r, r.c, gbest, grow, gcol)) { gbest = r.b; grow = r.r; gcol = r.c; }
         }
         if (lane == 0) {
             res[3 * (int64_t)p] = gbest;

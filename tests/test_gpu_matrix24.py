@@ -57,7 +57,8 @@ def test_scores_match_oracle(ctx, S):
 def test_long_tandem_repeats_int32_and_cells(ctx):
     rng = np.random.default_rng(8)
     motif = _with_extra_letters(rng, synth.random_seq(rng, 40), 0.2)
-    longs = [synth.tandem_repeat(rng, int(L), motif=motif) for L in (7000, 8000)]
+    # long enough that the same-motif pair scores above the int16 range (int32 rescoring)
+    longs = [synth.tandem_repeat(rng, int(L), motif=motif) for L in (11000, 12500)]
     ss = synth.SeqSet.from_list(longs + [_with_extra_letters(rng, synth.random_seq(rng, 300))])
     pairs = np.array([(0, 1), (1, 0), (0, 2), (2, 1)], dtype=np.int32)
     got = ctx.sw_score_batch(ss.seqs, ss.offsets, pairs, P24, 11, 1)
