@@ -293,6 +293,81 @@ def stratum_recall(found, truth, n):
     return float(np.isin(t, keys(found)).mean()) if len(t) else 1.0
 
 
+# algorithmic FLOPs of the ranker per residue row embedded: three 9-tap convolutions
+# (32 -> 128, 128 -> 128, 128 -> 128 channels), 2 FLOPs per multiply-add; training runs the
+# forward, the data-gradient and the weight-gradient contraction of each (3x the forward)
+RANKER_FWD_FLOPS_PER_ROW = 2 * 9 * (32 * 128 + 128 * 128 + 128 * 128)
+
+
+def measured_peak(key, fallback):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
+def run_train(args):
+    """--workload train: one training run of the learned ranker (the learned path's cost) on a
+    synthetic proteome, as a bench line against the bf16 tensor-core roofline.  Pairs are drawn
+    inside groups of --train-group proteins (grouped_training_pairs) and labelled by the GPU SW
+    path before the timed region; the timed region is cm_ranker_train for --epochs epochs."""
+    import torch
+    import paper_1908_10574_gb300 as cm
+
+    torch.cuda.set_device(0)
+    ctx = cm.Context(0)
+    tr = synth.proteome(args.train_seqs, family_size=8, singleton_frac=0.2, stream=3)
+    rng = np.random.default_rng(13)
+    group = max(args.train_group, 2)
+    pairs, _ = grouped_training_pairs(tr.family, args.train_pairs, group, rng)
+    y = (ctx.sw_score_batch(tr.seqs, tr.offsets, pairs, synth.BLOSUM62, GAP_OPEN, GAP_EXT) >
+         T_SIG).astype(np.float32)
+    batch_pairs = int(1.5 * len(pairs) * group / max(len(tr), 1)) + 64
+    flags = cm.CM_TRAIN_COMPONENTS | cm.CM_TRAIN_COSINE
+    ctx.ranker_init(13)
+    ctx.ranker_standardize(tr.seqs, tr.offsets, max_sample=2048)
+    warm = pairs[: max(1, len(pairs) // 20)]
+    ctx.ranker_train(tr.seqs, tr.offsets, warm, y[: len(warm)], epochs=1, batch_pairs=batch_pairs,
+                     lr=args.lr, seed=13, flags=flags)
+    ctx.ranker_init(13)
+    ctx.ranker_standardize(tr.seqs, tr.offsets, max_sample=2048)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0, args.clocks_dir)
+    clk.start()
+    ctx.reset_stats()
+    t0 = time.perf_counter()
+    loss = ctx.ranker_train(tr.seqs, tr.offsets, pairs, y, epochs=args.epochs,
+                            batch_pairs=batch_pairs, lr=args.lr, seed=13, flags=flags)
+    dt = time.perf_counter() - t0
+    clocks = clk.stop()
+    st = ctx.stats()
+    used = np.unique(pairs.reshape(-1))
+    rows = float(tr.lengths[used].astype(np.float64).sum()) * args.epochs
+    flops = 3.0 * RANKER_FWD_FLOPS_PER_ROW * rows
+    achieved = flops / dt / 1e12
+    peak, basis = measured_peak("bf16_tflops_sustained", 1700.0)
+    print(json.dumps({
+        "metric": "ranker training throughput (bf16 tensor-core convolutions)",
+        "value": achieved, "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "ranker training on %d synthetic proteins (lognormal lengths "
+                               "median 350), %d grouped pairs (groups of %d), %d epoch(s), "
+                               "whole components per step, cosine learning rate"
+                               % (len(tr), len(pairs), group, args.epochs)},
+        "train_seconds": dt, "epochs": args.epochs, "residue_rows": rows,
+        "algorithmic_tflop": flops / 1e12, "last_batch_loss": loss,
+        "gpu_launches": st["launches"], "device_ms": st["total_ms"],
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "bf16 dense, sustained (%s)" % basis,
+                     "achieved_basis": "3 x %d FLOPs per residue row embedded per epoch over "
+                                       "the wall time of cm_ranker_train (host and device)"
+                                       % RANKER_FWD_FLOPS_PER_ROW},
+        "clocks": clocks}))
+
+
 def run_cluster_merge(args):
     """ClusterMerge end to end on a proteome-shaped set (default: 100,000 proteins, 80,000 in
     10,000 families of 8 plus 20,000 singletons); recall against the GPU all-against-all when
@@ -321,11 +396,24 @@ def run_cluster_merge(args):
         ctx.ranker_standardize(ss.seqs, ss.offsets, max_sample=2048)
         z = ctx.ranker_logits(ss.seqs, ss.offsets, synth.random_pairs(len(ss), 20000, stream=21))
         ranker = {"untrained": True, "prune_logit": float(np.quantile(z, args.ranker_untrained))}
+    clk = ClockSampler(0, args.clocks_dir)
+    clk.start()
     t0 = time.perf_counter()
-    res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT, mU)
+    res = ctx.cluster_merge(ss.seqs, ss.offsets, synth.BLOSUM62, GAP_OPEN, GAP_EXT, T, mT, mU,
+                            state_path=args.cm_state, budget_seconds=args.cm_budget)
     dt = time.perf_counter() - t0
+    clocks = clk.stop()
+    if res is None:
+        # stopped at a round boundary past --cm-budget; the state is in --cm-state
+        print(json.dumps({"metric": "ClusterMerge seconds", "stopped": True,
+                          "state": args.cm_state, "seconds_this_call": dt, "clocks": clocks}),
+              flush=True)
+        return
+    if args.cm_state:
+        dt = res["stats"]["seconds"]                  # every call of the checkpointed run
     progress("plain merge", {"seconds": dt, "clusters": len(res["clusters"]),
-                             "similar_pairs": len(res["pairs"]), "stats": res["stats"]})
+                             "similar_pairs": len(res["pairs"]), "stats": res["stats"],
+                             "clocks": clocks})
     ranked = None
     if ranker is not None:
         t1 = time.perf_counter()
@@ -339,7 +427,7 @@ def run_cluster_merge(args):
                                   "similar_pairs": len(ranked["pairs"]), "stats": ranked["stats"]})
         ranker["clusters"] = len(ranked["clusters"])
         ranker["similar_pairs"] = len(ranked["pairs"])
-    out = {"metric": "ClusterMerge seconds", "value": dt, "unit": "s", "n_gpus": 1,
+    out = {"metric": "ClusterMerge seconds", "value": dt, "unit": "s", "n_gpus": 1, "clocks": clocks,
            "higher_is_better": False, "data": "synthetic", "dtype": "int16",
            "config": {"workload": "ClusterMerge of %d synthetic proteins (lognormal lengths, "
                                   "families of %d + %d%% singletons%s), BLOSUM62 11/1, T=%d, mT=%d, "
@@ -371,6 +459,8 @@ def run_cluster_merge(args):
         out["recall"] = r
         if ranked is not None:
             ranker["recall"] = subset_recall(ranked["pairs"][:, :2], subset, truth_sub)[0]
+        progress("sample recall", {"recall": r, "recall_sample": out["recall_sample"],
+                                   "seconds": out["all_pairs_seconds"]})
     elif args.recall:
         t1 = time.perf_counter()
         truth = set()
@@ -399,6 +489,7 @@ def run_cluster_merge(args):
                                 "seconds": time.perf_counter() - t1}
         if ranked is not None:
             ranker["family_recall"] = stratum_recall(ranked["pairs"][:, :2], truth_f, n)
+        progress("family recall", out["family_recall"])
     out["comparisons_fraction"] = (res["stats"]["rep_comparisons"] +
                                    res["stats"]["exchange_comparisons"] +
                                    res["stats"]["intra_comparisons"]) / max(n * (n - 1) / 2, 1)
@@ -608,8 +699,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "cm"],
-                    help="allpairs: SW GCUPS (default); cm: ClusterMerge seconds")
+    ap.add_argument("--workload", default="allpairs", choices=["allpairs", "cm", "train"],
+                    help="allpairs: SW GCUPS (default); cm: ClusterMerge seconds; train: ranker "
+                         "training TFLOP/s")
     ap.add_argument("--cm-seqs", type=int, default=100000)
     ap.add_argument("--recall", action="store_true")
     ap.add_argument("--recall-sample", type=float, default=0.0, metavar="F",
@@ -620,6 +712,11 @@ def main():
     ap.add_argument("--family-size", type=int, default=8, help="cm: proteins per family")
     ap.add_argument("--singleton-frac", type=float, default=0.2,
                     help="cm: fraction of proteins outside any family")
+    ap.add_argument("--cm-state", default=None, metavar="PATH",
+                    help="cm: checkpointed merge (cluster_merge_resume): resume from PATH if it "
+                         "holds a state, save the state there when stopping")
+    ap.add_argument("--cm-budget", type=float, default=0.0, metavar="S",
+                    help="cm with --cm-state: stop at the first round boundary after S seconds")
     ap.add_argument("--batch-slots", type=int, default=0,
                     help="cm: pair slots of one device batch of the rep wave (0: library default)")
     ap.add_argument("--long-tail", type=int, default=0,
@@ -655,6 +752,9 @@ def main():
     args = ap.parse_args()
     if args.workload == "cm":
         run_cluster_merge(args)
+        return
+    if args.workload == "train":
+        run_train(args)
         return
     world, rank, local = dist_init()
     if args.impl == "reference":

@@ -58,6 +58,7 @@ extern "C" {
 #define CM_ERR_TIMEOUT    -5   /* a bounded device wait gave up (a long pair's pass pipeline) */
 #define CM_ERR_CAPACITY   -6   /* output capacity too small; *n_found holds the needed size */
 #define CM_ERR_INTERNAL   -7   /* a kernel's own bounds check fired (a library bug) */
+#define CM_STOPPED         1   /* cluster_merge_resume stopped at a round boundary, state saved */
 
 /* ---- flags ---- */
 #define CM_DEVICE_PTRS    0x1u  /* all array arguments are device pointers */
@@ -252,6 +253,26 @@ int cluster_merge(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets, int3
                   const int8_t *matrix, int32_t gap_open, int32_t gap_extend,
                   const cm_params *params, cm_result **out, uint32_t flags);
 void cm_result_free(cm_result *result);
+
+/* cluster_merge_resume -- cluster_merge with round-state checkpoints (the position in
+ * Algorithm 2's merge schedule plus the clusters of every set a later round reads).  If
+ * `state_path` names a checkpoint, the run resumes after its last completed round; a
+ * checkpoint of another problem (sequence lengths, matrix, gaps, params or flags differ) is
+ * rejected with CM_ERR_ARG -- the caller must pass the same residues, which are not
+ * fingerprinted.  With budget_seconds > 0 the call stops after the first completed round at
+ * which budget_seconds have passed since it began (unless no round is left), writes the
+ * checkpoint to `state_path` (through a temporary file renamed over it) and returns CM_STOPPED
+ * with *out = NULL; call again to continue.  Otherwise, or once every round is done, it
+ * finishes as cluster_merge and returns CM_OK; result->seconds then sums the wall time of
+ * every call of the run.  The result equals cluster_merge's (clusters, member order, pairs and
+ * the logical comparison counts); comparisons_scored may grow, since scores cached in one call
+ * are recomputed in the next.  With the ranker, the context must hold the same ranker weights
+ * in every call (cm_ranker_load).  Errors as cluster_merge, plus CM_ERR_ARG for an unreadable,
+ * truncated or foreign state file or one that cannot be written. */
+int cluster_merge_resume(cm_ctx *ctx, const uint8_t *seqs, const int64_t *offsets,
+                         int32_t n_seqs, const int8_t *matrix, int32_t gap_open,
+                         int32_t gap_extend, const cm_params *params, const char *state_path,
+                         double budget_seconds, cm_result **out, uint32_t flags);
 
 /* greedy_cluster -- incremental greedy clustering, the comparison method of Sec. 2 (after
  * Wittwer et al.), on the same kernels: sequences in input order are compared with every

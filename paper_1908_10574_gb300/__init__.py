@@ -16,7 +16,7 @@ import numpy as np
 from . import _lib as _L
 from ._lib import (CMError, CM_ASCII, CM_GAP_BLAST, CM_FORCE_INT32, CM_DEVICE_PTRS,  # noqa: F401
                    CM_TRAIN_COMPONENTS, CM_TRAIN_COSINE, CM_MERGE_SEQUENTIAL, CM_MERGE_PARTIAL,
-                   CM_MATRIX24)
+                   CM_MATRIX24, CM_STOPPED)
 
 __all__ = ["Context", "sw_score_batch", "sw_cells_batch", "sw_allpairs", "CMError",
            "default_context", "sw_cells_batch_noalloc", "cluster_merge", "ops_to_cigar"]
@@ -260,10 +260,14 @@ class Context:
 
 
     def cluster_merge(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
-                      use_ranker=False, prune_logit=0.0, ranker_min_pairs=0, merge_mode=0):
+                      use_ranker=False, prune_logit=0.0, ranker_min_pairs=0, merge_mode=0,
+                      state_path=None, budget_seconds=0.0):
         """ClusterMerge (Algorithms 1 and 2 with the Sec. 4 transitivity test) plus the
         intra-cluster all-against-all.  Returns a dict: clusters [(rep, [members])], pairs
-        (k, 3) int64 (i, j, score) sorted, and the comparison counters."""
+        (k, 3) int64 (i, j, score) sorted, and the comparison counters.  With `state_path`
+        (cluster_merge_resume): resumes from the checkpoint there if there is one, and with
+        budget_seconds > 0 stops at the first round boundary past the budget, saves the
+        state and returns None."""
         seqs, offsets, matrix, _ = self._inputs(seqs, offsets, matrix)
         flags |= self._prep([seqs, offsets, matrix])
         flags |= self._matrix_flag(matrix)
@@ -271,9 +275,18 @@ class Context:
         prm = _L.cm_params(int(T), int(mT), int(mU), int(bool(use_ranker)), float(prune_logit),
                            int(ranker_min_pairs), int(merge_mode))
         res = ctypes.POINTER(_L.cm_result)()
-        _L.check(self._h, _L.lib().cluster_merge(self._h, _ptr(seqs), _ptr(offsets), n,
-                                                 _ptr(matrix), int(gap_open), int(gap_extend),
-                                                 ctypes.byref(prm), ctypes.byref(res), flags))
+        if state_path is None:
+            _L.check(self._h, _L.lib().cluster_merge(self._h, _ptr(seqs), _ptr(offsets), n,
+                                                     _ptr(matrix), int(gap_open), int(gap_extend),
+                                                     ctypes.byref(prm), ctypes.byref(res), flags))
+            return self._result(res)
+        code = _L.lib().cluster_merge_resume(self._h, _ptr(seqs), _ptr(offsets), n, _ptr(matrix),
+                                             int(gap_open), int(gap_extend), ctypes.byref(prm),
+                                             os.fsencode(state_path), float(budget_seconds),
+                                             ctypes.byref(res), flags)
+        if code == _L.CM_STOPPED:
+            return None
+        _L.check(self._h, code)
         return self._result(res)
 
     def greedy_cluster(self, seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0):
@@ -450,7 +463,8 @@ def sw_cells_batch_noalloc(seqs, offsets, pairs, matrix, gap_open, gap_extend, c
 
 
 def cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT, mU, flags=0,
-                  use_ranker=False, prune_logit=0.0, ranker_min_pairs=0, merge_mode=0):
+                  use_ranker=False, prune_logit=0.0, ranker_min_pairs=0, merge_mode=0,
+                  state_path=None, budget_seconds=0.0):
     return default_context().cluster_merge(seqs, offsets, matrix, gap_open, gap_extend, T, mT,
                                            mU, flags, use_ranker, prune_logit, ranker_min_pairs,
-                                           merge_mode)
+                                           merge_mode, state_path, budget_seconds)

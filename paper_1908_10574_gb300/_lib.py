@@ -11,6 +11,7 @@ LIB_PATH = os.path.join(_HERE, "libcm.so")
 
 CM_OK = 0
 CM_ERR_CAPACITY = -6
+CM_STOPPED = 1
 CM_DEVICE_PTRS = 0x1
 CM_ASCII = 0x2
 CM_GAP_BLAST = 0x4
@@ -99,6 +100,10 @@ def lib():
                                          ctypes.POINTER(ctypes.POINTER(cm_result)), u32]),
         "greedy_cluster": (ctypes.c_int, [p, p, p, i32, p, i32, i32, ctypes.POINTER(cm_params),
                                           ctypes.POINTER(ctypes.POINTER(cm_result)), u32]),
+        "cluster_merge_resume": (ctypes.c_int, [p, p, p, i32, p, i32, i32,
+                                                ctypes.POINTER(cm_params), ctypes.c_char_p,
+                                                ctypes.c_double,
+                                                ctypes.POINTER(ctypes.POINTER(cm_result)), u32]),
         "cm_result_free": (None, [ctypes.POINTER(cm_result)]),
         "cm_ranker_num_params": (i64, []),
         "cm_ranker_init": (ctypes.c_int, [p, ctypes.c_uint64]),

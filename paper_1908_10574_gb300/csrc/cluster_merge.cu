@@ -16,6 +16,8 @@
 // The result (clusters, member order, similar pairs, logical comparison counts) equals the
 // plain sequential algorithm's; speculation only adds alignments that are never looked at.
 #include <algorithm>
+#include <cstdio>
+#include <string>
 #include <cmath>
 #include <chrono>
 #include <cstdlib>
@@ -243,11 +245,12 @@ int Driver::run_round(const std::vector<Merge>& ms)
         by_len(cs2, lorder[m]);
     }
     // only the pairs with s > T can act in Algorithm 1 (every other visit is a `continue`),
-    // so only they come back from the device.  A plain merge of at least chunk_pairs rep pairs
-    // scores cs2 in rep_chunks column ranges: after each range the replay restricted to the
-    // columns scored so far is exact (a cs2 cluster an earlier row merged was merged at a
-    // column already scored), so the rows that broke are known and the later ranges skip
-    // them -- Algorithm 1 never visits the rest of a row after its cluster is absorbed.
+    // so only they come back from the device.  A plain merge of at least 2 chunk_pairs rep
+    // pairs scores cs2 in column ranges of at least chunk_pairs pairs (at most rep_chunks
+    // ranges): after each range the replay restricted to the columns scored so far is exact
+    // (a cs2 cluster an earlier row merged was merged at a column already scored), so the rows
+    // that broke are known and the later ranges skip them -- Algorithm 1 never visits the
+    // rest of a row after its cluster is absorbed.
     std::vector<std::vector<SigPair>> sigm(nm);       // per merge: (i1, i2, s), s > T
     std::vector<int32_t> cp;                          // candidate full merges: rep pairs
     std::vector<std::vector<std::pair<uint64_t, int64_t>>> cidx(nm);   // (i1, i2) -> cp index / 2
@@ -292,9 +295,11 @@ int Driver::run_round(const std::vector<Merge>& ms)
     int32_t max_chunks = 1;
     for (size_t m = 0; m < nm; ++m) {
         const int64_t pairs = (int64_t)sets[ms[m].left].size() * (int64_t)sets[ms[m].right].size();
-        if (!ranked[m] && pairs >= c->chunk_pairs && sets[ms[m].right].size() > 1) {
-            nchunks[m] = (int32_t)std::min<int64_t>(std::max(1, c->rep_chunks),
-                                                   (int64_t)sets[ms[m].right].size());
+        if (!ranked[m] && pairs >= 2 * c->chunk_pairs && sets[ms[m].right].size() > 1) {
+            // ranges of at least chunk_pairs pairs, at most rep_chunks of them
+            nchunks[m] = (int32_t)std::min<int64_t>(
+                std::min<int64_t>(std::max(1, c->rep_chunks), pairs / c->chunk_pairs),
+                (int64_t)sets[ms[m].right].size());
             max_chunks = std::max(max_chunks, nchunks[m]);
         }
     }
@@ -1031,6 +1036,58 @@ int Driver::run_greedy(int32_t n, int32_t chunk, std::vector<int32_t>& final_set
     return CM_OK;
 }
 
+// ---- round-state checkpoints: Algorithm 2's schedule position plus the cluster arena ----
+// File: "CMRS", version, a fingerprint of the problem (sequence lengths, matrix, gaps,
+// params), the rounds completed, the driver's counters and timers, the seconds of earlier
+// calls, then every set a later round reads: set id, its clusters (rep, members in order).
+// The score memo is not kept: a resumed run rescores what it needs, with the same results.
+constexpr uint32_t kStateMagic = 0x53524d43u;      // "CMRS"
+constexpr uint32_t kStateVersion = 1;
+
+uint64_t fnv(uint64_t h, const void* p, size_t n)
+{
+    const uint8_t* b = static_cast<const uint8_t*>(p);
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+uint64_t fingerprint(const Prepared& P, int32_t n, const cm_params& prm, uint32_t flags)
+{
+    uint64_t h = 14695981039346656037ull;
+    h = fnv(h, &n, sizeof(n));
+    h = fnv(h, P.hoff.data(), P.hoff.size() * sizeof(int64_t));
+    h = fnv(h, P.mat, sizeof(P.mat));
+    h = fnv(h, &P.g1, sizeof(P.g1));
+    h = fnv(h, &P.ge, sizeof(P.ge));
+    const int32_t pv[6] = {prm.T, prm.mT, prm.mU, prm.use_ranker, prm.ranker_min_pairs,
+                           prm.merge_mode};
+    h = fnv(h, pv, sizeof(pv));
+    h = fnv(h, &prm.prune_logit, sizeof(prm.prune_logit));
+    h = fnv(h, &flags, sizeof(flags));
+    return h;
+}
+
+struct StateFile {
+    FILE* f = nullptr;
+    bool ok = true;
+    ~StateFile() { if (f) std::fclose(f); }
+    template <class T> void put(const T& v) { ok = ok && std::fwrite(&v, sizeof(T), 1, f) == 1; }
+    template <class T> void get(T& v) { ok = ok && std::fread(&v, sizeof(T), 1, f) == 1; }
+    void put_vec(const std::vector<int32_t>& v)
+    {
+        put((uint64_t)v.size());
+        ok = ok && (v.empty() || std::fwrite(v.data(), sizeof(int32_t), v.size(), f) == v.size());
+    }
+    void get_vec(std::vector<int32_t>& v, uint64_t limit)
+    {
+        uint64_t k = 0;
+        get(k);
+        if (!ok || k > limit) { ok = false; return; }
+        v.resize((size_t)k);
+        ok = ok && (k == 0 || std::fread(v.data(), sizeof(int32_t), (size_t)k, f) == k);
+    }
+};
+
 }  // namespace
 }  // namespace cm
 
@@ -1038,9 +1095,10 @@ using namespace cm;
 
 extern "C" {
 
-int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
-                  const int8_t* matrix, int32_t gap_open, int32_t gap_extend,
-                  const cm_params* params, cm_result** out, uint32_t flags)
+static int run_cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets,
+                             int32_t n_seqs, const int8_t* matrix, int32_t gap_open,
+                             int32_t gap_extend, const cm_params* params, const char* state_path,
+                             double budget_seconds, cm_result** out, uint32_t flags)
 {
     if (!c) return CM_ERR_ARG;
     NvtxRange range("cluster_merge");
@@ -1056,26 +1114,10 @@ int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_
     if (params->merge_mode != CM_MERGE_SEQUENTIAL && params->merge_mode != CM_MERGE_PARTIAL)
         return fail(c, CM_ERR_ARG, "merge_mode must be CM_MERGE_SEQUENTIAL or CM_MERGE_PARTIAL");
     const uint32_t dflags = flags & CM_FORCE_INT32;     // device data is resident from here on
-    cm_result* res = (cm_result*)std::calloc(1, sizeof(cm_result));
-    if (!res) return fail(c, CM_ERR_OOM, "host allocation failed");
-    res->n_seqs = n_seqs;
     Driver D(c, P, *params, dflags);
-    if (params->use_ranker) {
-        const double tr = now_s();
-        r = ranker_unit_vectors(c, P, n_seqs, &D.U);
-        if (r) { cm_result_free(res); return r; }
-        D.t_rank += now_s() - tr;
-    }
 
     // Algorithm 2: FIFO of singleton sets -> merge DAG -> dependency rounds
-    D.arena.resize((size_t)n_seqs);
     D.sets.resize((size_t)std::max(1, 2 * n_seqs));
-    for (int32_t e = 0; e < n_seqs; ++e) {
-        D.arena[e].rep = e;
-        D.arena[e].objs = {e};
-        D.arena[e].mem = {e};
-        D.sets[e] = {e};
-    }
     std::deque<int32_t> q;
     std::vector<int32_t> round_of((size_t)std::max(1, 2 * n_seqs), 0);
     std::vector<std::vector<Merge>> rounds;
@@ -1091,18 +1133,154 @@ int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_
         rounds[rd - 1].push_back({a, b, o});
         q.push_back(o);
     }
-    for (auto& ms : rounds) {
-        r = D.run_round(ms);
-        if (r) { cm_result_free(res); return r; }
-        ++D.rounds;
+
+    const uint64_t fp = fingerprint(P, n_seqs, *params, dflags);
+    size_t first_round = 0;
+    double earlier_seconds = 0;
+    bool resumed = false;
+    if (state_path) {
+        StateFile F;
+        F.f = std::fopen(state_path, "rb");
+        if (F.f) {
+            uint32_t magic = 0, version = 0;
+            uint64_t fp_file = 0, nsets = 0;
+            int64_t done = 0;
+            F.get(magic);
+            F.get(version);
+            F.get(fp_file);
+            if (!F.ok || magic != kStateMagic || version != kStateVersion)
+                return fail(c, CM_ERR_ARG, "state file is not a ClusterMerge checkpoint");
+            if (fp_file != fp)
+                return fail(c, CM_ERR_ARG, "state file belongs to another problem or parameters");
+            F.get(done);
+            int64_t* cnt[] = {&D.rep_cmp, &D.exch_cmp, &D.full_merges, &D.exchanges, &D.scored,
+                              &D.cells_pairs, &D.batches, &D.merges, &D.waves, &D.selected};
+            for (int64_t* x : cnt) F.get(*x);
+            double* tm[] = {&D.t_rep, &D.t_cells, &D.t_exch, &D.t_intra, &D.t_rank,
+                            &earlier_seconds};
+            for (double* x : tm) F.get(*x);
+            F.get(nsets);
+            if (!F.ok || done < 0 || done > (int64_t)rounds.size() || nsets > D.sets.size())
+                return fail(c, CM_ERR_ARG, "state file is truncated or inconsistent");
+            for (uint64_t k = 0; k < nsets && F.ok; ++k) {
+                int32_t sid = -1;
+                uint64_t ncl = 0;
+                F.get(sid);
+                F.get(ncl);
+                if (!F.ok || sid < 0 || (size_t)sid >= D.sets.size() || ncl > (uint64_t)n_seqs) {
+                    F.ok = false;
+                    break;
+                }
+                for (uint64_t i = 0; i < ncl && F.ok; ++i) {
+                    Cluster cl;
+                    F.get(cl.rep);
+                    F.get_vec(cl.objs, (uint64_t)n_seqs);
+                    if (!F.ok || cl.objs.empty() || cl.objs[0] != cl.rep) { F.ok = false; break; }
+                    for (int32_t x : cl.objs) {
+                        if (x < 0 || x >= n_seqs || !cl.mem.insert(x).second) F.ok = false;
+                    }
+                    D.sets[sid].push_back((int32_t)D.arena.size());
+                    D.arena.push_back(std::move(cl));
+                }
+            }
+            if (!F.ok) return fail(c, CM_ERR_ARG, "state file is truncated or inconsistent");
+            first_round = (size_t)done;
+            D.rounds = done;
+            resumed = true;
+        }
     }
+    if (!resumed) {
+        D.arena.resize((size_t)n_seqs);
+        for (int32_t e = 0; e < n_seqs; ++e) {
+            D.arena[e].rep = e;
+            D.arena[e].objs = {e};
+            D.arena[e].mem = {e};
+            D.sets[e] = {e};
+        }
+    }
+    if (params->use_ranker) {
+        const double tr = now_s();
+        r = ranker_unit_vectors(c, P, n_seqs, &D.U);
+        if (r) return r;
+        D.t_rank += now_s() - tr;
+    }
+    auto elapsed = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    for (size_t k = first_round; k < rounds.size(); ++k) {
+        r = D.run_round(rounds[k]);
+        if (r) return r;
+        ++D.rounds;
+        if (state_path && budget_seconds > 0 && k + 1 < rounds.size() &&
+            elapsed() >= budget_seconds) {
+            // the sets later rounds read: inputs of rounds k+1.. made by rounds <= k or leaves
+            std::vector<int32_t> live;
+            for (size_t j = k + 1; j < rounds.size(); ++j)
+                for (const Merge& m : rounds[j])
+                    for (int32_t sid : {m.left, m.right})
+                        if (sid < n_seqs || round_of[sid] <= (int32_t)(k + 1)) live.push_back(sid);
+            std::sort(live.begin(), live.end());
+            live.erase(std::unique(live.begin(), live.end()), live.end());
+            const std::string tmp = std::string(state_path) + ".tmp";
+            {
+                StateFile F;
+                F.f = std::fopen(tmp.c_str(), "wb");
+                if (!F.f) return fail(c, CM_ERR_ARG, "cannot write the state file");
+                F.put(kStateMagic);
+                F.put(kStateVersion);
+                F.put(fp);
+                F.put((int64_t)(k + 1));
+                for (int64_t x : {D.rep_cmp, D.exch_cmp, D.full_merges, D.exchanges, D.scored,
+                                  D.cells_pairs, D.batches, D.merges, D.waves, D.selected})
+                    F.put(x);
+                for (double x : {D.t_rep, D.t_cells, D.t_exch, D.t_intra, D.t_rank,
+                                 earlier_seconds + elapsed()})
+                    F.put(x);
+                F.put((uint64_t)live.size());
+                for (int32_t sid : live) {
+                    F.put(sid);
+                    F.put((uint64_t)D.sets[sid].size());
+                    for (int32_t ci : D.sets[sid]) {
+                        F.put(D.arena[ci].rep);
+                        F.put_vec(D.arena[ci].objs);
+                    }
+                }
+                if (!F.ok || std::fflush(F.f) != 0)
+                    return fail(c, CM_ERR_ARG, "cannot write the state file");
+            }
+            if (std::rename(tmp.c_str(), state_path) != 0)
+                return fail(c, CM_ERR_ARG, "cannot write the state file");
+            return CM_STOPPED;
+        }
+    }
+    cm_result* res = (cm_result*)std::calloc(1, sizeof(cm_result));
+    if (!res) return fail(c, CM_ERR_OOM, "host allocation failed");
+    res->n_seqs = n_seqs;
     std::vector<int32_t> final_set;
     if (!q.empty()) final_set = D.sets[q.front()];
     r = D.finish(final_set, res);
     if (r) { cm_result_free(res); return r; }
-    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    res->seconds = earlier_seconds + elapsed();
     *out = res;
     return CM_OK;
+}
+
+int cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,
+                  const int8_t* matrix, int32_t gap_open, int32_t gap_extend,
+                  const cm_params* params, cm_result** out, uint32_t flags)
+{
+    return run_cluster_merge(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, params,
+                             nullptr, 0.0, out, flags);
+}
+
+int cluster_merge_resume(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets,
+                         int32_t n_seqs, const int8_t* matrix, int32_t gap_open,
+                         int32_t gap_extend, const cm_params* params, const char* state_path,
+                         double budget_seconds, cm_result** out, uint32_t flags)
+{
+    if (!state_path) return c ? fail(c, CM_ERR_ARG, "null state path") : CM_ERR_ARG;
+    return run_cluster_merge(c, seqs, offsets, n_seqs, matrix, gap_open, gap_extend, params,
+                             state_path, budget_seconds, out, flags);
 }
 
 int greedy_cluster(cm_ctx* c, const uint8_t* seqs, const int64_t* offsets, int32_t n_seqs,

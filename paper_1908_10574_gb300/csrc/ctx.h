@@ -39,8 +39,8 @@ struct cm_ctx {
     int64_t max_batch_slots = (int64_t)1 << 32;   // slots of one rep-wave device batch
     int32_t wait_limit = 1 << 24;           // polls (~100 ns each) of a bounded device wait
     int32_t greedy_chunk = 2048;            // sequences per device batch of greedy_cluster
-    int64_t chunk_pairs = (int64_t)1 << 24; // plain merges with more rep pairs score cs2 in chunks
-    int32_t rep_chunks = 4;                 // ... of this many columns ranges
+    int64_t chunk_pairs = (int64_t)1 << 24; // plain merges of >= 2x this many rep pairs score cs2
+    int32_t rep_chunks = 16;                // ... in column ranges of >= chunk_pairs, at most this many
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t aux = nullptr;             // second stream: alternate length bins overlap tails
     cudaEvent_t fork = nullptr, join = nullptr;

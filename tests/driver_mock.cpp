@@ -6,7 +6,8 @@
 // output slot of a plan is written exactly once.
 //
 // Input (stdin, whitespace separated): K instances, each
-//   n T mT mU use_ranker ranker_min_pairs merge_mode algorithm (0 cluster_merge, 1 greedy)
+//   n T mT mU use_ranker ranker_min_pairs merge_mode algorithm (0 cluster_merge, 1 greedy,
+//   2 cluster_merge_resume stopping after every round; argv[1] = the state file)
 //   len[n]  M[n*n]  cov[n*n]  keep[n*n]
 // Output per instance: "clusters C" then C lines "rep size members...", "pairs P" then P lines
 // "i j s", then "stats rep exchange intra full_merges exchanges merges", or "error code msg".
@@ -230,8 +231,9 @@ cudaError_t launch_kept_expand(const KeptList* lists, int32_t nlists, const uint
 
 }  // namespace cm
 
-int main()
+int main(int argc, char** argv)
 {
+    const char* state_path = argc > 1 ? argv[1] : "driver_mock.state";
     int K = 0;
     std::cin >> K;
     for (int inst = 0; inst < K; ++inst) {
@@ -270,8 +272,35 @@ int main()
         int8_t mat[400] = {};
         uint8_t dummy = 0;
         cm_result* res = nullptr;
-        const int r = algorithm ? greedy_cluster(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm, &res, 0)
-                                : cluster_merge(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm, &res, 0);
+        int r = 0;
+        if (algorithm == 1) {
+            r = greedy_cluster(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm, &res, 0);
+        } else if (algorithm == 2) {
+            // checkpointed run: stop after every round, resume from the state file
+            std::remove(state_path);
+            int calls = 0;
+            do {
+                r = cluster_merge_resume(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm,
+                                         state_path, 1e-12, &res, 0);
+                ++calls;
+            } while (r == CM_STOPPED && calls < 64);
+            if (r == CM_OK && calls > 1) {
+                // a checkpoint of another problem is refused
+                cm_params other = prm;
+                other.T += 1;
+                cm_result* res2 = nullptr;
+                const int r2 = cluster_merge_resume(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1,
+                                                    &other, state_path, 0.0, &res2, 0);
+                if (r2 != CM_ERR_ARG || res2) {
+                    std::printf("error %d foreign checkpoint accepted\n", r2);
+                    cm_result_free(res);
+                    continue;
+                }
+            }
+            if (r == CM_OK) std::fprintf(stderr, "resumed %d\n", calls);
+        } else {
+            r = cluster_merge(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1, &prm, &res, 0);
+        }
         if (r) {
             std::printf("error %d %s\n", r, ctx.err.c_str());
             continue;

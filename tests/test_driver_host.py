@@ -14,6 +14,7 @@ oracle's merge_partial) and for the incremental greedy clustering (greedy_cluste
 oracle's greedy)."""
 import importlib
 import os
+import re
 import shutil
 import subprocess
 
@@ -71,15 +72,17 @@ def _instance(rng):
     greedy = int(rng.random() < 0.25)
     if greedy:
         use_ranker = partial = 0
+    resume = int(not greedy and rng.random() < 0.3)
     return dict(n=n, T=T, mT=mT, mU=mU, use_ranker=use_ranker, min_pairs=min_pairs, L=L, M=M,
-                cov=cov, keep=keep, partial=partial, greedy=greedy)
+                cov=cov, keep=keep, partial=partial, greedy=greedy, resume=resume)
 
 
 def _serialise(insts):
     out = [str(len(insts))]
     for d in insts:
         out.append("%d %d %d %d %d %d %d %d" % (d["n"], d["T"], d["mT"], d["mU"], d["use_ranker"],
-                                               d["min_pairs"], d["partial"], d["greedy"]))
+                                               d["min_pairs"], d["partial"],
+                                               2 if d["resume"] else d["greedy"]))
         for key in ("L", "M", "cov", "keep"):
             out.append(" ".join(str(int(v)) for v in np.asarray(d[key]).reshape(-1)))
     return "\n".join(out) + "\n"
@@ -146,11 +149,12 @@ def test_driver_replay_matches_oracle(tmp_path):
                     "-x", "c++", os.path.join(HERE, "driver_mock.cpp"), "-o", exe], check=True)
     rng = np.random.default_rng(1908)
     insts = [_instance(rng) for _ in range(400)]
-    out = subprocess.run([exe], input=_serialise(insts), capture_output=True, text=True,
-                         timeout=600)
+    out = subprocess.run([exe, str(tmp_path / "cm.state")], input=_serialise(insts),
+                         capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     got = _parse(out.stdout, len(insts))
-    exercised = {"ranked": 0, "full": 0, "exchange": 0, "long": 0, "partial": 0, "greedy": 0}
+    exercised = {"ranked": 0, "full": 0, "exchange": 0, "long": 0, "partial": 0, "greedy": 0,
+                 "resumed": sum(int(x) > 2 for x in re.findall(r"resumed (\d+)", out.stderr))}
     for d, g in zip(insts, got):
         want = _oracle(d)
         assert g[0] == want[0], ("clusters", d["n"], d["use_ranker"])

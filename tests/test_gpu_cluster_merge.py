@@ -128,3 +128,23 @@ def test_transitivity_handworked_cases(ctx):
         _check(got, _oracle_cm(ss, tt.T, case["mT"], case["mU"]))
         cells = ctx.sw_cells_batch(ss.seqs, ss.offsets, np.array([[0, 1]], np.int32), S62, 11, 1)
         assert tuple(cells[0]) == (case["score"],) + case["cells"], case["why"]
+
+
+def test_checkpointed_run_matches_uninterrupted(ctx, tmp_path):
+    """cluster_merge_resume stopping after every round (budget ~0), resumed from the state file
+    until done: the same clusters, pairs and logical counts as the oracle's uninterrupted run,
+    and the state of this problem is refused for other parameters."""
+    ss = synth.proteome(600, family_size=6, singleton_frac=0.25, stream=5)
+    T, mT, mU = 100, 138, 15
+    want = _oracle_cm(ss, T, mT, mU)
+    path = str(tmp_path / "cm.state")
+    calls, got = 0, None
+    while got is None and calls < 40:
+        got = ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T, mT, mU, state_path=path,
+                                budget_seconds=1e-9)
+        calls += 1
+    assert got is not None and calls > 3        # one call per round boundary, then the finish
+    _check(got, want)
+    assert got["stats"]["rounds"] == calls
+    with pytest.raises(cm.CMError):
+        ctx.cluster_merge(ss.seqs, ss.offsets, S62, 11, 1, T + 1, mT, mU, state_path=path)
