@@ -358,7 +358,7 @@ def run_train(args):
                                % (len(tr), len(pairs), group, args.epochs)},
         "train_seconds": dt, "epochs": args.epochs, "residue_rows": rows,
         "algorithmic_tflop": flops / 1e12, "last_batch_loss": loss,
-        "gpu_launches": st["launches"], "device_ms": st["total_ms"],
+        "gpu_launches": st["launches"],
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_basis": "bf16 dense, sustained (%s)" % basis,
