@@ -65,7 +65,6 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
                  "l"(src), "r"(valid ? 16 : 0));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // sum the per-chunk partials into the gradient vector (first M rows of the padded tile)
@@ -124,14 +123,28 @@ __global__ void pool_bwd_kernel(const float* __restrict__ dv, const int32_t* __r
 }
 
 // db3[n] += sum over the batch's non-empty sequences of dv[s][n]
-__global__ void dv_sum_kernel(const float* __restrict__ dv, const int32_t* __restrict__ slen,
-                              int64_t ns, float* __restrict__ db)
+// the last layer's bias gradient: the sum over the batch's (non-empty) sequences of dv; one
+// block of kDvGroups x kCh threads, group g summing sequences g, g + kDvGroups, ..., then the
+// groups' partial sums in a fixed order (deterministic)
+constexpr int kDvGroups = 8;
+
+__global__ void __launch_bounds__(kDvGroups * kCh)
+dv_sum_kernel(const float* __restrict__ dv, const int32_t* __restrict__ slen, int64_t ns,
+              float* __restrict__ db)
 {
-    const int n = threadIdx.x;
+    __shared__ float part[kDvGroups][kCh];
+    const int n = threadIdx.x % kCh, g = threadIdx.x / kCh;
     float t = 0.f;
-    for (int64_t s = 0; s < ns; ++s)
+    for (int64_t s = g; s < ns; s += kDvGroups)
         if (slen[s] > 0) t += dv[s * kCh + n];
-    db[n] += t;
+    part[g][n] = t;
+    __syncthreads();
+    if (g == 0) {
+        float u = 0.f;
+#pragma unroll
+        for (int k = 0; k < kDvGroups; ++k) u += part[k][n];
+        db[n] += u;
+    }
 }
 
 // one warp per pair: logit = alpha * cos(v_a, v_b) + beta, the loss and the gradients of v,
@@ -488,12 +501,16 @@ template <int CIN, int NOUT, int EPI>
 int conv_tc(cm_ctx* c, Ranker* K, const bf16* X, int64_t R, const bf16* Wk, const ConvEpi& ep)
 {
     using C = tc::ConvCfg<CIN, NOUT>;
+    const int64_t tiles = blocks_for(R, tc::kTcRows);
+    if (tiles == 0) return CM_OK;
     CUtensorMap ta, tb;
-    CUDA_TRY(tc::make_tmap_bf16(&ta, X, CIN, (uint64_t)R, C::BK, tc::kTcRows));
+    CUDA_TRY(tc::make_tmap_bf16(&ta, X, CIN, (uint64_t)R, C::BK, C::AROWS));
     CUDA_TRY(tc::make_tmap_bf16(&tb, Wk, kTaps * CIN, NOUT, C::BK, NOUT));
     auto kern = tc::conv_tc_kernel<CIN, NOUT, EPI>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    kern<<<blocks_for(R, tc::kTcRows), 128, C::SMEM, c->stream>>>(ta, tb, R, ep, K->tc_err);
+    // persistent: one CTA per SM over the 128-row tiles
+    const int grid = (int)std::min<int64_t>(tiles, std::max(1, c->num_sms));
+    kern<<<grid, tc::kConvThreads, C::SMEM, c->stream>>>(ta, tb, R, ep, K->tc_err);
     CUDA_TRY(cudaGetLastError());
     c->stats.launches += 1;
     return CM_OK;
@@ -581,7 +598,8 @@ int wgrad(cm_ctx* c, Ranker* K, const bf16* X, const bf16* dY, int64_t R, float*
     using C = tc::WgradCfg<CIN>;
     const int M = kTaps * CIN;
     const int mtiles = C::MTILES, MPAD = mtiles * 128;
-    const int64_t want = std::max<int64_t>(1, (2 * (int64_t)c->num_sms + mtiles - 1) / mtiles);
+    // chunks of rows: about one CTA per SM over all m-tiles (each CTA a long K loop)
+    const int64_t want = std::max<int64_t>(1, (int64_t)c->num_sms / mtiles);
     const int64_t steps = (R + C::BKR - 1) / C::BKR;
     const int64_t rpc = ((steps + want - 1) / want) * C::BKR;
     const int64_t nch = (R + rpc - 1) / rpc;
@@ -697,7 +715,7 @@ int loss_grad_packed(cm_ctx* c, const Prepared& P, Ranker* K, const Packed& B, c
     AENSURE(A_DY2, R * kCh * 2, dY2);
     pool_bwd_kernel<<<blocks_for(R * (kCh / 8), 256), 256, 0, st>>>(dv, rowseq, d_slen, R, dZ);  // dY3
     // b3's gradient: every real row of a sequence carries dv / len, so the rows sum to dv
-    dv_sum_kernel<<<1, kCh, 0, st>>>(dv, d_slen, ns, K->grad + kOffB3);
+    dv_sum_kernel<<<1, kDvGroups * kCh, 0, st>>>(dv, d_slen, ns, K->grad + kOffB3);
     c->stats.launches += 2;
     ConvEpi ep{};
     ep.rowseq = rowseq;
