@@ -82,9 +82,10 @@ def total_cells(ss):
 
 
 # DRAM bytes per cell of the int16 kernel, from one ncu capture of the small case
-# (`--parts-per-gpu 512 --part-offset 50 --warps 16 --rows 8192`): 6,589,184 bytes read and 0
-# written for 64,034,019,251 cells; sequence rows are re-read from L2, not HBM.
-DRAM_BYTES_PER_CELL = 6589184 / 64034019251
+# (`--steps 1 --warmup 0 --parts-per-gpu 512 --part-offset 50 --no-e2e --no-cpu-baseline --no-cm
+# --warps 16 --rows 8192`, `-k regex:sw16_kernel -c 1`): 6,448,640 bytes read and 0 written for
+# 64,034,019,251 cells in 11.71 ms; sequence rows are re-read from L2, not HBM.
+DRAM_BYTES_PER_CELL = 6448640 / 64034019251
 
 
 def part_sequence(n_parts, count, offset=0):
@@ -841,7 +842,7 @@ def main():
             "traffic": DRAM_BYTES_PER_CELL * cells_per_launch,
             "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the "
                              "small case (part 253 of 512: sw16_kernel<22,16,0>, 6.40e10 cells, "
-                             "6.59 MB read, 0 written), scaled by cells per launch",
+                             "6.45 MB read, 0 written), scaled by cells per launch",
             "kernel": "sw16_kernel (int16x2 DPX wavefront)",
             "peak_basis": "%d SMs x median SM clock under load x %.2f DPX lane-ops per clk per SM "
                           "(measured in this run by cm_dpx_rate) x 2 cells per %.1f ops (the "
