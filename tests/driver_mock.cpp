@@ -285,7 +285,32 @@ int main(int argc, char** argv)
                 ++calls;
             } while (r == CM_STOPPED && calls < 64);
             if (r == CM_OK && calls > 1) {
-                // a checkpoint of another problem is refused
+                // a truncated checkpoint is refused, and so is one of another problem
+                {
+                    FILE* f = std::fopen(state_path, "rb");
+                    std::vector<char> bytes;
+                    if (f) {
+                        int ch;
+                        while ((ch = std::fgetc(f)) != EOF) bytes.push_back((char)ch);
+                        std::fclose(f);
+                    }
+                    const std::string cut = std::string(state_path) + ".cut";
+                    FILE* g2 = std::fopen(cut.c_str(), "wb");
+                    if (g2) {
+                        std::fwrite(bytes.data(), 1, bytes.size() / 2, g2);
+                        std::fclose(g2);
+                    }
+                    cm_result* res3 = nullptr;
+                    const int r3 = cluster_merge_resume(&ctx, &dummy, I.off.data(), I.n, mat, 11, 1,
+                                                        &prm, cut.c_str(), 0.0, &res3, 0);
+                    std::remove(cut.c_str());
+                    if (r3 != CM_ERR_ARG || res3) {
+                        std::printf("error %d truncated checkpoint accepted\n", r3);
+                        cm_result_free(res3);
+                        cm_result_free(res);
+                        continue;
+                    }
+                }
                 cm_params other = prm;
                 other.T += 1;
                 cm_result* res2 = nullptr;
