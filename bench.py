@@ -62,7 +62,7 @@ M_T, M_U = 138, 15
 GAP_OPEN, GAP_EXT = 11, 1
 PARTS_PER_GPU = 16
 OPS_PER_PACKED_CELL = 4.5    # DPX/ALU-pipe operations of the kernel's cell update, 2 cells each
-OPS_PER_PACKED_CELL_SURVEY = 7.0   # the plain per-cell count (E 2, F 2, H 2, running max 1)
+OPS_PER_PACKED_CELL_PLAIN = 7.0   # the plain per-cell count (E 2, F 2, H 2, running max 1)
 
 
 def workload_desc(n_parts):
@@ -835,7 +835,7 @@ def main():
     # the DPX issue rate measured on this GPU in this run (cm_dpx_rate), lane-ops / clk / SM
     rate = dpx_rate
     peak = n_sm * (clk_mhz * 1e6) * rate * 2.0 / OPS_PER_PACKED_CELL / 1e9 if clk_mhz else None
-    peak7 = n_sm * (clk_mhz * 1e6) * rate * 2.0 / OPS_PER_PACKED_CELL_SURVEY / 1e9 if clk_mhz else None
+    peak7 = n_sm * (clk_mhz * 1e6) * rate * 2.0 / OPS_PER_PACKED_CELL_PLAIN / 1e9 if clk_mhz else None
     cells_per_launch = st["cells"] / max(st["sw16_launches"], 1)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
             "frac": (achieved / peak) if (achieved and peak) else None,
