@@ -506,6 +506,73 @@ int compact_sig(cm_ctx* c, const int32_t* out, int64_t slots, int32_t T,
     return CM_OK;
 }
 
+int score_pairs_int32(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& pairs,
+                      std::vector<int32_t>& scores)
+{
+    const int64_t n = (int64_t)pairs.size() / 2;
+    scores.assign((size_t)n, 0);
+    if (n == 0) return CM_OK;
+    if (n >= ((int64_t)1 << 31)) return fail(c, CM_ERR_ARG, "too many pairs");
+    const cudaStream_t st = c->stream;
+    std::vector<PairRef> lst((size_t)n);
+    for (int64_t k = 0; k < n; ++k) lst[k] = PairRef{pairs[2 * k], pairs[2 * k + 1], 0, 0, k};
+    // long pairs first, for whole CTAs; the rest longest first on one warp each
+    auto is_long = [&](const PairRef& x) {
+        return P.len(x.q) >= kLongMinCols && P.len(x.x) >= kLongMinRows;
+    };
+    std::stable_sort(lst.begin(), lst.end(), [&](const PairRef& x, const PairRef& y) {
+        const bool lx = is_long(x), ly = is_long(y);
+        if (lx != ly) return lx;
+        return P.len(x.q) * P.len(x.x) > P.len(y.q) * P.len(y.x);
+    });
+    int32_t nlong = 0;
+    while (nlong < n && is_long(lst[nlong])) ++nlong;
+    PairRef* d_pref;
+    int32_t *d_out, *d_flags;
+    uint2* d_bnd;
+    ENSURE(B_PREF, n, d_pref);
+    ENSURE(B_OUT, n, d_out);
+    ENSURE(B_FLAGS, kFlagWords, d_flags);
+    const int64_t stride = (P.maxlen + 64 + 1) & ~(int64_t)1;
+    const int64_t nslot = std::max<int64_t>((int64_t)c->num_sms * kLongSlots,
+                                            (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
+    ENSURE(B_BND, nslot * stride, d_bnd);
+    int r = copy_in(c, d_pref, lst.data(), lst.size() * sizeof(PairRef), false);
+    if (r) return r;
+    CUDA_TRY(cudaMemsetAsync(d_flags, 0, kFlagWords * sizeof(int32_t), st));
+    SwArgs a{};
+    a.db = P.db;
+    a.off = P.off;
+    a.out = d_out;
+    a.err = d_flags + 1;
+    a.wait_limit = c->wait_limit;
+    std::memcpy(a.mat, P.mat, sizeof(a.mat));
+    a.gap_open = P.g1;
+    a.gap_extend = P.ge;
+    a.beta = P.beta;
+    a.sat_thr = P.sat_thr;
+    a.bnd = d_bnd;
+    a.bnd_stride = stride;
+    if (nlong > 0) {
+        CUDA_TRY(launch_long_sw32((int)std::min<int64_t>(nlong, c->num_sms), a, d_pref, nlong,
+                                  d_flags + 5, st));
+        c->stats.launches += 1;
+    }
+    if (n > nlong) {
+        const int grid = (int)std::min<int64_t>(n - nlong, (int64_t)c->num_sms * std::max(1, sw32_ctas_per_sm()));
+        CUDA_TRY(launch_sw32(16, grid, a, d_pref + nlong, (int32_t)(n - nlong), d_flags + 3, st));
+        c->stats.launches += 1;
+    }
+    int32_t kerr = 0;
+    CUDA_TRY(cudaMemcpyAsync(scores.data(), d_out, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&kerr, d_flags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (kerr == 2) return fail(c, CM_ERR_TIMEOUT, "a long-pair pipeline wait gave up");
+    if (kerr) return fail(c, CM_ERR_INTERNAL, "kernel bounds check fired (boundary buffer)");
+    c->stats.pairs += n;
+    return CM_OK;
+}
+
 int run_cells(cm_ctx* c, const Prepared& P, const int32_t* hp, int64_t n_pairs, int32_t* hcells)
 {
     if (n_pairs == 0) return CM_OK;

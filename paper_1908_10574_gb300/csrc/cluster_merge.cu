@@ -801,43 +801,83 @@ int Driver::score_ranked(const std::vector<Merge>& ms, const std::vector<char>& 
 int Driver::finish(std::vector<int32_t>& final_set, cm_result* res)
 {
     NvtxRange range("cm intra-cluster pairs");
-    // intra-cluster all-against-all: one TRI block per cluster (members in length order)
-    std::vector<int32_t> ids;
+    // intra-cluster all-against-all: one TRI block per cluster (members in length order).  A
+    // cluster with two or more members longer than kLongSubject splits: TRI over its short
+    // members, a CROSS block of the long members (queries) against the short ones, and the
+    // long x long pairs straight on the int32 whole-CTA kernels (in a TRI block each of them
+    // is one warp's stream over dozens of column passes while the CTA's other warps wait,
+    // and such pairs of one family exceed the int16 range and are rescored anyway).
+    std::vector<int32_t> ids, ll;
     std::vector<BlockReq> req;
+    auto add_block = [&](int32_t kind, const int32_t* a, int64_t na, const int32_t* b, int64_t nb) {
+        BlockReq blk{};
+        blk.kind = kind;
+        blk.swap = 0;
+        blk.a_begin = (int64_t)ids.size();
+        blk.a_count = na;
+        ids.insert(ids.end(), a, a + na);
+        if (kind == kTri) {
+            blk.b_begin = blk.a_begin;
+            blk.b_count = na;
+        } else {
+            blk.b_begin = (int64_t)ids.size();
+            blk.b_count = nb;
+            ids.insert(ids.end(), b, b + nb);
+        }
+        req.push_back(blk);
+    };
     for (int32_t ci : final_set) {
         const Cluster& cl = arena[ci];
         if (cl.objs.size() < 2) continue;
         std::vector<int32_t> mem = by_length(cl.objs);
-        BlockReq b{};
-        b.kind = kTri;
-        b.swap = 0;
-        b.a_begin = b.b_begin = (int64_t)ids.size();
-        b.a_count = b.b_count = (int64_t)mem.size();
-        ids.insert(ids.end(), mem.begin(), mem.end());
-        req.push_back(b);
+        const int64_t n = (int64_t)mem.size();
+        int64_t p = n;                                   // first member longer than kLongSubject
+        while (p > 0 && P.len(mem[p - 1]) > kLongSubject) --p;
+        if (n - p < 2) {
+            add_block(kTri, mem.data(), n, nullptr, 0);
+            continue;
+        }
+        if (p >= 2) add_block(kTri, mem.data(), p, nullptr, 0);
+        if (p >= 1) add_block(kCross, mem.data() + p, n - p, mem.data(), p);
+        for (int64_t k = p + 1; k < n; ++k)
+            for (int64_t s2 = p; s2 < k; ++s2) {
+                ll.push_back(mem[k]);
+                ll.push_back(mem[s2]);
+            }
     }
-    std::vector<int32_t> S;
+    std::vector<int32_t> S, SL;
     std::vector<int64_t> base;
     const double t0 = now_s();
-    int r = score_blocks(c, P, ids, req, S, base, flags);
+    int r = req.empty() ? CM_OK : score_blocks(c, P, ids, req, S, base, flags);
+    if (r) return r;
+    r = score_pairs_int32(c, P, ll, SL);
     if (r) return r;
     t_intra += now_s() - t0;
-    scored += (int64_t)S.size();
+    scored += (int64_t)S.size() + (int64_t)SL.size();
     ++batches;
     std::vector<uint64_t> all;
     std::vector<std::pair<uint64_t, int32_t>> sig;
-    all.reserve(S.size());
+    all.reserve(S.size() + SL.size());
+    auto visit = [&](int32_t x, int32_t y, int32_t score) {
+        const int32_t i = std::min(x, y), j = std::max(x, y);
+        all.push_back(key2(i, j));
+        if (score > prm.T) sig.push_back({key2(i, j), score});
+    };
     for (size_t b = 0; b < req.size(); ++b) {
         const int32_t* A = ids.data() + req[b].a_begin;
         const int64_t na = req[b].a_count;
         int64_t slot = base[b];
-        for (int64_t k = 1; k < na; ++k)
-            for (int64_t s = 0; s < k; ++s, ++slot) {
-                const int32_t i = std::min(A[k], A[s]), j = std::max(A[k], A[s]);
-                all.push_back(key2(i, j));
-                if (S[slot] > prm.T) sig.push_back({key2(i, j), S[slot]});
-            }
+        if (req[b].kind == kTri) {
+            for (int64_t k = 1; k < na; ++k)
+                for (int64_t s2 = 0; s2 < k; ++s2, ++slot) visit(A[k], A[s2], S[slot]);
+        } else {
+            const int32_t* B = ids.data() + req[b].b_begin;
+            const int64_t nb = req[b].b_count;
+            for (int64_t k = 0; k < na; ++k)
+                for (int64_t s2 = 0; s2 < nb; ++s2, ++slot) visit(A[k], B[s2], S[slot]);
+        }
     }
+    for (size_t k = 0; k < SL.size(); ++k) visit(ll[2 * k], ll[2 * k + 1], SL[k]);
     std::sort(all.begin(), all.end());
     const int64_t intra = std::unique(all.begin(), all.end()) - all.begin();
     std::sort(sig.begin(), sig.end());

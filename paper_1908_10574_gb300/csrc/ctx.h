@@ -172,6 +172,14 @@ int score_blocks_sig(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& i
 int compact_sig(cm_ctx* c, const int32_t* out, int64_t nslots, int32_t T,
                 std::vector<std::pair<int64_t, int32_t>>& sig);
 
+// Exact int32 scores of host pairs (pairs[2k] = query: columns, pairs[2k + 1] = subject:
+// rows) straight on the int32 kernels, with no int16 pass: pairs of >= kLongMinCols columns and
+// >= kLongMinRows rows on whole CTAs (passes pipelined over the warps), the rest one warp each.
+// Meant for pairs of two long sequences, for which the int16 pass runs one warp per pair and
+// mostly marks the pair for rescoring anyway.  scores[k] = f(pair k).
+int score_pairs_int32(cm_ctx* c, const Prepared& P, const std::vector<int32_t>& pairs,
+                      std::vector<int32_t>& scores);
+
 // Score and alignment cells (5 int32 per pair) of host pairs, on the device data of P.
 int run_cells(cm_ctx* c, const Prepared& P, const int32_t* host_pairs, int64_t n_pairs,
               int32_t* host_cells);

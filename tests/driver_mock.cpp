@@ -181,6 +181,17 @@ int run_plan(cm_ctx* c, const Prepared&, Plan& plan, int32_t* out, const int64_t
     return CM_OK;
 }
 
+int g_int32_pairs = 0;                               // pairs scored by score_pairs_int32
+
+int score_pairs_int32(cm_ctx*, const Prepared&, const std::vector<int32_t>& pairs,
+                      std::vector<int32_t>& scores)
+{
+    scores.resize(pairs.size() / 2);
+    for (size_t k = 0; k < scores.size(); ++k) scores[k] = pair_score(pairs[2 * k], pairs[2 * k + 1], 0);
+    g_int32_pairs += (int)scores.size();
+    return CM_OK;
+}
+
 int run_cells(cm_ctx*, const Prepared&, const int32_t* hp, int64_t n_pairs, int32_t* hcells)
 {
     for (int64_t k = 0; k < n_pairs; ++k) {
@@ -345,5 +356,6 @@ int main(int argc, char** argv)
                     (long long)res->full_merges, (long long)res->exchanges, (long long)res->merges);
         cm_result_free(res);
     }
+    std::fprintf(stderr, "int32 pairs %d\n", g_int32_pairs);
     return 0;
 }

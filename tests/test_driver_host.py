@@ -154,7 +154,8 @@ def test_driver_replay_matches_oracle(tmp_path):
     assert out.returncode == 0, out.stderr[-2000:]
     got = _parse(out.stdout, len(insts))
     exercised = {"ranked": 0, "full": 0, "exchange": 0, "long": 0, "partial": 0, "greedy": 0,
-                 "resumed": sum(int(x) > 2 for x in re.findall(r"resumed (\d+)", out.stderr))}
+                 "resumed": sum(int(x) > 2 for x in re.findall(r"resumed (\d+)", out.stderr)),
+                 "long x long": int(re.findall(r"int32 pairs (\d+)", out.stderr)[-1])}
     for d, g in zip(insts, got):
         want = _oracle(d)
         assert g[0] == want[0], ("clusters", d["n"], d["use_ranker"])
