@@ -1223,6 +1223,11 @@ static int run_cluster_merge(cm_ctx* c, const uint8_t* seqs, const int64_t* offs
                     D.arena.push_back(std::move(cl));
                 }
             }
+            // every set a remaining round reads must have come back (and hold a cluster)
+            for (size_t j = (size_t)done; j < rounds.size() && F.ok; ++j)
+                for (const Merge& m : rounds[j])
+                    for (int32_t sid : {m.left, m.right})
+                        if (round_of[sid] <= (int32_t)done && D.sets[sid].empty()) F.ok = false;
             if (!F.ok) return fail(c, CM_ERR_ARG, "state file is truncated or inconsistent");
             first_round = (size_t)done;
             D.rounds = done;
