@@ -611,7 +611,8 @@ def grouped_training_pairs(family, n_pairs, group, rng):
     gend = cum[last]
     gsize = gend - gstart
     n = len(family)
-    k = np.maximum(2, np.round(n_pairs * gsize / n).astype(np.int64))
+    # a group of one protein (a trailing singleton) has no pair to draw
+    k = np.where(gsize >= 2, np.maximum(2, np.round(n_pairs * gsize / n).astype(np.int64)), 0)
     multi = np.flatnonzero(sizes > 1)
     mg = gid_fam[multi]
     mcount = np.bincount(mg, minlength=ngroups)
@@ -676,6 +677,12 @@ def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, tra
                             flags=(cm.CM_TRAIN_COMPONENTS if group > 0 else 0) |
                                   (cm.CM_TRAIN_COSINE if cosine else 0))
     t_train = time.perf_counter() - t0
+    # algorithmic convolution work of the training run: with whole components per step every
+    # protein of the training pairs is embedded once per epoch (3 x the forward per row)
+    tflops = None
+    if group > 0:
+        rows = float(tr.lengths[np.unique(pairs[:cut].reshape(-1))].astype(np.float64).sum())
+        tflops = 3.0 * RANKER_FWD_FLOPS_PER_ROW * rows * epochs / max(t_train, 1e-9) / 1e12
     z = ctx.ranker_logits(tr.seqs, tr.offsets, pairs[cut:])
     yh = y[cut:]
     thr = float(np.quantile(z[yh == 1], 1.0 - keep))
@@ -689,6 +696,9 @@ def train_ranker(ctx, n_train_seqs, n_pairs, epochs, keep, seed=13, lr=1e-3, tra
             "group": group, "batch_pairs": batch_pairs, "cosine": cosine,
             "positives": float(y.mean()), "epochs": epochs, "lr": lr, "last_batch_loss": loss,
             "label_seconds": t_label, "train_seconds": t_train, "heldout_auc": auc,
+            "train_tflops": tflops,
+            "train_frac_of_bf16_sustained": (tflops / measured_peak("bf16_tflops_sustained", 1700.0)[0]
+                                             if tflops is not None else None),
             "prune_logit": thr, "keep_heldout_positives": keep,
             "heldout_negatives_kept": float((z[yh == 0] >= thr).mean())}
 
