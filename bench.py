@@ -570,7 +570,9 @@ def cm_comparison(ctx, n_seqs=100000, recipes=(CM_RECIPE,), clocks_dir=None, dev
         out["learned"].append({
             "recipe": rc, "seconds_total": t_train + t_merge, "seconds_merge": t_merge,
             "seconds_training_path": t_train, "label_seconds": info["label_seconds"],
-            "train_seconds": info["train_seconds"], "heldout_auc": info["heldout_auc"],
+            "train_seconds": info["train_seconds"], "train_tflops": info["train_tflops"],
+            "train_frac_of_bf16_sustained": info["train_frac_of_bf16_sustained"],
+            "heldout_auc": info["heldout_auc"],
             "heldout_negatives_kept": info["heldout_negatives_kept"],
             "recall": recall(ranked),
             "family_recall": stratum_recall(ranked["pairs"][:, :2], truth_f, n),

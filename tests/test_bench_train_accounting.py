@@ -1,7 +1,8 @@
-"""The benchmark's learned-path record (bench.train_ranker) on the CPU with a stand-in context:
-the training pairs, the held-out split, the pruning threshold and the algorithmic convolution
-work it reports (3 x the forward FLOPs per residue of every protein in the training pairs, per
-epoch) -- no GPU call is made."""
+"""The benchmark's learned-path record (bench.train_ranker) and the default line's ClusterMerge
+comparison (bench.cm_comparison) on the CPU with a stand-in context: the training pairs, the
+held-out split, the pruning threshold, the algorithmic convolution work it reports (3 x the
+forward FLOPs per residue of every protein in the training pairs, per epoch) and the keys of
+the comparison record -- no GPU call is made."""
 import os
 import sys
 
@@ -58,3 +59,35 @@ def test_training_work_accounting():
     assert 0 < info["train_frac_of_bf16_sustained"] < info["train_tflops"]
     # separable stand-in logits: every held-out negative is pruned at a 99.9 % keep
     assert info["heldout_auc"] == 1.0 and info["heldout_negatives_kept"] == 0.0
+
+
+class StandInMerge(StandInContext):
+    """Adds ClusterMerge and the all-against-all: similar pairs = the within-family pairs."""
+
+    def _family_pairs(self):
+        fp = bench.family_pairs(self.family)
+        return np.concatenate([fp, np.full((len(fp), 1), bench.T_SIG + 50)], 1).astype(np.int64)
+
+    def cluster_merge(self, seqs, offsets, matrix, go, ge, T, mT, mU, use_ranker=False,
+                      prune_logit=0.0, ranker_min_pairs=0):
+        keys = ("rep_comparisons", "exchange_comparisons", "intra_comparisons",
+                "comparisons_scored", "full_merges", "exchanges", "rounds", "t_rep", "t_cells",
+                "t_exchange", "t_intra", "t_rank", "ranker_selected")
+        return {"pairs": self._family_pairs(), "clusters": [(0, [0])],
+                "stats": {k: 1 for k in keys}}
+
+    def sw_allpairs(self, seqs, offsets, matrix, go, ge, T, part, parts, capacity=0):
+        p = self._family_pairs()
+        return p[part::parts, :2].astype(np.int32), p[part::parts, 2].astype(np.int32)
+
+
+def test_comparison_record_on_the_cpu():
+    """The default bench line's ClusterMerge comparison, end to end on the stand-in: every
+    key of the record is present and the learned entry carries the training work."""
+    out = bench.cm_comparison(StandInMerge(synth.proteome(300, family_size=8, singleton_frac=0.2,
+                                                          stream=3).family), n_seqs=300)
+    assert out["plain"]["recall"] == 1.0 and out["truth_pairs"] > 0
+    (lr,) = out["learned"]
+    assert lr["recall"] == 1.0 and lr["train_tflops"] > 0
+    assert 0 < lr["train_frac_of_bf16_sustained"] < 1e6
+    assert lr["seconds_total"] >= lr["seconds_merge"] > 0
